@@ -1,0 +1,209 @@
+"""Python face of the CPU oracle (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It loads ``liboracle.so`` (built from
+``lgf_oracle.c`` with gcc + OpenMP) through ctypes and wraps it with numpy.
+Nothing here touches the CUDA library, and the CUDA library never calls this.
+
+Functions (each cites the passage of Liska & Colonius, arXiv:1604.01814, that
+it follows; the C source documents the numerical method):
+  ive_all            e^{-z} I_k(z), k = 0..nmax                App. A, Eq. lgf_intfac
+  lgf_quad           G_L(n) by quadrature of the Bessel form    App. A, Eq. lgf_lap
+  lgf_asym           far-field expansion of G_L                  Sec. 2.2 / App. A footnote
+  lgf_table          G_L over sorted offsets up to R             App. A (look-up table)
+  poisson_direct     u = dx^2 sum_m G_L(n-m) f(m)                Sec. 2.2, Eq. dpoisson_conv
+  intfactor_weights  e^{-2a} I_n(2a), n = 0..nmax                App. A, Eq. lgf_intfac
+  intfactor_box      u = E(alpha) f on a dense box (untruncated) Sec. 2.3 footnote
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lgf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (gcc -O2 -fopenmp).  Returns the library path."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            L.orc_ive_all.argtypes = [ctypes.c_int, ctypes.c_double, _dp]
+            L.orc_gk15_poly.argtypes = [ctypes.c_int, _dp, _dp]
+            L.orc_lgf_quad.argtypes = [ctypes.c_int] * 3
+            L.orc_lgf_quad.restype = ctypes.c_double
+            L.orc_lgf_asym.argtypes = [ctypes.c_int] * 4
+            L.orc_lgf_asym.restype = ctypes.c_double
+            L.orc_table_index.argtypes = [ctypes.c_int] * 3
+            L.orc_table_index.restype = ctypes.c_int64
+            L.orc_table_size.argtypes = [ctypes.c_int]
+            L.orc_table_size.restype = ctypes.c_int64
+            L.orc_lgf_table.argtypes = [ctypes.c_int, _dp]
+            L.orc_lgf.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_lgf.restype = ctypes.c_double
+            L.orc_poisson_direct.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_int64, _ip,
+                                             ctypes.c_double, _dp, ctypes.c_int, _dp]
+            L.orc_intfactor_weights.argtypes = [ctypes.c_double, ctypes.c_int, _dp]
+            L.orc_intfactor_box.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+            L.orc_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def ive_all(nmax: int, z: float) -> np.ndarray:
+    out = np.empty(nmax + 1)
+    if lib().orc_ive_all(int(nmax), float(z), _p(out)) != 0:
+        raise ValueError("bad arguments")
+    return out
+
+
+def gk15_poly(k: int):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().orc_gk15_poly(int(k), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def lgf_quad(n1: int, n2: int, n3: int) -> float:
+    return float(lib().orc_lgf_quad(int(n1), int(n2), int(n3)))
+
+
+def lgf_asym(n1: int, n2: int, n3: int, order: int = 7) -> float:
+    return float(lib().orc_lgf_asym(int(n1), int(n2), int(n3), int(order)))
+
+
+def table_index(a: int, b: int, c: int) -> int:
+    return int(lib().orc_table_index(a, b, c))
+
+
+_table_cache: dict[int, np.ndarray] = {}
+
+
+def lgf_table(R: int) -> np.ndarray:
+    """G_L over sorted offsets a >= b >= c >= 0, a <= R (cached per process)."""
+    R = int(R)
+    if R not in _table_cache:
+        n = int(lib().orc_table_size(R))
+        out = np.empty(n)
+        if lib().orc_lgf_table(R, _p(out)) != 0:
+            raise RuntimeError("orc_lgf_table failed")
+        _table_cache[R] = out
+    return _table_cache[R]
+
+
+def lgf(n, R: int = 32) -> np.ndarray:
+    """G_L at integer offsets n (shape [..., 3]); table up to R, expansion beyond."""
+    n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
+    tab = lgf_table(R)
+    L = lib()
+    out = np.array([L.orc_lgf(_p(tab), R, int(a), int(b), int(c)) for a, b, c in n])
+    return out
+
+
+def poisson_direct(b: int, src_coords, f, tgt_pts, dx: float = 1.0, R: int = 32) -> np.ndarray:
+    """u(t) = dx^2 sum_{m in src blocks} G_L(t - m) f(m) at lattice points tgt_pts [n][3].
+
+    f: [nsrc][b^3] (x fastest inside a block), float64."""
+    src = np.ascontiguousarray(src_coords, dtype=np.int32).reshape(-1, 3)
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(src.shape[0], b ** 3)
+    tp = np.ascontiguousarray(tgt_pts, dtype=np.int32).reshape(-1, 3)
+    tab = lgf_table(R)
+    out = np.empty(tp.shape[0])
+    rc = lib().orc_poisson_direct(int(b), src.shape[0], _p(src, _ip), _p(f), tp.shape[0], _p(tp, _ip),
+                                  float(dx), _p(tab), int(R), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_poisson_direct failed ({rc})")
+    return out
+
+
+def intfactor_weights(alpha: float, nmax: int) -> np.ndarray:
+    out = np.empty(nmax + 1)
+    if lib().orc_intfactor_weights(float(alpha), int(nmax), _p(out)) != 0:
+        raise ValueError("bad arguments")
+    return out
+
+
+def intfactor_box(alpha: float, f_box: np.ndarray) -> np.ndarray:
+    """u = E(alpha) f on a dense box f_box[z, y, x]; every offset inside the box kept."""
+    f = np.ascontiguousarray(f_box, dtype=np.float64)
+    nz, ny, nx = f.shape
+    u = np.empty_like(f)
+    if lib().orc_intfactor_box(float(alpha), nx, ny, nz, _p(f), _p(u)) != 0:
+        raise RuntimeError("orc_intfactor_box failed")
+    return u
+
+
+# ----------------------------------------------------------------------------
+# Block-set helpers (pure data movement between block layout and dense boxes).
+# ----------------------------------------------------------------------------
+def blocks_to_box(b: int, coords, vals, lo=None, shape=None):
+    """Scatter block-layout values [nblk][b^3] into a dense box [z, y, x]."""
+    coords = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
+    if lo is None:
+        lo = coords.min(axis=0)
+    if shape is None:
+        hi = coords.max(axis=0) + 1
+        shape = tuple(int(v) for v in ((hi - lo) * b)[::-1])
+    box = np.zeros(shape)
+    v = np.asarray(vals, dtype=np.float64).reshape(-1, b, b, b)
+    for i, (cx, cy, cz) in enumerate(coords - lo):
+        box[cz * b:(cz + 1) * b, cy * b:(cy + 1) * b, cx * b:(cx + 1) * b] = v[i]
+    return box, lo
+
+
+def box_to_blocks(b: int, coords, box, lo):
+    coords = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
+    out = np.empty((coords.shape[0], b, b, b))
+    for i, (cx, cy, cz) in enumerate(coords - np.asarray(lo)):
+        out[i] = box[cz * b:(cz + 1) * b, cy * b:(cy + 1) * b, cx * b:(cx + 1) * b]
+    return out.reshape(coords.shape[0], b ** 3)
+
+
+def intfactor_blocks(alpha: float, b: int, src_coords, f, tgt_coords) -> np.ndarray:
+    """u = E(alpha) f restricted to the target blocks; f is zero outside src blocks."""
+    src = np.asarray(src_coords).reshape(-1, 3)
+    tgt = np.asarray(tgt_coords).reshape(-1, 3)
+    allc = np.concatenate([src, tgt])
+    lo = allc.min(axis=0)
+    hi = allc.max(axis=0) + 1
+    shape = tuple(int(v) for v in ((hi - lo) * b)[::-1])
+    box, _ = blocks_to_box(b, src, f, lo, shape)
+    u = intfactor_box(alpha, box)
+    return box_to_blocks(b, tgt, u, lo)
+
+
+def block_points(b: int, coords) -> np.ndarray:
+    """All lattice points of the blocks, in block layout order: [nblk*b^3][3] (x, y, z)."""
+    coords = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
+    r = np.arange(b)
+    z, y, x = np.meshgrid(r, r, r, indexing="ij")
+    loc = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+    return (coords[:, None, :] * b + loc[None, :, :]).reshape(-1, 3)

@@ -1,0 +1,283 @@
+"""Pins of the CPU oracle to facts that do not come from the oracle itself.
+
+Every check here ties an oracle function to a closed form, a library routine
+(scipy), a value cited in tests/golden/pins.json, an invariant of the
+mathematics, or an independent numerical route (time stepping), so that a
+dropped term, a wrong sign, a wrong index or a wrong constant fails a test.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "pins.json")))
+
+
+# ---------------------------------------------------------------- quadrature
+def test_gauss_kronrod_rule_exactness(oracle):
+    # K15 integrates polynomials of degree <= 22 exactly, G7 of degree <= 13.
+    for k in range(0, 23):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        k15, g7 = oracle.gk15_poly(k)
+        assert abs(k15 - exact) < 1e-15, k
+        if k <= 13:
+            assert abs(g7 - exact) < 1e-15, k
+    # and G7 is not exact at degree 14 (it is a 7-point rule)
+    _, g7 = oracle.gk15_poly(14)
+    assert abs(g7 - 2.0 / 15) > 1e-8
+
+
+# ------------------------------------------------------------------- Bessel
+@pytest.mark.parametrize("z", [1e-6, 0.1, 0.5, 2.0, 4.0, 17.3, 100.0, 2500.0, 1e5])
+def test_scaled_bessel_vs_scipy(oracle, z):
+    from scipy.special import ive
+    n = np.arange(0, 41)
+    ref = ive(n, z)
+    got = oracle.ive_all(40, z)
+    big = ref > 1e-290
+    assert np.allclose(got[big], ref[big], rtol=2e-13, atol=0)
+
+
+def test_scaled_bessel_zero_argument(oracle):
+    got = oracle.ive_all(5, 0.0)
+    assert got[0] == 1.0 and np.all(got[1:] == 0.0)
+
+
+# ------------------------------------------------------------ G_L quadrature
+def test_lgf_origin_watson(oracle):
+    pin = GOLD["lgf_origin"]["value"]
+    assert abs(oracle.lgf_quad(0, 0, 0) - pin) < 2e-15
+
+
+def test_lgf_neighbour_closed_form(oracle):
+    g0 = oracle.lgf_quad(0, 0, 0)
+    for n in [(1, 0, 0), (0, -1, 0), (0, 0, 1)]:
+        assert abs(oracle.lgf_quad(*n) - g0 - GOLD["lgf_neighbour_minus_origin"]["value"]) < 2e-15
+
+
+def test_lgf_symmetry_of_quadrature(oracle):
+    ref = oracle.lgf_quad(5, 3, 1)
+    for n in [(3, 5, 1), (1, 3, 5), (-5, 3, -1), (3, -1, -5)]:
+        assert abs(oracle.lgf_quad(*n) - ref) < 1e-16
+
+
+def test_lgf_table_satisfies_lattice_poisson(oracle):
+    """L G_L = delta at every point of a cube (the defining equation, Eq. dpoisson)."""
+    R = 14
+    tab = oracle.lgf_table(R + 1)
+
+    def G(a, b, c):
+        a, b, c = sorted((abs(a), abs(b), abs(c)), reverse=True)
+        return tab[oracle.table_index(a, b, c)]
+
+    worst = 0.0
+    for a in range(0, R + 1):
+        for b in range(0, a + 1):
+            for c in range(0, b + 1):
+                lap = (G(a + 1, b, c) + G(a - 1, b, c) + G(a, b + 1, c) + G(a, b - 1, c)
+                       + G(a, b, c + 1) + G(a, b, c - 1) - 6.0 * G(a, b, c))
+                worst = max(worst, abs(lap - (1.0 if a == b == c == 0 else 0.0)))
+    assert worst < 1e-13
+
+
+def test_lgf_table_matches_pointwise_quadrature(oracle):
+    tab = oracle.lgf_table(6)
+    for n in [(0, 0, 0), (6, 0, 0), (4, 3, 2), (6, 6, 6)]:
+        assert tab[oracle.table_index(*n)] == oracle.lgf_quad(*n)
+
+
+# -------------------------------------------------------- far-field expansion
+@pytest.mark.parametrize("n", [(16, 0, 0), (24, 0, 0), (32, 0, 0), (40, 0, 0), (20, 11, 5), (17, 17, 17),
+                               (30, 9, 2), (24, 24, 0), (36, 20, 8)])
+def test_asymptotic_matches_quadrature(oracle, n):
+    """Each added term reduces the error, and the order-7 error falls like r^-8."""
+    q = oracle.lgf_quad(*n)
+    r = math.sqrt(sum(v * v for v in n))
+    errs = [abs(oracle.lgf_asym(*n, order=o) - q) / abs(q) for o in (1, 3, 5, 7)]
+    assert errs[0] > errs[1] > errs[3]
+    assert errs[2] > errs[3]
+    assert errs[3] < 120.0 / r ** 8
+
+
+def test_far_field_leading_term(oracle):
+    lead = GOLD["far_field_leading_term"]["value"]
+    vals = [abs(oracle.lgf_quad(k, 0, 0) * k - lead) for k in (8, 16, 32)]
+    # converges to -1/(4 pi) like 1/r^2 (first correction 1/(16 pi r^3) on an axis)
+    assert vals[0] > vals[1] > vals[2]
+    assert vals[2] < 1e-4
+    assert oracle.lgf_quad(32, 0, 0) < 0.0
+
+
+def test_lgf_lookup_switches_to_expansion(oracle):
+    R = 10
+    tab = oracle.lgf_table(R)
+    assert oracle.lgf([(10, 3, 1)], R)[0] == tab[oracle.table_index(10, 3, 1)]
+    assert oracle.lgf([(11, 3, 1)], R)[0] == oracle.lgf_asym(11, 3, 1, 7)
+
+
+# ---------------------------------------------------------- Poisson direct sum
+def test_poisson_direct_point_source_reproduces_table(oracle):
+    b = 4
+    f = np.zeros((1, b ** 3))
+    f[0, (1 * b + 2) * b + 3] = 1.0                 # point (3, 2, 1) of block (0, 0, 0)
+    tgt = np.array([[3, 2, 1], [9, -4, 7], [40, 1, 1], [3, 2, 2]])
+    u = oracle.poisson_direct(b, [[0, 0, 0]], f, tgt, dx=1.0, R=16)
+    for (x, y, z), v in zip(tgt, u):
+        assert v == oracle.lgf([(x - 3, y - 2, z - 1)], 16)[0]
+    u2 = oracle.poisson_direct(b, [[0, 0, 0]], f, tgt, dx=0.5, R=16)
+    assert np.allclose(u2, 0.25 * u, rtol=0, atol=1e-18)
+
+
+def test_poisson_direct_solves_lattice_poisson(oracle):
+    """u = G_L * f satisfies L u = f at every lattice point (Eq. dpoisson)."""
+    rng = np.random.default_rng(11)
+    b = 4
+    src = np.array([[0, 0, 0], [1, 0, 0]])
+    f = rng.uniform(-1, 1, size=(2, b ** 3))
+    pts = []
+    for x in range(-2, 10):
+        for y in range(-2, 6):
+            for z in range(-2, 6):
+                pts.append((x, y, z))
+    pts = np.array(pts)
+    u = oracle.poisson_direct(b, src, f, pts, R=16)
+    U = {tuple(p): v for p, v in zip(pts.tolist(), u)}
+    F = {}
+    for s, (cx, cy, cz) in enumerate(src):
+        for z in range(b):
+            for y in range(b):
+                for x in range(b):
+                    F[(cx * b + x, cy * b + y, cz * b + z)] = f[s, (z * b + y) * b + x]
+    worst = 0.0
+    for (x, y, z) in U:
+        nb = [(x + 1, y, z), (x - 1, y, z), (x, y + 1, z), (x, y - 1, z), (x, y, z + 1), (x, y, z - 1)]
+        if not all(q in U for q in nb):
+            continue
+        lap = sum(U[q] for q in nb) - 6 * U[(x, y, z)]
+        worst = max(worst, abs(lap - F.get((x, y, z), 0.0)))
+    assert worst < 1e-12
+
+
+def test_poisson_direct_linear_and_translation_invariant(oracle):
+    rng = np.random.default_rng(5)
+    b = 4
+    f1 = rng.uniform(-1, 1, size=(1, b ** 3))
+    f2 = rng.uniform(-1, 1, size=(1, b ** 3))
+    tgt = np.array([[1, 2, 3], [7, -3, 0], [20, 20, 20]])
+    u1 = oracle.poisson_direct(b, [[0, 0, 0]], f1, tgt)
+    u2 = oracle.poisson_direct(b, [[0, 0, 0]], f2, tgt)
+    u12 = oracle.poisson_direct(b, [[0, 0, 0]], 2 * f1 - f2, tgt)
+    assert np.allclose(u12, 2 * u1 - u2, rtol=1e-13, atol=1e-15)
+    ushift = oracle.poisson_direct(b, [[1, -1, 2]], f1, tgt + np.array([4, -4, 8]))
+    assert np.allclose(ushift, u1, rtol=1e-14, atol=1e-16)
+
+
+# --------------------------------------------------------- integrating factor
+@pytest.mark.parametrize("alpha", [0.0, 0.05, 0.1, 0.25, 0.5, 1.0, 2.0])
+def test_intfactor_weights_are_skellam(oracle, alpha):
+    """e^{-2a} I_n(2a) is the Skellam(a, a) pmf: total mass 1, variance 2a."""
+    w = oracle.intfactor_weights(alpha, 80)
+    n = np.arange(81)
+    assert abs(w[0] + 2 * w[1:].sum() - 1.0) < 1e-14
+    assert abs(2 * (n[1:] ** 2 * w[1:]).sum() - 2 * alpha) < 1e-13
+    if alpha == 0.0:
+        assert w[0] == 1.0 and np.all(w[1:] == 0.0)
+
+
+@pytest.mark.parametrize("a,b", [(0.1, 0.25), (0.5, 0.5), (1.0, 0.05)])
+def test_intfactor_semigroup(oracle, a, b):
+    """E(a) E(b) = E(a + b): the 1-D factors convolve to the factor of a + b."""
+    N = 60
+    wa = oracle.intfactor_weights(a, N)
+    wb = oracle.intfactor_weights(b, N)
+    wab = oracle.intfactor_weights(a + b, N)
+    fa = np.concatenate([wa[:0:-1], wa])
+    fb = np.concatenate([wb[:0:-1], wb])
+    c = np.convolve(fa, fb)
+    mid = len(c) // 2
+    assert np.allclose(c[mid:mid + 30], wab[:30], rtol=1e-13, atol=4e-16)
+
+
+def test_intfactor_decay_bound_from_paper(oracle):
+    bound = GOLD["intfactor_decay_bound"]["value"]
+    for alpha in np.linspace(0.0, 1.0, 11):
+        w = oracle.intfactor_weights(alpha, 20)
+        worst = 0.0
+        for a in range(0, 15):
+            for b in range(0, a + 1):
+                for c in range(0, b + 1):
+                    if a * a + b * b + c * c <= 100:
+                        continue
+                    worst = max(worst, w[a] * w[b] * w[c] / w[0] ** 3)
+        assert worst < bound
+
+
+def test_intfactor_apply_matches_heat_equation(oracle):
+    """E(alpha) f equals the solution of dh/dt = L h after time alpha (Sec. 2.3
+    footnote), here by classical RK4 with small steps on a padded box."""
+    rng = np.random.default_rng(7)
+    alpha, n, pad = 0.5, 6, 14
+    N = n + 2 * pad
+    f = np.zeros((N, N, N))
+    f[pad:pad + n, pad:pad + n, pad:pad + n] = rng.uniform(-1, 1, size=(n, n, n))
+
+    def L(h):
+        out = -6.0 * h
+        for ax in range(3):
+            out += np.roll(h, 1, ax) + np.roll(h, -1, ax)
+        return out
+
+    h = f.copy()
+    steps = 500
+    dt = alpha / steps
+    for _ in range(steps):
+        k1 = L(h)
+        k2 = L(h + 0.5 * dt * k1)
+        k3 = L(h + 0.5 * dt * k2)
+        k4 = L(h + dt * k3)
+        h = h + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    u = oracle.intfactor_box(alpha, f)
+    assert np.max(np.abs(u - h)) < 1e-10
+
+
+def test_intfactor_blocks_point_source(oracle):
+    b = 4
+    f = np.zeros((1, b ** 3))
+    f[0, (2 * b + 1) * b + 0] = 1.0                 # point (0, 1, 2)
+    tgt = np.array([[0, 0, 0], [1, 0, 0], [-1, 1, 0]])
+    u = oracle.intfactor_blocks(0.3, b, [[0, 0, 0]], f, tgt).reshape(3, b, b, b)
+    w = oracle.intfactor_weights(0.3, 20)
+    for ti, (cx, cy, cz) in enumerate(tgt):
+        for z in range(b):
+            for y in range(b):
+                for x in range(b):
+                    X, Y, Z = cx * b + x, cy * b + y, cz * b + z
+                    ref = w[abs(X - 0)] * w[abs(Y - 1)] * w[abs(Z - 2)]
+                    assert abs(u[ti, z, y, x] - ref) <= 2e-15 * ref + 1e-300
+
+
+# -------------------------------------------------------- input generators
+def test_delta_kernel_partition_of_unity():
+    import lgf_inputs as li
+    for x in np.linspace(-0.5, 0.5, 23):
+        j = np.arange(-3, 4)
+        phi = li.delta3(x - j)
+        assert abs(phi.sum() - 1.0) < 1e-14
+        assert abs((phi * (x - j)).sum()) < 1e-14          # first moment vanishes
+
+
+def test_icosphere_marker_counts():
+    import lgf_inputs as li
+    for lev in (1, 2, 3, 4):
+        X = li.icosphere_markers(lev)
+        assert X.shape[0] == 20 * 4 ** (lev - 1)
+        assert np.allclose(np.linalg.norm(X, axis=1), 1.0)
+
+
+def test_plate_marker_spacing():
+    import lgf_inputs as li
+    X = li.plate_markers(40.0, 80.0, 1.05, 30.0)
+    d = np.linalg.norm(X[1] - X[0])
+    assert 1.0 < d < 1.1
