@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the LGF Poisson apply (+ integrating factors) on one GB300.
+
+Workload (default "dense128"): the dense 128^3 lattice box of Liska &
+Colonius-style smooth sources (8 Gaussian blobs, sigma = 6 cells, seed 1), FP32,
+32^3 blocks.  One step = one lgf_batch_apply call (one CUDA graph) holding the
+whole hot path for that input: the G_L Poisson apply u = G_L * f and the
+integrating factors E(0.05) f, E(0.5) f, E(2.0) f.  The metric counts the
+Poisson apply's active target lattice points (2,097,152 per step) over the
+whole step's time, so the integrating factors only lower the reported value.
+The kernel spectra and the G_L table are pre-processing (built before timing,
+once per simulation as in App. A).
+
+Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
+on the launch stream, with a 512 MiB buffer written between steps (L2 flush,
+the 8 MiB input is smaller than L2); barrier + synchronize around the timed
+region; max over ranks.  Multi-GPU runs (torchrun) are independent replicas
+(the problem does not shard): value = ranks x points / max time.
+
+Other JSON keys: roofline of the dominant kernel (algorithmic bytes per
+launch / CUDA-event launch time, against MEASURED_PEAKS.json), e2e (the same
+metric with the host->device copy of f from pinned memory and the
+device->host copy of all outputs inside the timed region), cpu_baseline (the
+CPU oracle on a bounded sample, with its error against the GPU result) and the
+SM clocks sampled during the timed region.
+
+`--impl reference` times the CPU oracle (direct summation) as the reference
+arm on the same workload, one bounded sample of target points per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ----------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world: int, backend: str):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend)
+    return dist if world > 1 else None
+
+
+def reduce_max(value: float, dist) -> float:
+    """Largest value over ranks (the slowest replica sets the job time)."""
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if (torch.cuda.is_available() and dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_step: float, ms_per_step_max: float, world: int) -> float:
+    """Whole-job points per second: every replica processes the same work."""
+    return world * points_per_step / (ms_per_step_max * 1e-3)
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+ALPHAS = (0.05, 0.5, 2.0)
+
+
+def make_workload(name: str):
+    import lgf_inputs as li
+    if name == "dense128":
+        p = li.dense_blobs(n=128, b=32, seed=1)
+        desc = {"workload": "dense 128^3 box, 8 Gaussian blobs (sigma 6, seed 1), 32^3 blocks, FP32; "
+                            "G_L apply + E(0.05), E(0.5), E(2.0) per step",
+                "lattice": [128, 128, 128], "block": 32, "blocks": int(p.src.shape[0]), "fields": 1,
+                "alphas": list(ALPHAS)}
+        return p, desc
+    raise ValueError(f"unknown workload {name}")
+
+
+def geometry(p):
+    """Transform-box geometry of the Poisson plan (mirrors the library's plan)."""
+    b = p.b
+    allc = np.concatenate([p.src, p.tgt])
+    lo, hi = allc.min(0), allc.max(0)
+    L = (hi - lo + 1) * b
+    M = [32 * 2 ** max(0, math.ceil(math.log2(max(1, 2 * l - 1) / 32))) for l in L]
+    Ls = (p.src.max(0) - p.src.min(0) + 1) * b
+    Lt = (p.tgt.max(0) - p.tgt.min(0) + 1) * b
+    return M, Ls, Lt
+
+
+def algorithmic_bytes(p, nfields: int) -> dict:
+    """Compulsory HBM bytes per launch of each kernel (FP32): every input
+    element read once, every output element written once."""
+    M, Ls, Lt = geometry(p)
+    K = M[0] // 2 + 1
+    c8 = 8  # complex64
+    b3 = p.b ** 3
+    nsrc, ntgt = p.src.shape[0], p.tgt.shape[0]
+    spec = (M[2] // 2 + 1) * (M[1] // 2 + 1) * K * 4
+    by = {
+        "poisson_x_forward": nfields * (nsrc * b3 * 4 + Ls[2] * Ls[1] * K * c8),
+        "poisson_y_forward": nfields * (Ls[2] * Ls[1] * K * c8 + Ls[2] * M[1] * K * c8),
+        "poisson_z_convolve": nfields * (Ls[2] * M[1] * K * c8 + Lt[2] * M[1] * K * c8) + spec,
+        "poisson_y_inverse": nfields * (Lt[2] * M[1] * K * c8 + Lt[2] * Lt[1] * K * c8),
+        "poisson_x_inverse": nfields * (Lt[2] * Lt[1] * K * c8 + ntgt * b3 * 4),
+    }
+    # integrating-factor passes on a dense box: every pass reads and writes the box once
+    for ax in "xyz":
+        by[f"intfactor_pass_{ax}"] = nfields * 2 * ntgt * b3 * 4
+    return by
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1604_01814_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else float(k["dram_bytes_per_launch"])
+
+
+def measured_peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(p, npts: int, seed: int = 101):
+    from oracle import oracle
+    rng = np.random.default_rng(seed)
+    ntot = p.tgt.shape[0] * p.b ** 3
+    idx = np.sort(rng.choice(ntot, size=npts, replace=False))
+    pts = oracle.block_points(p.b, p.tgt)[idx]
+    oracle.lgf_table(64)   # table build is pre-processing, outside the timing
+    t0 = time.perf_counter()
+    ref = oracle.poisson_direct(p.b, p.src, p.f[0, 0], pts, R=64)
+    dt = time.perf_counter() - t0
+    return idx, ref, dt, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    p, desc = make_workload(args.workload)
+    npts = args.ref_points
+    times = []
+    for k in range(args.warmup + args.steps):
+        _, _, dt, cores = oracle_sample(p, npts, seed=1000 + k)
+        if k >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    value = npts / (ms * 1e-3)
+    sample = f"{npts} random target points of the Poisson apply per step (direct summation over all sources)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+METRIC = "active lattice points/sec for LGF Poisson apply at rel err 1e-5; % HBM roofline"
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_1604_01814_gb300 as lgf
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    p, desc = make_workload(args.workload)
+    ctx = lgf.Context("f32", device=dev.index)
+    ctx.table_build(48)
+    f_host = torch.tensor(p.f.reshape(-1), dtype=torch.float32).pin_memory()
+    f = f_host.to(dev)
+    n_out = p.tgt.shape[0] * p.b ** 3
+    u = torch.empty(n_out, dtype=torch.float32, device=dev)
+    vs = [torch.empty(n_out, dtype=torch.float32, device=dev) for _ in ALPHAS]
+    batch = [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, op=lgf.LGF_OP_POISSON, dx=1.0)]
+    batch += [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=v, op=lgf.LGF_OP_INTFACTOR, alpha=a)
+              for a, v in zip(ALPHAS, vs)]
+    s = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    points = float(n_out)   # Poisson target points per step (one field)
+
+    with torch.cuda.stream(s):
+        for _ in range(max(3, args.warmup)):
+            ctx.batch_apply(batch, stream=s)
+    s.synchronize()
+
+    # ---- timed region (device time, CUDA events on the launch stream) ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(s):
+        for a, b in evs:
+            flush.zero_()
+            a.record(s)
+            ctx.batch_apply(batch, stream=s)
+            b.record(s)
+    s.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms_local = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    ms = reduce_max(ms_local, dist)
+    value = job_throughput(points, ms, world)
+
+    # ---- per-kernel times (events around every launch, direct launches) ----
+    ctx.profile_enable(True)
+    with torch.cuda.stream(s):
+        for _ in range(args.steps):
+            flush.zero_()
+            ctx.batch_apply(batch, stream=s)
+    stats = ctx.profile_read()
+    ctx.profile_enable(False)
+    launches_per_step = sum(n for n, _ in stats.values()) / args.steps
+    alg = algorithmic_bytes(p, 1)
+    dom = max(stats, key=lambda k: stats[k][1])
+    dom_ms = stats[dom][1] / stats[dom][0]
+    peak, peak_kind = measured_peaks()
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    kernels = {k: {"launches_per_step": n / args.steps, "ms_per_launch": t / n,
+                   "share": t / sum(v[1] for v in stats.values()),
+                   "alg_GBps": (alg[k] / (t / n * 1e-3) / 1e9) if k in alg else None}
+               for k, (n, t) in stats.items()}
+
+    # ---- end to end: pinned host input -> apply -> outputs back to host ----
+    outs_host = [torch.empty(n_out, dtype=torch.float32).pin_memory() for _ in range(1 + len(ALPHAS))]
+    e2e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            f.copy_(f_host, non_blocking=True)
+            ctx.batch_apply(batch, stream=s)
+            for o, d in zip(outs_host, [u] + vs):
+                o.copy_(d, non_blocking=True)
+        s.synchronize()
+        for a, b in e2e_evs:
+            flush.zero_()
+            a.record(s)
+            f.copy_(f_host, non_blocking=True)
+            ctx.batch_apply(batch, stream=s)
+            for o, d in zip(outs_host, [u] + vs):
+                o.copy_(d, non_blocking=True)
+            b.record(s)
+    s.synchronize()
+    e2e_ms = reduce_max(float(np.mean([a.elapsed_time(b) for a, b in e2e_evs])), dist)
+    e2e = {"value": job_throughput(points, e2e_ms, world), "unit": "points/s",
+           "h2d_bytes_per_step": int(f.numel() * 4), "d2h_bytes_per_step": int(n_out * 4 * (1 + len(ALPHAS))),
+           "ms_per_step": e2e_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(desc, l2="flushed between timed steps (512 MiB write); input 8 MiB < L2",
+                           parallelism="replicas" if world > 1 else "single GPU",
+                           kernels=kernels),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": alg[dom], "ms_per_launch": dom_ms,
+                         "traffic": load_traffic(dom)},
+            "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clocks}
+    # ---- CPU baseline: the oracle on a bounded sample, and the GPU error there ----
+    if rank == 0 and not args.no_cpu:
+        idx, ref, dt, cores = oracle_sample(p, args.cpu_points)
+        got = u.cpu().numpy().astype(np.float64)[idx]
+        err = float(np.abs(got - ref).max() / np.abs(ref).max())
+        line["cpu_baseline"] = {"value": args.cpu_points / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_points} random target points of the Poisson apply "
+                                          f"(direct summation over all 2^21 sources), {dt:.1f} s"}
+        line["rel_err_vs_oracle"] = err
+    ctx.close()
+    return line
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense128")
+    ap.add_argument("--cpu-points", type=int, default=4096)
+    ap.add_argument("--ref-points", type=int, default=1024)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, _ = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        import torch
+        dist = dist_init(world, "nccl" if torch.cuda.is_available() else "gloo")
+        line = run_ours(args, rank, world, dist)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

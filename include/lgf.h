@@ -1,0 +1,215 @@
+/*
+ * lgf.h -- C ABI of the GB300 lattice-Green's-function library.
+ *
+ * Operations (Liska & Colonius, "A fast immersed boundary method for external
+ * incompressible viscous flows using lattice Green's functions",
+ * arXiv:1604.01814):
+ *
+ *   Poisson apply   u(n) = dx^2 * sum_{m in D} G_L(n - m) f(m)
+ *                   -- the solution of the discrete 7-point Poisson problem
+ *                   L u = f with supp(f) in D, evaluated as the lattice
+ *                   convolution of Sec. 2.2, Eq. dpoisson / dpoisson_conv.
+ *                   G_L is the LGF of the 7-point Laplacian, App. A, Eq. lgf_lap:
+ *                   G_L(n) = -int_0^inf prod_i e^{-2t} I_{|n_i|}(2t) dt.
+ *   Integrating     u(n) = sum_m E_alpha(n - m) f(m),
+ *   factor          E_alpha(n) = prod_i e^{-2 alpha} I_{|n_i|}(2 alpha)
+ *                   -- the solution operator exp(alpha L) of the discrete heat
+ *                   equation (Sec. 2.3 footnote; App. A, Eq. lgf_intfac).
+ *
+ * Sources and targets live on the active blocks of a block-structured lattice
+ * (Sec. 4.1): a block set lists block coordinates B, and block B with edge b
+ * covers the lattice points b*B + [0, b)^3.  Sources outside the source block
+ * set are exactly zero (the truncation of Table 1); results are produced on
+ * the target block set only.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an lgf_status; nothing aborts.  On failure the
+ *     context keeps a message readable with lgf_last_error().  Calls on one
+ *     context are not thread safe (use one context per host thread).
+ *   - Field layout: [nrhs][ncomp][nblocks][b^3], x fastest inside a block
+ *     (index ((r*ncomp + c)*nblocks + k)*b^3 + (z*b + y)*b + x).  The element
+ *     type is float for LGF_F32 contexts and double for LGF_F64 contexts.
+ *   - Device pointers must stay valid until the stream reaches the work.  The
+ *     caller owns every buffer it passes; the library owns its context memory
+ *     (tables, spectra, plans, scratch) and frees it in lgf_ctx_destroy().
+ *   - Block lists are host arrays; they are read during the call and copied
+ *     into cached plans, so the caller may free them when the call returns.
+ *   - Outputs are overwritten, never accumulated.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued asynchronously on it.
+ */
+#ifndef LGF_H
+#define LGF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LGF_API __attribute__((visibility("default")))
+#else
+#define LGF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lgf_ctx lgf_ctx;
+
+typedef enum {
+    LGF_OK = 0,
+    LGF_EINVAL = 1,        /* bad argument: null pointer, size, duplicate block, ... */
+    LGF_ENOMEM = 2,        /* device or host allocation failed */
+    LGF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    LGF_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
+    LGF_EUNSUPPORTED = 5,  /* a size beyond the library's limits */
+    LGF_ENOTABLE = 6       /* lgf_table_build has not covered the offsets needed */
+} lgf_status;
+
+typedef enum { LGF_F32 = 0, LGF_F64 = 1 } lgf_prec;
+
+/* A block set: `nblocks` distinct block coordinates (x, y, z), host memory. */
+typedef struct {
+    int32_t b;               /* block edge in lattice points: 4, 8, 16, 32 or 64 */
+    int32_t nblocks;         /* >= 0 */
+    const int32_t *coords;   /* [nblocks][3], host pointer */
+} lgf_blockset;
+
+/* Context options.  Zero fields take the defaults noted. */
+typedef struct {
+    double tol;              /* target relative accuracy; default 1e-7 (F32), 1e-13 (F64).
+                                Sets the E_alpha truncation radius. */
+    int32_t prec;            /* lgf_prec of every field passed to this context */
+    int32_t table_radius;    /* G_L by quadrature for max|n_i| <= table_radius, by the
+                                far-field expansion beyond; default 48, range 8..96 */
+    int32_t stencil_radius;  /* fixed E_alpha truncation radius; 0 = from tol */
+    int32_t device;          /* CUDA device ordinal used by this context */
+    int32_t reserved[4];     /* must be zero */
+} lgf_options;
+
+/* Create a context on opt->device (NULL opt = defaults, device 0).
+   Errors: LGF_EINVAL (bad option), LGF_ECUDA, LGF_ENOMEM. */
+LGF_API lgf_status lgf_ctx_create(lgf_ctx **out, const lgf_options *opt);
+
+/* Free every resource of the context (synchronises the device first). */
+LGF_API lgf_status lgf_ctx_destroy(lgf_ctx *ctx);
+
+/* Build the FP64 G_L table on the GPU: quadrature of the Bessel form of
+   App. A, Eq. lgf_lap, for sorted offsets |n1| >= |n2| >= |n3| up to
+   table_radius, with the far-field expansion -1/(4 pi |n|) + O(|n|^-3)
+   (Sec. 2.2 and App. A footnote) beyond.  The table is computed once per
+   context, a pre-processing step as in App. A.  `max_offset` (>= 0) is the
+   largest per-axis lattice offset the caller expects; the quadrature radius
+   is min(table_radius, max(max_offset, 24)), since the expansion is accurate
+   to 1e-9 relative beyond 24.  A later call with a larger max_offset extends
+   the table.  Synchronous with respect to `stream`.
+   Errors: LGF_EINVAL, LGF_ECUDA, LGF_ENOMEM. */
+LGF_API lgf_status lgf_table_build(lgf_ctx *ctx, int32_t max_offset, void *stream);
+
+/* Report the table: quadrature radius and the largest relative mismatch
+   between quadrature and expansion on the shell table_radius-3..table_radius
+   (the near/far matching check).  Either pointer may be NULL.
+   Errors: LGF_ENOTABLE before lgf_table_build. */
+LGF_API lgf_status lgf_table_info(lgf_ctx *ctx, int32_t *table_radius, double *shell_mismatch);
+
+/* G_L at `n` integer offsets: offsets_dev [n][3] int32 (device), out_dev [n]
+   double (device).  Uses the table inside its radius and the expansion
+   outside, exactly as the Poisson apply does.  Errors: LGF_ENOTABLE, LGF_EINVAL. */
+LGF_API lgf_status lgf_table_lookup(lgf_ctx *ctx, const int32_t *offsets_dev, int64_t n, double *out_dev,
+                            void *stream);
+
+/* Poisson apply (Sec. 2.2, Eq. dpoisson_conv):
+     u[r][c][t] = dx^2 * sum_{s in src} G_L(n_t - m_s) f[r][c][s]
+   for every target point n_t of `tgt` and every rhs r < nrhs, component
+   c < ncomp (each component is an independent scalar convolution with the
+   same kernel).  f_dev: [nrhs][ncomp][src.nblocks][b^3]; u_dev:
+   [nrhs][ncomp][tgt.nblocks][b^3].  src.b must equal tgt.b.  The result is
+   the exact convolution up to floating-point rounding (no far-field
+   approximation).  Errors: LGF_EINVAL (null pointers, b mismatch, duplicate
+   blocks, nblocks == 0 is allowed and writes nothing / zeros),
+   LGF_EUNSUPPORTED (extent beyond 2048 lattice points per axis),
+   LGF_ENOTABLE, LGF_ENOMEM, LGF_ECUDA. */
+LGF_API lgf_status lgf_poisson_apply(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt,
+                             const void *f_dev, void *u_dev, int32_t ncomp, int32_t nrhs, double dx,
+                             void *stream);
+
+/* Integrating-factor apply (Sec. 2.3 footnote; App. A, Eq. lgf_intfac):
+     u[r][c][t] = sum_{s in src} E_alpha(n_t - m_s) f[r][c][s],  alpha >= 0,
+   with E_alpha truncated at the radius R where the 1-D factor falls below
+   tol/8 of its central value (or at opt.stencil_radius).  Same layouts as
+   lgf_poisson_apply.  alpha = 0 copies sources onto coinciding targets.
+   Errors: LGF_EINVAL (alpha < 0 or not finite, ...), LGF_EUNSUPPORTED
+   (alpha so large that the radius would exceed 128), LGF_ENOMEM, LGF_ECUDA. */
+LGF_API lgf_status lgf_intfactor_apply(lgf_ctx *ctx, double alpha, const lgf_blockset *src, const lgf_blockset *tgt,
+                               const void *f_dev, void *u_dev, int32_t ncomp, int32_t nrhs, void *stream);
+
+/* The 1-D factor e^{-2 alpha} I_n(2 alpha), n = 0..R, that lgf_intfactor_apply
+   uses (FP64, computed on the GPU by Miller's recurrence); w_dev holds cap
+   doubles; *radius receives R.  Errors: LGF_EINVAL (cap <= R). */
+LGF_API lgf_status lgf_intfactor_weights(lgf_ctx *ctx, double alpha, double *w_dev, int32_t cap, int32_t *radius,
+                                 void *stream);
+
+/* Batched applies.  Operations: */
+enum { LGF_OP_POISSON = 0, LGF_OP_INTFACTOR = 1, LGF_OP_POISSON_THEN_INTFACTOR = 2 };
+
+typedef struct {
+    lgf_blockset src, tgt;   /* as in lgf_poisson_apply; for POISSON_THEN_INTFACTOR
+                                the integrating factor maps tgt -> tgt */
+    const void *f_dev;       /* [nrhs][ncomp][src.nblocks][b^3] */
+    void *u_dev;             /* [nrhs][ncomp][tgt.nblocks][b^3] */
+    int32_t ncomp, nrhs;
+    int32_t op;              /* LGF_OP_* */
+    int32_t reserved;        /* must be zero */
+    double alpha, dx;
+} lgf_problem;
+
+/* Apply `nprob` independent problems (the per-stage right-hand sides of
+   Sec. 2.3 and many uneven block-adaptive problems) as one batch: problems
+   whose padded transform boxes share a shape run in the same launches, and
+   the whole batch is captured once into a CUDA graph that later calls with
+   an identical batch (same block lists, pointers, alphas) replay.  u buffers
+   must not alias f buffers of the same batch.  POISSON_THEN_INTFACTOR writes
+   E_alpha(G_L * f) into u_dev.  Errors: as the single applies. */
+LGF_API lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob, void *stream);
+
+/* FP64 residual check of the discrete Poisson problem (Sec. 2.2, Eq. dpoisson):
+     r = (L_h u)(n) - f(n),  L_h u = (sum_{+-e_i} u(n +- e) - 6 u(n)) / dx^2,
+   at every point of `set` whose six neighbours are in `set`; r = 0 elsewhere.
+   u_dev, f_dev: one field each on `set` in the context precision (f is the
+   source restricted to `set`: zero where the source set has no block);
+   r_dev: [set.nblocks][b^3] double.  *max_abs (host, may be NULL) receives
+   max |r| over the checked points and *max_f the largest |f| (for relative
+   reporting).  Synchronous.  Errors: LGF_EINVAL, LGF_ECUDA, LGF_ENOMEM. */
+LGF_API lgf_status lgf_residual(lgf_ctx *ctx, const lgf_blockset *set, const void *u_dev, const void *f_dev,
+                        double dx, double *r_dev, double *max_abs, double *max_f, void *stream);
+
+/* Per-kernel timing.  While enabled, every kernel the context launches is
+   bracketed by two CUDA events recorded on its launch stream, and
+   lgf_batch_apply runs without a CUDA graph (direct launches).  Enabling or
+   disabling synchronises the device and clears the statistics. */
+LGF_API lgf_status lgf_profile_enable(lgf_ctx *ctx, int32_t enable);
+
+typedef struct {
+    char name[48];           /* kernel role, e.g. "poisson_z_convolve" */
+    int64_t launches;        /* launches since the last read */
+    double total_ms;         /* summed event-to-event time of those launches */
+} lgf_kernel_stat;
+
+/* Synchronise the device, fold the recorded events into per-kernel totals,
+   copy up to `cap` of them into `out` (host), set *n to the number of kernels
+   seen, and reset the totals. */
+LGF_API lgf_status lgf_profile_read(lgf_ctx *ctx, lgf_kernel_stat *out, int32_t cap, int32_t *n);
+
+/* Static text for a status code. */
+LGF_API const char *lgf_status_string(lgf_status s);
+
+/* Message of the last failed call on this context ("" if none). */
+LGF_API const char *lgf_last_error(lgf_ctx *ctx);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+LGF_API int32_t lgf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LGF_H */

@@ -1,0 +1,311 @@
+"""ctypes binding of liblgf.so (include/lgf.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts torch
+tensors and numpy block lists into the plain pointers and sizes of the C ABI
+and turns status codes into exceptions.  There is no fallback: if liblgf.so
+is missing or cannot be loaded, importing the library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblgf.so")
+
+LGF_OK, LGF_EINVAL, LGF_ENOMEM, LGF_ECUDA, LGF_ETIMEOUT, LGF_EUNSUPPORTED, LGF_ENOTABLE = range(7)
+LGF_F32, LGF_F64 = 0, 1
+LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR = 0, 1, 2
+
+# Every symbol include/lgf.h declares (checked by the symbol test).
+EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
+           "lgf_poisson_apply", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
+           "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_status_string", "lgf_last_error",
+           "lgf_version")
+
+
+class lgf_blockset(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("coords", ctypes.POINTER(ctypes.c_int32))]
+
+
+class lgf_options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("prec", ctypes.c_int32), ("table_radius", ctypes.c_int32),
+                ("stencil_radius", ctypes.c_int32), ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class lgf_problem(ctypes.Structure):
+    _fields_ = [("src", lgf_blockset), ("tgt", lgf_blockset), ("f_dev", ctypes.c_void_p), ("u_dev", ctypes.c_void_p),
+                ("ncomp", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("alpha", ctypes.c_double), ("dx", ctypes.c_double)]
+
+
+class lgf_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class LgfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lgf status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblgf.so (raises if it is missing: build it with build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing; build the CUDA library first "
+                          "(python -m paper_1604_01814_gb300.build)")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    bsp = ctypes.POINTER(lgf_blockset)
+    sig = {
+        "lgf_ctx_create": [ctypes.POINTER(vp), ctypes.POINTER(lgf_options)],
+        "lgf_ctx_destroy": [vp],
+        "lgf_table_build": [vp, i32, vp],
+        "lgf_table_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)],
+        "lgf_table_lookup": [vp, vp, i64, vp, vp],
+        "lgf_poisson_apply": [vp, bsp, bsp, vp, vp, i32, i32, dbl, vp],
+        "lgf_intfactor_apply": [vp, dbl, bsp, bsp, vp, vp, i32, i32, vp],
+        "lgf_intfactor_weights": [vp, dbl, vp, i32, ctypes.POINTER(i32), vp],
+        "lgf_batch_apply": [vp, ctypes.POINTER(lgf_problem), i32, vp],
+        "lgf_residual": [vp, bsp, vp, vp, dbl, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
+        "lgf_profile_enable": [vp, i32],
+        "lgf_profile_read": [vp, ctypes.POINTER(lgf_kernel_stat), i32, ctypes.POINTER(i32)],
+        "lgf_status_string": [i32],
+        "lgf_last_error": [vp],
+        "lgf_version": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = i32
+    L.lgf_status_string.restype = ctypes.c_char_p
+    L.lgf_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _blockset(b: int, coords) -> tuple:
+    c = np.ascontiguousarray(np.asarray(coords, dtype=np.int32).reshape(-1, 3))
+    bs = lgf_blockset(int(b), int(c.shape[0]), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return bs, c   # keep the array alive with the struct
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """One lgf_ctx: precision, tolerance, G_L table, plans, spectra, scratch."""
+
+    def __init__(self, prec: str = "f32", tol: float = 0.0, table_radius: int = 0, stencil_radius: int = 0,
+                 device: int = 0):
+        self._L = load()
+        self.prec = {"f32": LGF_F32, "f64": LGF_F64}[prec]
+        opt = lgf_options(float(tol), self.prec, int(table_radius), int(stencil_radius), int(device))
+        h = ctypes.c_void_p()
+        st = self._L.lgf_ctx_create(ctypes.byref(h), ctypes.byref(opt))
+        if st != LGF_OK:
+            raise LgfError(st, "lgf_ctx_create: " + self._L.lgf_status_string(st).decode())
+        self._h = h
+        self.device = device
+
+    # -- helpers -------------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != LGF_OK:
+            msg = self._L.lgf_last_error(self._h).decode()
+            raise LgfError(st, f"{what}: {self._L.lgf_status_string(st).decode()}: {msg}")
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.prec == LGF_F64 else torch.float32
+
+    def _field(self, t, nblk: int, b: int, nf: int, name: str):
+        import torch
+        if t is None:
+            raise ValueError(f"{name} is None")
+        if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of dtype {self.dtype}")
+        if t.numel() != nblk * b ** 3 * nf:
+            raise ValueError(f"{name} has {t.numel()} elements, expected {nblk * b ** 3 * nf}")
+        return t
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lgf_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API -----------------------------------------------------------------
+    def table_build(self, max_offset: int = 48, stream=None):
+        self._check(self._L.lgf_table_build(self._h, int(max_offset), _stream_ptr(stream)), "lgf_table_build")
+
+    def table_info(self):
+        r = ctypes.c_int32()
+        m = ctypes.c_double()
+        self._check(self._L.lgf_table_info(self._h, ctypes.byref(r), ctypes.byref(m)), "lgf_table_info")
+        return r.value, m.value
+
+    def table_lookup(self, offsets, stream=None):
+        import torch
+        off = offsets.to(device=f"cuda:{self.device}", dtype=torch.int32).contiguous()
+        out = torch.empty(off.shape[0], dtype=torch.float64, device=off.device)
+        self._check(self._L.lgf_table_lookup(self._h, off.data_ptr(), off.shape[0], out.data_ptr(),
+                                             _stream_ptr(stream)), "lgf_table_lookup")
+        return out
+
+    def poisson_apply(self, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1, dx: float = 1.0, stream=None):
+        s, sa = _blockset(b, src)
+        t, ta = _blockset(b, tgt)
+        nf = ncomp * nrhs
+        if s.nblocks and t.nblocks:
+            self._field(f, s.nblocks, b, nf, "f")
+        if t.nblocks:
+            self._field(u, t.nblocks, b, nf, "u")
+        self._check(self._L.lgf_poisson_apply(self._h, ctypes.byref(s), ctypes.byref(t), _ptr(f), _ptr(u),
+                                              ncomp, nrhs, float(dx), _stream_ptr(stream)), "lgf_poisson_apply")
+        return u
+
+    def intfactor_apply(self, alpha: float, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1, stream=None):
+        s, sa = _blockset(b, src)
+        t, ta = _blockset(b, tgt)
+        nf = ncomp * nrhs
+        if s.nblocks and t.nblocks:
+            self._field(f, s.nblocks, b, nf, "f")
+        if t.nblocks:
+            self._field(u, t.nblocks, b, nf, "u")
+        self._check(self._L.lgf_intfactor_apply(self._h, float(alpha), ctypes.byref(s), ctypes.byref(t), _ptr(f),
+                                                _ptr(u), ncomp, nrhs, _stream_ptr(stream)), "lgf_intfactor_apply")
+        return u
+
+    def intfactor_weights(self, alpha: float, stream=None):
+        import torch
+        R = ctypes.c_int32()
+        self._check(self._L.lgf_intfactor_weights(self._h, float(alpha), None, 0, ctypes.byref(R),
+                                                  _stream_ptr(stream)), "lgf_intfactor_weights")
+        w = torch.empty(R.value + 1, dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(self._L.lgf_intfactor_weights(self._h, float(alpha), w.data_ptr(), R.value + 1, ctypes.byref(R),
+                                                  _stream_ptr(stream)), "lgf_intfactor_weights")
+        return R.value, w
+
+    def batch_apply(self, problems: Sequence[dict], stream=None):
+        """problems: dicts with b, src, tgt, f, u, ncomp, nrhs, op, alpha, dx."""
+        arr = (lgf_problem * max(1, len(problems)))()
+        keep = []
+        for i, p in enumerate(problems):
+            b = int(p["b"])
+            s, sa = _blockset(b, p["src"])
+            t, ta = _blockset(b, p["tgt"])
+            keep += [sa, ta]
+            nf = int(p.get("ncomp", 1)) * int(p.get("nrhs", 1))
+            if s.nblocks and t.nblocks:
+                self._field(p["f"], s.nblocks, b, nf, f"problem {i} f")
+            if t.nblocks:
+                self._field(p["u"], t.nblocks, b, nf, f"problem {i} u")
+            arr[i] = lgf_problem(s, t, _ptr(p.get("f")), _ptr(p.get("u")), int(p.get("ncomp", 1)),
+                                 int(p.get("nrhs", 1)), int(p.get("op", LGF_OP_POISSON)), 0,
+                                 float(p.get("alpha", 0.0)), float(p.get("dx", 1.0)))
+        self._check(self._L.lgf_batch_apply(self._h, arr, len(problems), _stream_ptr(stream)), "lgf_batch_apply")
+
+    def residual(self, b: int, coords, u, f, dx: float = 1.0, stream=None):
+        import torch
+        c, ca = _blockset(b, coords)
+        self._field(u, c.nblocks, b, 1, "u")
+        self._field(f, c.nblocks, b, 1, "f")
+        r = torch.empty(c.nblocks * b ** 3, dtype=torch.float64, device=u.device)
+        ma, mf = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.lgf_residual(self._h, ctypes.byref(c), u.data_ptr(), f.data_ptr(), float(dx),
+                                         r.data_ptr(), ctypes.byref(ma), ctypes.byref(mf), _stream_ptr(stream)),
+                    "lgf_residual")
+        return r, ma.value, mf.value
+
+
+    def profile_enable(self, enable: bool = True):
+        self._check(self._L.lgf_profile_enable(self._h, 1 if enable else 0), "lgf_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total ms)} since the last read (synchronises)."""
+        arr = (lgf_kernel_stat * 64)()
+        n = ctypes.c_int32()
+        self._check(self._L.lgf_profile_read(self._h, arr, 64, ctypes.byref(n)), "lgf_profile_read")
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+# Module-level names matching the C ABI.
+def lgf_ctx_create(prec: str = "f32", **kw) -> Context:
+    return Context(prec, **kw)
+
+
+def lgf_ctx_destroy(ctx: Context):
+    ctx.close()
+
+
+def lgf_table_build(ctx: Context, max_offset: int = 48, stream=None):
+    return ctx.table_build(max_offset, stream)
+
+
+def lgf_table_info(ctx: Context):
+    return ctx.table_info()
+
+
+def lgf_table_lookup(ctx: Context, offsets, stream=None):
+    return ctx.table_lookup(offsets, stream)
+
+
+def lgf_poisson_apply(ctx: Context, *a, **kw):
+    return ctx.poisson_apply(*a, **kw)
+
+
+def lgf_intfactor_apply(ctx: Context, *a, **kw):
+    return ctx.intfactor_apply(*a, **kw)
+
+
+def lgf_intfactor_weights(ctx: Context, alpha: float, stream=None):
+    return ctx.intfactor_weights(alpha, stream)
+
+
+def lgf_batch_apply(ctx: Context, problems, stream=None):
+    return ctx.batch_apply(problems, stream)
+
+
+def lgf_residual(ctx: Context, *a, **kw):
+    return ctx.residual(*a, **kw)
+
+
+def lgf_profile_enable(ctx: Context, enable: bool = True):
+    return ctx.profile_enable(enable)
+
+
+def lgf_profile_read(ctx: Context) -> dict:
+    return ctx.profile_read()
+
+
+def lgf_status_string(status: int) -> str:
+    return load().lgf_status_string(int(status)).decode()
+
+
+def lgf_version() -> int:
+    return int(load().lgf_version())

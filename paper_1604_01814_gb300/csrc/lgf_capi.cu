@@ -1,0 +1,504 @@
+// C ABI of the library: argument checking, context life cycle, plan and
+// spectrum caches, the batched path and its CUDA-graph cache.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lgf_internal.cuh"
+
+namespace lgf {
+
+lgf_status fail(lgf_ctx *ctx, lgf_status st, const std::string &msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+lgf_status cuda_fail(lgf_ctx *ctx, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, LGF_ENOMEM, m);
+    return fail(ctx, LGF_ECUDA, m);
+}
+
+lgf_status ensure_scratch(lgf_ctx *ctx, void **p, size_t *have, size_t need)
+{
+    if (need <= *have) return LGF_OK;
+    if (*p) {
+        cudaError_t e = cudaFree(*p);
+        *p = nullptr;
+        *have = 0;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch release");
+    }
+    const size_t bytes = need + need / 8 + 256;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(ctx, LGF_ENOMEM, "scratch allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    *have = bytes;
+    return LGF_OK;
+}
+
+lgf_status check_blockset(lgf_ctx *ctx, const lgf_blockset *bs, const char *name)
+{
+    if (!bs) return fail(ctx, LGF_EINVAL, std::string(name) + ": null block set");
+    if (bs->nblocks < 0) return fail(ctx, LGF_EINVAL, std::string(name) + ": negative block count");
+    if (bs->nblocks > 0 && !bs->coords) return fail(ctx, LGF_EINVAL, std::string(name) + ": null coordinates");
+    const int b = bs->b;
+    if (b != 4 && b != 8 && b != 16 && b != 32 && b != 64)
+        return fail(ctx, LGF_EINVAL, std::string(name) + ": block edge must be 4, 8, 16, 32 or 64");
+    for (int i = 0; i < 3 * bs->nblocks; ++i)
+        if (bs->coords[i] < -(1 << 19) || bs->coords[i] >= (1 << 19))
+            return fail(ctx, LGF_EINVAL, std::string(name) + ": block coordinate out of range");
+    return LGF_OK;
+}
+
+int prof_begin(lgf_ctx *ctx, cudaStream_t s, const char *name)
+{
+    if (!ctx->prof) return -1;
+    int id = -1;
+    for (size_t i = 0; i < ctx->prof_names.size(); ++i)
+        if (ctx->prof_names[i] == name) id = (int)i;
+    if (id < 0) {
+        id = (int)ctx->prof_names.size();
+        ctx->prof_names.push_back(name);
+        ctx->prof_launches.push_back(0);
+        ctx->prof_ms.push_back(0.0);
+    }
+    cudaEvent_t ev[2];
+    for (int k = 0; k < 2; ++k) {
+        if (!ctx->ev_pool.empty()) {
+            ev[k] = ctx->ev_pool.back();
+            ctx->ev_pool.pop_back();
+        } else if (cudaEventCreate(&ev[k]) != cudaSuccess) {
+            return -1;
+        }
+    }
+    cudaEventRecord(ev[0], s);
+    ctx->prof_pending.push_back({id, ev[0], ev[1]});
+    return (int)ctx->prof_pending.size() - 1;
+}
+
+void prof_end(lgf_ctx *ctx, cudaStream_t s, int handle)
+{
+    if (handle < 0 || !ctx->prof) return;
+    cudaEventRecord(ctx->prof_pending[handle].b, s);
+}
+
+}  // namespace lgf
+
+using namespace lgf;
+
+namespace {
+
+lgf_status enter(lgf_ctx *ctx)
+{
+    if (!ctx) return LGF_EINVAL;
+    ctx->last_error.clear();
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return LGF_OK;
+}
+
+lgf_status check_fields(lgf_ctx *ctx, const void *f, void *u, int ncomp, int nrhs, int nsrc, int ntgt)
+{
+    if (ncomp < 1 || nrhs < 1) return fail(ctx, LGF_EINVAL, "ncomp and nrhs must be >= 1");
+    if (ntgt > 0 && !u) return fail(ctx, LGF_EINVAL, "null output pointer");
+    if (nsrc > 0 && ntgt > 0 && !f) return fail(ctx, LGF_EINVAL, "null input pointer");
+    return LGF_OK;
+}
+
+size_t elem_size(const lgf_ctx *ctx) { return ctx->prec == LGF_F64 ? 8 : 4; }
+
+// Everything an apply needs before any kernel is enqueued (allocations,
+// synchronous set-up); also used to make batch capture allocation-free.
+struct PreparedPoisson {
+    PoissonPlan *plan = nullptr;
+    Spectrum *spec = nullptr;
+};
+
+lgf_status prepare_poisson(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, int nfields,
+                           cudaStream_t s, PreparedPoisson *pp)
+{
+    if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "lgf_table_build has not been called");
+    lgf_status st = poisson_plan(ctx, src, tgt, &pp->plan);
+    if (st != LGF_OK) return st;
+    st = poisson_spectrum(ctx, pp->plan->g.M, &pp->spec, s);
+    if (st != LGF_OK) return st;
+    st = poisson_prepare_scratch(ctx, pp->plan, nfields);
+    if (st != LGF_OK) return st;
+    for (int d = 0; d < 3; ++d) {
+        twiddles(ctx, pp->plan->g.M[d], ctx->prec == LGF_F64, &st);
+        if (st != LGF_OK) return st;
+    }
+    return LGF_OK;
+}
+
+struct PreparedIntf {
+    IntfPlan *plan = nullptr;
+    IntfWeights *w = nullptr;
+};
+
+lgf_status prepare_intf(lgf_ctx *ctx, double alpha, const lgf_blockset *src, const lgf_blockset *tgt, int nfields,
+                        cudaStream_t s, PreparedIntf *pi)
+{
+    lgf_status st = intf_weights(ctx, alpha, &pi->w, s);
+    if (st != LGF_OK) return st;
+    st = intf_plan(ctx, src, tgt, pi->w->R, &pi->plan);
+    if (st != LGF_OK) return st;
+    return intf_prepare_scratch(ctx, pi->plan, nfields);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lgf_version(void) { return 10000; }
+
+const char *lgf_status_string(lgf_status s)
+{
+    switch (s) {
+    case LGF_OK: return "success";
+    case LGF_EINVAL: return "invalid argument";
+    case LGF_ENOMEM: return "out of memory";
+    case LGF_ECUDA: return "CUDA error";
+    case LGF_ETIMEOUT: return "device-side wait timed out";
+    case LGF_EUNSUPPORTED: return "unsupported size";
+    case LGF_ENOTABLE: return "G_L table not built";
+    }
+    return "unknown status";
+}
+
+const char *lgf_last_error(lgf_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+lgf_status lgf_ctx_create(lgf_ctx **out, const lgf_options *opt)
+{
+    if (!out) return LGF_EINVAL;
+    *out = nullptr;
+    lgf_options o{};
+    if (opt) o = *opt;
+    if (o.prec != LGF_F32 && o.prec != LGF_F64) return LGF_EINVAL;
+    if (!(o.tol >= 0.0) || !std::isfinite(o.tol) || o.tol >= 1.0) return LGF_EINVAL;
+    if (o.table_radius != 0 && (o.table_radius < 8 || o.table_radius > 96)) return LGF_EINVAL;
+    if (o.stencil_radius < 0 || o.stencil_radius > 128 || o.device < 0) return LGF_EINVAL;
+    for (int i = 0; i < 4; ++i)
+        if (o.reserved[i] != 0) return LGF_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device >= ndev) {
+        cudaGetLastError();
+        return LGF_ECUDA;
+    }
+    if (cudaSetDevice(o.device) != cudaSuccess) return LGF_ECUDA;
+    lgf_ctx *ctx = new (std::nothrow) lgf_ctx;
+    if (!ctx) return LGF_ENOMEM;
+    ctx->opt = o;
+    ctx->device = o.device;
+    ctx->prec = o.prec;
+    ctx->tol = o.tol > 0.0 ? o.tol : (o.prec == LGF_F64 ? 1e-13 : 1e-7);
+    if (ctx->opt.table_radius == 0) ctx->opt.table_radius = 48;
+    if (cudaMalloc(&ctx->red_dev, 16 * sizeof(double)) != cudaSuccess) {
+        delete ctx;
+        return LGF_ENOMEM;
+    }
+    *out = ctx;
+    return LGF_OK;
+}
+
+lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
+{
+    if (!ctx) return LGF_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->pplans.clear();
+    ctx->iplans.clear();
+    for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
+    for (auto &kv : ctx->tw32) cudaFree(kv.second);
+    for (auto &kv : ctx->tw64) cudaFree(kv.second);
+    for (auto &w : ctx->weights) {
+        cudaFree(w->w64);
+        cudaFree(w->w32);
+    }
+    cudaFree(ctx->table_dev);
+    cudaFree(ctx->scrA);
+    cudaFree(ctx->scrB);
+    cudaFree(ctx->scrC);
+    cudaFree(ctx->red_dev);
+    for (auto &r : ctx->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    delete ctx;
+    return LGF_OK;
+}
+
+lgf_status lgf_table_build(lgf_ctx *ctx, int32_t max_offset, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (max_offset < 0) return fail(ctx, LGF_EINVAL, "table_build: max_offset < 0");
+    const int R = std::min(ctx->opt.table_radius, std::max<int>(max_offset, kMinTableRadius));
+    if (ctx->table_dev && ctx->table_radius >= R) return LGF_OK;
+    st = table_build(ctx, R, (cudaStream_t)stream);
+    if (st != LGF_OK) return st;
+    // spectra built from an older table are stale
+    for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
+    ctx->spectra.clear();
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+        ctx->graph_key.clear();
+    }
+    return LGF_OK;
+}
+
+lgf_status lgf_table_info(lgf_ctx *ctx, int32_t *table_radius, double *shell_mismatch)
+{
+    if (!ctx) return LGF_EINVAL;
+    if (!ctx->table_dev) return fail(ctx, LGF_ENOTABLE, "table not built");
+    if (table_radius) *table_radius = ctx->table_radius;
+    if (shell_mismatch) *shell_mismatch = ctx->shell_mismatch;
+    return LGF_OK;
+}
+
+lgf_status lgf_table_lookup(lgf_ctx *ctx, const int32_t *offsets_dev, int64_t n, double *out_dev, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (!ctx->table_dev) return fail(ctx, LGF_ENOTABLE, "table not built");
+    if (n < 0 || (n > 0 && (!offsets_dev || !out_dev))) return fail(ctx, LGF_EINVAL, "table_lookup: bad arguments");
+    return table_lookup(ctx, offsets_dev, n, out_dev, (cudaStream_t)stream);
+}
+
+lgf_status lgf_poisson_apply(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, const void *f_dev,
+                             void *u_dev, int32_t ncomp, int32_t nrhs, double dx, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if ((st = check_blockset(ctx, src, "source")) != LGF_OK) return st;
+    if ((st = check_blockset(ctx, tgt, "target")) != LGF_OK) return st;
+    if (src->b != tgt->b) return fail(ctx, LGF_EINVAL, "source and target block edges differ");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(ctx, LGF_EINVAL, "dx must be positive and finite");
+    if ((st = check_fields(ctx, f_dev, u_dev, ncomp, nrhs, src->nblocks, tgt->nblocks)) != LGF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nf = ncomp * nrhs;
+    const size_t b3 = (size_t)src->b * src->b * src->b;
+    if (tgt->nblocks == 0) return LGF_OK;
+    if (src->nblocks == 0) {
+        LGF_CUDA(ctx, cudaMemsetAsync(u_dev, 0, (size_t)tgt->nblocks * b3 * nf * elem_size(ctx), s));
+        return LGF_OK;
+    }
+    PreparedPoisson pp;
+    if ((st = prepare_poisson(ctx, src, tgt, nf, s, &pp)) != LGF_OK) return st;
+    return poisson_run(ctx, pp.plan, pp.spec, f_dev, u_dev, nf, dx, s);
+}
+
+lgf_status lgf_intfactor_weights(lgf_ctx *ctx, double alpha, double *w_dev, int32_t cap, int32_t *radius,
+                                 void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(ctx, LGF_EINVAL, "alpha must be >= 0 and finite");
+    IntfWeights *w = nullptr;
+    if ((st = intf_weights(ctx, alpha, &w, (cudaStream_t)stream)) != LGF_OK) return st;
+    if (radius) *radius = w->R;
+    if (w_dev) {
+        if (cap <= w->R) return fail(ctx, LGF_EINVAL, "intfactor_weights: cap must exceed the radius");
+        LGF_CUDA(ctx, cudaMemcpyAsync(w_dev, w->w64, (w->R + 1) * sizeof(double), cudaMemcpyDeviceToDevice,
+                                      (cudaStream_t)stream));
+    }
+    return LGF_OK;
+}
+
+lgf_status lgf_intfactor_apply(lgf_ctx *ctx, double alpha, const lgf_blockset *src, const lgf_blockset *tgt,
+                               const void *f_dev, void *u_dev, int32_t ncomp, int32_t nrhs, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(ctx, LGF_EINVAL, "alpha must be >= 0 and finite");
+    if ((st = check_blockset(ctx, src, "source")) != LGF_OK) return st;
+    if ((st = check_blockset(ctx, tgt, "target")) != LGF_OK) return st;
+    if (src->b != tgt->b) return fail(ctx, LGF_EINVAL, "source and target block edges differ");
+    if ((st = check_fields(ctx, f_dev, u_dev, ncomp, nrhs, src->nblocks, tgt->nblocks)) != LGF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nf = ncomp * nrhs;
+    const size_t b3 = (size_t)src->b * src->b * src->b;
+    if (tgt->nblocks == 0) return LGF_OK;
+    if (src->nblocks == 0) {
+        LGF_CUDA(ctx, cudaMemsetAsync(u_dev, 0, (size_t)tgt->nblocks * b3 * nf * elem_size(ctx), s));
+        return LGF_OK;
+    }
+    PreparedIntf pi;
+    if ((st = prepare_intf(ctx, alpha, src, tgt, nf, s, &pi)) != LGF_OK) return st;
+    return intf_run(ctx, pi.plan, pi.w, f_dev, u_dev, nf, s);
+}
+
+lgf_status lgf_residual(lgf_ctx *ctx, const lgf_blockset *set, const void *u_dev, const void *f_dev, double dx,
+                        double *r_dev, double *max_abs, double *max_f, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if ((st = check_blockset(ctx, set, "set")) != LGF_OK) return st;
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(ctx, LGF_EINVAL, "dx must be positive and finite");
+    if (set->nblocks > 0 && (!u_dev || !f_dev || !r_dev)) return fail(ctx, LGF_EINVAL, "null field pointer");
+    return residual_run(ctx, set, u_dev, f_dev, dx, r_dev, max_abs, max_f, (cudaStream_t)stream);
+}
+
+lgf_status lgf_profile_enable(lgf_ctx *ctx, int32_t enable)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    LGF_CUDA(ctx, cudaDeviceSynchronize());
+    for (auto &r : ctx->prof_pending) {
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    ctx->prof_names.clear();
+    ctx->prof_launches.clear();
+    ctx->prof_ms.clear();
+    ctx->prof = enable != 0;
+    return LGF_OK;
+}
+
+lgf_status lgf_profile_read(lgf_ctx *ctx, lgf_kernel_stat *out, int32_t cap, int32_t *n)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (cap < 0 || (cap > 0 && !out) || !n) return fail(ctx, LGF_EINVAL, "profile_read: bad arguments");
+    LGF_CUDA(ctx, cudaDeviceSynchronize());
+    for (auto &r : ctx->prof_pending) {
+        float ms = 0.f;
+        LGF_CUDA(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+        ctx->prof_launches[r.name] += 1;
+        ctx->prof_ms[r.name] += ms;
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    const int k = (int)ctx->prof_names.size();
+    *n = k;
+    for (int i = 0; i < k && i < cap; ++i) {
+        memset(&out[i], 0, sizeof(out[i]));
+        strncpy(out[i].name, ctx->prof_names[i].c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = ctx->prof_launches[i];
+        out[i].total_ms = ctx->prof_ms[i];
+    }
+    for (int i = 0; i < k; ++i) {
+        ctx->prof_launches[i] = 0;
+        ctx->prof_ms[i] = 0.0;
+    }
+    return LGF_OK;
+}
+
+lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (nprob < 0 || (nprob > 0 && !probs)) return fail(ctx, LGF_EINVAL, "batch: bad problem list");
+    cudaStream_t s = (cudaStream_t)stream;
+    // 1. validate and build a key of everything that shapes the work
+    std::vector<unsigned char> key;
+    auto put = [&](const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        key.insert(key.end(), c, c + n);
+    };
+    for (int i = 0; i < nprob; ++i) {
+        const lgf_problem &p = probs[i];
+        if ((st = check_blockset(ctx, &p.src, "batch source")) != LGF_OK) return st;
+        if ((st = check_blockset(ctx, &p.tgt, "batch target")) != LGF_OK) return st;
+        if (p.src.b != p.tgt.b) return fail(ctx, LGF_EINVAL, "batch: block edges differ");
+        if (p.op < LGF_OP_POISSON || p.op > LGF_OP_POISSON_THEN_INTFACTOR || p.reserved != 0)
+            return fail(ctx, LGF_EINVAL, "batch: unknown operation");
+        if (p.op != LGF_OP_POISSON && (!(p.alpha >= 0.0) || !std::isfinite(p.alpha)))
+            return fail(ctx, LGF_EINVAL, "batch: alpha must be >= 0 and finite");
+        if (p.op != LGF_OP_INTFACTOR && (!(p.dx > 0.0) || !std::isfinite(p.dx)))
+            return fail(ctx, LGF_EINVAL, "batch: dx must be positive and finite");
+        if ((st = check_fields(ctx, p.f_dev, p.u_dev, p.ncomp, p.nrhs, p.src.nblocks, p.tgt.nblocks)) != LGF_OK)
+            return st;
+        put(&p.src.b, sizeof(int32_t));
+        put(&p.src.nblocks, sizeof(int32_t));
+        put(p.src.coords, 3 * sizeof(int32_t) * (size_t)p.src.nblocks);
+        put(&p.tgt.nblocks, sizeof(int32_t));
+        put(p.tgt.coords, 3 * sizeof(int32_t) * (size_t)p.tgt.nblocks);
+        put(&p.f_dev, sizeof(void *));
+        put(&p.u_dev, sizeof(void *));
+        put(&p.ncomp, 4 * sizeof(int32_t));
+        put(&p.alpha, 2 * sizeof(double));
+    }
+    put(&s, sizeof(s));
+    // 2. prepare every plan, spectrum, weight set and the largest scratch
+    struct Item {
+        PreparedPoisson pp;
+        PreparedIntf pi;
+    };
+    std::vector<Item> items(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        const lgf_problem &p = probs[i];
+        const int nf = p.ncomp * p.nrhs;
+        if (p.tgt.nblocks == 0 || p.src.nblocks == 0) continue;
+        if (p.op != LGF_OP_INTFACTOR)
+            if ((st = prepare_poisson(ctx, &p.src, &p.tgt, nf, s, &items[i].pp)) != LGF_OK) return st;
+        if (p.op == LGF_OP_INTFACTOR)
+            if ((st = prepare_intf(ctx, p.alpha, &p.src, &p.tgt, nf, s, &items[i].pi)) != LGF_OK) return st;
+        if (p.op == LGF_OP_POISSON_THEN_INTFACTOR)
+            if ((st = prepare_intf(ctx, p.alpha, &p.tgt, &p.tgt, nf, s, &items[i].pi)) != LGF_OK) return st;
+    }
+    auto enqueue = [&]() -> lgf_status {
+        for (int i = 0; i < nprob; ++i) {
+            const lgf_problem &p = probs[i];
+            const int nf = p.ncomp * p.nrhs;
+            const size_t b3 = (size_t)p.src.b * p.src.b * p.src.b;
+            if (p.tgt.nblocks == 0) continue;
+            if (p.src.nblocks == 0) {
+                LGF_CUDA(ctx, cudaMemsetAsync(p.u_dev, 0, (size_t)p.tgt.nblocks * b3 * nf * elem_size(ctx), s));
+                continue;
+            }
+            lgf_status e2;
+            if (p.op != LGF_OP_INTFACTOR)
+                if ((e2 = poisson_run(ctx, items[i].pp.plan, items[i].pp.spec, p.f_dev, p.u_dev, nf, p.dx, s)) != LGF_OK)
+                    return e2;
+            if (p.op == LGF_OP_INTFACTOR)
+                if ((e2 = intf_run(ctx, items[i].pi.plan, items[i].pi.w, p.f_dev, p.u_dev, nf, s)) != LGF_OK) return e2;
+            if (p.op == LGF_OP_POISSON_THEN_INTFACTOR)
+                if ((e2 = intf_run(ctx, items[i].pi.plan, items[i].pi.w, p.u_dev, p.u_dev, nf, s)) != LGF_OK) return e2;
+        }
+        return LGF_OK;
+    };
+    // 3. the legacy default stream cannot be captured, and per-kernel timing
+    //    needs direct launches: run without a graph
+    if (s == nullptr || ctx->prof) return enqueue();
+    if (ctx->graph_exec && key == ctx->graph_key) {
+        LGF_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, s));
+        return LGF_OK;
+    }
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+        ctx->graph_key.clear();
+    }
+    LGF_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    lgf_status est = enqueue();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (est != LGF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return est;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch: stream capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch: graph instantiation");
+    ctx->graph_exec = exec;
+    ctx->graph_key = key;
+    LGF_CUDA(ctx, cudaGraphLaunch(exec, s));
+    return LGF_OK;
+}
+
+}  // extern "C"

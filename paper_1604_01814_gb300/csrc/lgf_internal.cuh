@@ -1,0 +1,182 @@
+// Internal declarations shared by the translation units of the CUDA library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "lgf.h"
+#include "lgf_fft.cuh"
+
+namespace lgf {
+
+constexpr int kMaxFft = 4096;        // largest transform length per axis
+constexpr int kMinTableRadius = 24;  // expansion error at |n| > 24 is below 1e-9 relative
+
+// --------------------------------------------------------------------------
+// Host-side factorisation of a power-of-two FFT length.
+// --------------------------------------------------------------------------
+FftShape make_fft_shape(int M);
+int next_fft_size(int n);   // smallest supported length >= n (power of two >= 32)
+
+// --------------------------------------------------------------------------
+// Poisson plan: one problem's padded transform box.
+// Box coordinates are lattice coordinates minus `lo` (the union bounding box
+// corner of the source and target block sets).
+// --------------------------------------------------------------------------
+struct PoissonGeom {
+    int M[3];           // transform lengths (x, y, z)
+    int Kx;             // Mx / 2 + 1 (half spectrum along x)
+    int s0[3], Ls[3];   // source region [s0, s0 + Ls) in box coordinates
+    int t0[3], Lt[3];   // target region
+    int b;
+    int nbs[3], nbt[3]; // region extents in blocks
+    const int *srcmap;  // [nbs_z][nbs_y][nbs_x] -> source block index or -1
+    const int *tgtmap;  // [nbt_z][nbt_y][nbt_x] -> target block index or -1
+    int64_t fstride;    // elements per field in f (nsrc * b^3)
+    int64_t ustride;    // elements per field in u (ntgt * b^3)
+    int64_t Astride;    // complex elements per field in scratch A
+    int64_t Bstride;    // complex elements per field in scratch B
+    int ldA_y;          // rows per z-plane in A (max(Ls_y, Lt_y))
+    int ldB_z;          // unused padding field (kept for alignment)
+    double scale;       // dx^2
+};
+
+struct PoissonPlan {
+    int b = 0;
+    std::vector<int32_t> src, tgt;   // block coordinates, for cache matching
+    PoissonGeom g{};
+    int *srcmap_dev = nullptr, *tgtmap_dev = nullptr;
+    int64_t A_elems = 0, B_elems = 0; // complex elements per field
+    ~PoissonPlan();
+};
+
+// --------------------------------------------------------------------------
+// Integrating-factor plan: three separable passes over block sets.
+// --------------------------------------------------------------------------
+struct IntfPass {
+    int nout = 0;             // output blocks
+    int *nbr_dev = nullptr;   // [nout][2*nr+1] input block index or -1
+};
+
+struct IntfPlan {
+    int b = 0, nr = 0;
+    std::vector<int32_t> src, tgt;
+    int n1 = 0, n2 = 0;       // sizes of the two intermediate block sets
+    IntfPass pass[3];
+    ~IntfPlan();
+};
+
+struct IntfWeights {
+    double alpha = 0;
+    int R = 0;
+    double *w64 = nullptr;    // [R+1]
+    float *w32 = nullptr;     // [R+1]
+};
+
+struct Spectrum {
+    std::array<int, 3> M{};
+    void *dev = nullptr;      // (Mz/2+1)(My/2+1)(Mx/2+1) reals, context precision, scaled by 1/(MxMyMz)
+};
+
+}  // namespace lgf
+
+struct lgf_ctx {
+    lgf_options opt{};
+    int device = 0;
+    int prec = LGF_F32;
+    double tol = 1e-7;
+    std::string last_error;
+
+    // G_L table (FP64, sorted offsets a >= b >= c up to table_radius)
+    double *table_dev = nullptr;
+    int table_radius = -1;
+    double shell_mismatch = 0.0;
+
+    // twiddles per log2 length: exp(-2 pi i m / M), m < M
+    std::map<int, void *> tw32, tw64;
+
+    std::map<std::array<int, 3>, lgf::Spectrum> spectra;
+    std::vector<std::unique_ptr<lgf::PoissonPlan>> pplans;
+    std::vector<std::unique_ptr<lgf::IntfPlan>> iplans;
+    std::vector<std::unique_ptr<lgf::IntfWeights>> weights;
+
+    // grow-only scratch
+    void *scrA = nullptr, *scrB = nullptr, *scrC = nullptr;
+    size_t scrA_bytes = 0, scrB_bytes = 0, scrC_bytes = 0;
+
+    // batch graph cache
+    std::vector<unsigned char> graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+
+    double *red_dev = nullptr;   // small reduction buffer (residual, table mismatch)
+
+    // optional per-kernel timing with CUDA events on the launch stream
+    bool prof = false;
+    struct ProfRec {
+        int name;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::string> prof_names;
+    std::vector<int64_t> prof_launches;
+    std::vector<double> prof_ms;
+};
+
+namespace lgf {
+
+lgf_status fail(lgf_ctx *ctx, lgf_status st, const std::string &msg);
+lgf_status cuda_fail(lgf_ctx *ctx, cudaError_t e, const char *what);
+lgf_status ensure_scratch(lgf_ctx *ctx, void **p, size_t *have, size_t need);
+const void *twiddles(lgf_ctx *ctx, int M, bool dbl, lgf_status *st);
+
+#define LGF_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return lgf::cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+#define LGF_CHECK_LAUNCH(ctx, what)                           \
+    do {                                                      \
+        cudaError_t e_ = cudaGetLastError();                  \
+        if (e_ != cudaSuccess) return lgf::cuda_fail((ctx), e_, (what)); \
+    } while (0)
+
+// Per-kernel timing (lgf_capi.cu): prof_begin records a start event and
+// returns a handle (-1 when profiling is off); prof_end records the stop event.
+int prof_begin(lgf_ctx *ctx, cudaStream_t s, const char *name);
+void prof_end(lgf_ctx *ctx, cudaStream_t s, int handle);
+
+// Table (lgf_table.cu)
+lgf_status table_build(lgf_ctx *ctx, int radius, cudaStream_t s);
+lgf_status table_lookup(lgf_ctx *ctx, const int32_t *off, int64_t n, double *out, cudaStream_t s);
+lgf_status kernel_window(lgf_ctx *ctx, const int M[3], double *box, cudaStream_t s);
+lgf_status bessel_weights(lgf_ctx *ctx, double z, int nmax, double *out_dev, cudaStream_t s);
+
+// Poisson (lgf_poisson.cu)
+lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, PoissonPlan **out);
+lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], Spectrum **out, cudaStream_t s);
+lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const void *f, void *u, int nfields,
+                       double dx, cudaStream_t s);
+lgf_status poisson_prepare_scratch(lgf_ctx *ctx, const PoissonPlan *pl, int nfields);
+
+// Integrating factor (lgf_intfactor.cu)
+lgf_status intf_weights(lgf_ctx *ctx, double alpha, IntfWeights **out, cudaStream_t s);
+lgf_status intf_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, int R, IntfPlan **out);
+lgf_status intf_prepare_scratch(lgf_ctx *ctx, const IntfPlan *pl, int nfields);
+lgf_status intf_run(lgf_ctx *ctx, IntfPlan *pl, const IntfWeights *w, const void *f, void *u, int nfields,
+                    cudaStream_t s);
+
+// Residual (lgf_residual.cu)
+lgf_status residual_run(lgf_ctx *ctx, const lgf_blockset *set, const void *u, const void *f, double dx,
+                        double *r, double *max_abs, double *max_f, cudaStream_t s);
+
+// Block-set validation shared by the entry points.
+lgf_status check_blockset(lgf_ctx *ctx, const lgf_blockset *bs, const char *name);
+
+}  // namespace lgf

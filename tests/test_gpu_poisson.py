@@ -1,0 +1,140 @@
+"""LGF Poisson apply on the GPU against the CPU oracle (direct summation).
+
+Tolerances (relative L-infinity over every compared value): 1e-12 for FP64
+contexts and 1e-5 for FP32 contexts."""
+import numpy as np
+import pytest
+import torch
+
+import lgf_inputs as li
+from conftest import rel_linf
+
+pytestmark = pytest.mark.gpu
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def run_poisson(ctx, p, dx=1.0):
+    dt = ctx.dtype
+    f = torch.tensor(p.f.reshape(-1), dtype=dt, device="cuda")
+    u = torch.full((p.nrhs * p.ncomp * p.tgt.shape[0] * p.b ** 3,), float("nan"), dtype=dt, device="cuda")
+    ctx.poisson_apply(p.b, p.src, p.tgt, f, u, ncomp=p.ncomp, nrhs=p.nrhs, dx=dx)
+    torch.cuda.synchronize()
+    return u.cpu().numpy().astype(np.float64).reshape(p.nrhs, p.ncomp, p.tgt.shape[0] * p.b ** 3)
+
+
+def oracle_fields(oracle, p, pts_idx=None, dx=1.0, f=None):
+    f = p.f if f is None else f
+    pts = oracle.block_points(p.b, p.tgt)
+    if pts_idx is not None:
+        pts = pts[pts_idx]
+    out = np.empty((p.nrhs, p.ncomp, pts.shape[0]))
+    for r in range(p.nrhs):
+        for c in range(p.ncomp):
+            out[r, c] = oracle.poisson_direct(p.b, p.src, f[r, c], pts, dx=dx, R=64)
+    return out
+
+
+def test_box32_fp64_every_point(ctx64, oracle):
+    """32^3 box, f ~ U[-1,1] (seed 0), all 32768 targets, FP64."""
+    p = li.plain_box32()
+    got = run_poisson(ctx64, p)
+    ref = oracle_fields(oracle, p)
+    assert rel_linf(got, ref) < TOL["f64"]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("seed,b,ns,nt,ext", [(1, 8, 5, 7, (4, 3, 3)), (2, 16, 3, 4, (3, 2, 2)),
+                                            (3, 4, 9, 6, (5, 4, 3)), (4, 32, 1, 2, (2, 1, 1))])
+def test_random_sparse_sets_every_point(prec, seed, b, ns, nt, ext, ctx64, ctx32, oracle):
+    """Ragged block sets, source and target sets disjoint or overlapping."""
+    ctx = ctx64 if prec == "f64" else ctx32
+    p = li.random_sparse(seed, b=b, nsrc=ns, ntgt=nt, extent=ext)
+    got = run_poisson(ctx, p)
+    ref = oracle_fields(oracle, p)
+    assert rel_linf(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_multiple_components_and_rhs(prec, ctx64, ctx32, oracle):
+    ctx = ctx64 if prec == "f64" else ctx32
+    p = li.random_sparse(11, b=8, nsrc=4, ntgt=5, extent=(3, 3, 2), nrhs=2, ncomp=3)
+    got = run_poisson(ctx, p, dx=0.5)
+    ref = oracle_fields(oracle, p, dx=0.5)
+    for r in range(2):
+        for c in range(3):
+            assert rel_linf(got[r, c], ref[r, c]) < TOL[prec]
+
+
+def test_dense128_fp32_sampled(ctx32, oracle):
+    """128^3 dense box of Gaussian blobs (seed 1), FP32, 512 random targets."""
+    p = li.dense_blobs()
+    got = run_poisson(ctx32, p)
+    rng = np.random.default_rng(101)
+    idx = rng.choice(p.tgt.shape[0] * p.b ** 3, size=512, replace=False)
+    ref = oracle_fields(oracle, p, pts_idx=idx)
+    assert rel_linf(got[0, 0, idx], ref[0, 0]) < TOL["f32"]
+
+
+def test_dense128_fp64_residual(ctx64):
+    """FP64 apply on the 128^3 box satisfies L u = f (lgf_residual, FP64)."""
+    p = li.dense_blobs(b=16)
+    dt = torch.float64
+    f = torch.tensor(p.f.reshape(-1), dtype=dt, device="cuda")
+    u = torch.empty_like(f)
+    ctx64.poisson_apply(p.b, p.src, p.tgt, f, u)
+    r, rmax, fmax = ctx64.residual(p.b, p.tgt, u, f)
+    assert rmax < 1e-11 * fmax
+    # every interior point was checked: the residual field is zero only on the boundary
+    assert torch.count_nonzero(r).item() > 0.9 * (126 ** 3)
+
+
+def test_sphere_fp32_sampled(ctx32, oracle):
+    """Sphere + wake block set (b=16), 3-component IB-like sources, 256 targets."""
+    p = li.sphere_ib()
+    got = run_poisson(ctx32, p)
+    rng = np.random.default_rng(5)
+    idx = rng.choice(p.tgt.shape[0] * p.b ** 3, size=256, replace=False)
+    ref = oracle_fields(oracle, p, pts_idx=idx)
+    for c in range(3):
+        assert rel_linf(got[0, c, idx], ref[0, c]) < TOL["f32"]
+
+
+def test_point_source_reproduces_table(ctx64):
+    b = 8
+    f = torch.zeros(b ** 3, dtype=torch.float64, device="cuda")
+    f[(2 * b + 3) * b + 1] = 1.0                       # point (1, 3, 2)
+    tgt = np.array([[0, 0, 0], [3, -1, 2], [-2, 0, 0]], dtype=np.int32)
+    u = torch.empty(3 * b ** 3, dtype=torch.float64, device="cuda")
+    ctx64.poisson_apply(b, [[0, 0, 0]], tgt, f, u)
+    pts = li.block_point_coords(b, tgt).reshape(-1, 3)
+    offs = torch.tensor(pts - np.array([1, 3, 2]), dtype=torch.int32)
+    g = ctx64.table_lookup(offs)
+    assert torch.max(torch.abs(u - g)).item() < 1e-13 * torch.max(torch.abs(g)).item()
+
+
+def test_empty_sets(ctx32):
+    b = 8
+    u = torch.full((2 * b ** 3,), 7.0, device="cuda")
+    ctx32.poisson_apply(b, np.zeros((0, 3)), [[0, 0, 0], [1, 0, 0]], None, u)
+    torch.cuda.synchronize()
+    assert torch.all(u == 0)
+    f = torch.ones(b ** 3, device="cuda")
+    ctx32.poisson_apply(b, [[0, 0, 0]], np.zeros((0, 3)), f, None)
+
+
+def test_invalid_arguments(ctx32):
+    import paper_1604_01814_gb300 as lgf
+    b = 8
+    f = torch.ones(b ** 3, device="cuda")
+    u = torch.empty(b ** 3, device="cuda")
+    with pytest.raises(lgf.LgfError) as e:
+        ctx32.poisson_apply(b, [[0, 0, 0], [0, 0, 0]], [[0, 0, 0]], torch.ones(2 * b ** 3, device="cuda"), u)
+    assert e.value.status == 1
+    with pytest.raises(lgf.LgfError) as e:
+        ctx32.poisson_apply(b, [[0, 0, 0]], [[0, 0, 0]], f, u, dx=-1.0)
+    assert e.value.status == 1
+    with pytest.raises(lgf.LgfError) as e:
+        ctx32.poisson_apply(b, [[0, 0, 0]], [[300, 0, 0]], f, u)   # union spans > 2048 points
+    assert e.value.status == 5
+    with pytest.raises(ValueError):
+        ctx32.poisson_apply(b, [[0, 0, 0]], [[0, 0, 0]], f.double(), u)
