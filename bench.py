@@ -384,7 +384,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense128")
-    ap.add_argument("--cpu-points", type=int, default=4096)
+    ap.add_argument("--cpu-points", type=int, default=3072)
     ap.add_argument("--ref-points", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args(argv)

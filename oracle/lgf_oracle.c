@@ -209,9 +209,16 @@ static const mono T7M[] = {{6,0,0,-647}, {5,1,0,16419}, {5,0,1,16419}, {4,2,0,-1
 
 static double mono_sum(const mono *m, int count, double X, double Y, double Z)
 {
+    double px[7], py[7], pz[7];   /* X^k, Y^k, Z^k for k <= 6 */
+    px[0] = py[0] = pz[0] = 1.0;
+    for (int k = 1; k < 7; ++k) {
+        px[k] = px[k - 1] * X;
+        py[k] = py[k - 1] * Y;
+        pz[k] = pz[k - 1] * Z;
+    }
     double s = 0.0;
     for (int i = 0; i < count; ++i)
-        s += m[i].v * pow(X, m[i].a) * pow(Y, m[i].b) * pow(Z, m[i].c);
+        s += m[i].v * px[m[i].a] * py[m[i].b] * pz[m[i].c];
     return s;
 }
 
@@ -222,9 +229,10 @@ double orc_lgf_asym(int n1, int n2, int n3, int order)
     const double r2 = X + Y + Z, r = sqrt(r2);
     if (r2 == 0.0) return NAN;
     double g = -1.0 / (4.0 * ORC_PI * r);
-    if (order >= 3) g += mono_sum(T3M, 6, X, Y, Z) / (16.0 * ORC_PI * pow(r, 7));
-    if (order >= 5) g += mono_sum(T5M, 15, X, Y, Z) / (128.0 * ORC_PI * pow(r, 13));
-    if (order >= 7) g += mono_sum(T7M, 28, X, Y, Z) / (512.0 * ORC_PI * pow(r, 19));
+    const double r6 = r2 * r2 * r2, r7 = r6 * r;
+    if (order >= 3) g += mono_sum(T3M, 6, X, Y, Z) / (16.0 * ORC_PI * r7);
+    if (order >= 5) g += mono_sum(T5M, 15, X, Y, Z) / (128.0 * ORC_PI * r7 * r6);
+    if (order >= 7) g += mono_sum(T7M, 28, X, Y, Z) / (512.0 * ORC_PI * r7 * r6 * r6);
     return g;
 }
 
