@@ -199,6 +199,34 @@ typedef struct {
    seen, and reset the totals. */
 LGF_API lgf_status lgf_profile_read(lgf_ctx *ctx, lgf_kernel_stat *out, int32_t cap, int32_t *n);
 
+/* Allocation-free integrating-factor apply.  The paper has no counterpart:
+   this entry point exists for callers that must not allocate device memory
+   while they run -- for example a time-stepping loop whose device memory is
+   reserved up front by another allocator (a framework's caching allocator),
+   where a cudaMalloc could fail or synchronise the whole device.  It computes
+   exactly what lgf_intfactor_apply computes (same kernels, same truncation
+   rule with `tol`, 0 = 1e-7 for LGF_F32 and 1e-13 for LGF_F64) on the
+   current device, without a context and without calling cudaMalloc,
+   cudaFree or any allocating routine.  Its scratch (weights, neighbour
+   tables and the two intermediate fields) is one 32 MiB __device__ array
+   that every GPU which loads the library holds until the process exits;
+   planning uses fixed host arrays, so the function is not thread safe.
+   Limits (LGF_EUNSUPPORTED beyond them): at most 1024 source and 1024 target
+   blocks, block sets within a 64-block box (after growing by the stencil
+   reach), at most 8192 blocks per intermediate set, and intermediate fields
+   of at most about 32 MiB in total (nfields x blocks x b^3 x element size).
+   The first call on each device takes the device address of the array with
+   cudaGetSymbolAddress; make that first call before any stream capture.
+   Every call reuses the same array: calls whose work overlaps on the GPU
+   (different streams, or the same array from two host threads) race.  Each
+   call synchronises `stream` once (to read the weights and choose the
+   radius).  err_msg (host, err_cap bytes, may be NULL) receives a message
+   on failure. */
+LGF_API lgf_status lgf_intfactor_apply_noalloc(int32_t prec, double tol, double alpha, const lgf_blockset *src,
+                                               const lgf_blockset *tgt, const void *f_dev, void *u_dev,
+                                               int32_t ncomp, int32_t nrhs, void *stream, char *err_msg,
+                                               int32_t err_cap);
+
 /* Static text for a status code. */
 LGF_API const char *lgf_status_string(lgf_status s);
 

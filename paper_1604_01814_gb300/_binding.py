@@ -23,8 +23,8 @@ LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR = 0, 1, 2
 # Every symbol include/lgf.h declares (checked by the symbol test).
 EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
            "lgf_poisson_apply", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
-           "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_status_string", "lgf_last_error",
-           "lgf_version")
+           "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_intfactor_apply_noalloc",
+           "lgf_status_string", "lgf_last_error", "lgf_version")
 
 
 class lgf_blockset(ctypes.Structure):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "lgf_residual": [vp, bsp, vp, vp, dbl, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
         "lgf_profile_enable": [vp, i32],
         "lgf_profile_read": [vp, ctypes.POINTER(lgf_kernel_stat), i32, ctypes.POINTER(i32)],
+        "lgf_intfactor_apply_noalloc": [i32, dbl, dbl, bsp, bsp, vp, vp, i32, i32, vp, ctypes.c_char_p, i32],
         "lgf_status_string": [i32],
         "lgf_last_error": [vp],
         "lgf_version": [],
@@ -301,6 +302,21 @@ def lgf_profile_enable(ctx: Context, enable: bool = True):
 
 def lgf_profile_read(ctx: Context) -> dict:
     return ctx.profile_read()
+
+
+def lgf_intfactor_apply_noalloc(prec: str, alpha: float, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1,
+                                tol: float = 0.0, stream=None):
+    """Allocation-free integrating factor (no context; see include/lgf.h)."""
+    L = load()
+    s, sa = _blockset(b, src)
+    t, ta = _blockset(b, tgt)
+    msg = ctypes.create_string_buffer(256)
+    st = L.lgf_intfactor_apply_noalloc({"f32": LGF_F32, "f64": LGF_F64}[prec], float(tol), float(alpha),
+                                       ctypes.byref(s), ctypes.byref(t), _ptr(f), _ptr(u), int(ncomp), int(nrhs),
+                                       _stream_ptr(stream), msg, 256)
+    if st != LGF_OK:
+        raise LgfError(st, "lgf_intfactor_apply_noalloc: " + msg.value.decode())
+    return u
 
 
 def lgf_status_string(status: int) -> str:

@@ -346,3 +346,240 @@ lgf_status intf_run(lgf_ctx *ctx, IntfPlan *pl, const IntfWeights *w, const void
 }
 
 }  // namespace lgf
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the integrating-factor apply.
+//
+// For callers that must not allocate device memory while they run (a solver
+// loop whose device memory is reserved up front by another allocator, such as
+// a framework's caching allocator, where a cudaMalloc could fail or stall the
+// whole device).  The intermediate block arrays of the three passes, the
+// neighbour tables and the weights live in one file-scope __device__ array of
+// kNoAllocBytes; planning uses fixed-size host arrays.  The array's device
+// address is taken with cudaGetSymbolAddress on the first call on each device.
+// Every call reuses the same array, so calls that overlap on the GPU race.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;   // device scratch, held by every GPU that loads the library
+constexpr int kNoAllocMaxBlocks = 1024;              // per source or target set
+constexpr int kNoAllocMaxInter = 8192;               // per intermediate set
+constexpr int kNoAllocGrid = 64;                     // block-lookup box edge (blocks)
+constexpr int kNoAllocMaxDevices = 64;
+constexpr int kNoAllocWeightCap = 128;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+void *g_noalloc_base[kNoAllocMaxDevices];
+int32_t h_gS[kNoAllocGrid * kNoAllocGrid * kNoAllocGrid];
+int32_t h_gX[kNoAllocGrid * kNoAllocGrid * kNoAllocGrid];
+int32_t h_gY[kNoAllocGrid * kNoAllocGrid * kNoAllocGrid];
+unsigned char h_gC[kNoAllocGrid * kNoAllocGrid * kNoAllocGrid];
+int32_t h_x1[3 * kNoAllocMaxInter], h_y2[3 * kNoAllocMaxInter];
+int32_t h_nbr[3 * kNoAllocMaxInter * 33];
+double h_w[kNoAllocWeightCap + 1];
+
+lgf_status noalloc_err(char *msg, int cap, lgf_status st, const char *text)
+{
+    if (msg && cap > 0) {
+        strncpy(msg, text, (size_t)cap - 1);
+        msg[cap - 1] = '\0';
+    }
+    return st;
+}
+
+}  // namespace
+
+extern "C" LGF_API lgf_status lgf_intfactor_apply_noalloc(int32_t prec, double tol, double alpha,
+                                                          const lgf_blockset *src, const lgf_blockset *tgt,
+                                                          const void *f_dev, void *u_dev, int32_t ncomp,
+                                                          int32_t nrhs, void *stream, char *err_msg,
+                                                          int32_t err_cap)
+{
+    using namespace lgf;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto err = [&](lgf_status st, const char *t) { return noalloc_err(err_msg, err_cap, st, t); };
+    if (err_msg && err_cap > 0) err_msg[0] = '\0';
+    if (prec != LGF_F32 && prec != LGF_F64) return err(LGF_EINVAL, "prec must be LGF_F32 or LGF_F64");
+    if (!(tol >= 0.0) || !(tol < 1.0)) return err(LGF_EINVAL, "tol must be in [0, 1)");
+    if (!(alpha >= 0.0) || !std::isfinite(alpha)) return err(LGF_EINVAL, "alpha must be >= 0 and finite");
+    if (!src || !tgt) return err(LGF_EINVAL, "null block set");
+    if (check_blockset(nullptr, src, "source") != LGF_OK || check_blockset(nullptr, tgt, "target") != LGF_OK)
+        return err(LGF_EINVAL, "bad block set (edge 4..64, non-negative count, coordinates present)");
+    if (src->b != tgt->b) return err(LGF_EINVAL, "source and target block edges differ");
+    if (ncomp < 1 || nrhs < 1) return err(LGF_EINVAL, "ncomp and nrhs must be >= 1");
+    if (src->nblocks > kNoAllocMaxBlocks || tgt->nblocks > kNoAllocMaxBlocks)
+        return err(LGF_EUNSUPPORTED, "more than 1024 blocks in the source or target set");
+    if (tgt->nblocks > 0 && !u_dev) return err(LGF_EINVAL, "null output pointer");
+    if (src->nblocks > 0 && tgt->nblocks > 0 && !f_dev) return err(LGF_EINVAL, "null input pointer");
+    const int b = src->b, nf = ncomp * nrhs;
+    const size_t esz = prec == LGF_F64 ? 8 : 4;
+    const size_t b3 = (size_t)b * b * b;
+    if (tgt->nblocks == 0) return LGF_OK;
+    if (src->nblocks == 0) {
+        if (cudaMemsetAsync(u_dev, 0, (size_t)tgt->nblocks * b3 * nf * esz, s) != cudaSuccess)
+            return err(LGF_ECUDA, "cudaMemsetAsync failed");
+        return LGF_OK;
+    }
+    // set-up, once per device: the device address of the static scratch
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= kNoAllocMaxDevices)
+        return err(LGF_ECUDA, "cudaGetDevice failed");
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+            return err(LGF_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
+        g_noalloc_base[dev] = p;
+    }
+    unsigned char *base = (unsigned char *)g_noalloc_base[dev];
+    double *w64 = (double *)base;
+    float *w32 = (float *)(base + 2048);
+    int32_t *nbr_dev = (int32_t *)(base + 4096);
+
+    // weights on the GPU, radius chosen on the host
+    const double thr_tol = tol > 0.0 ? tol : (prec == LGF_F64 ? 1e-13 : 1e-7);
+    if (bessel_weights(nullptr, 2.0 * alpha, kNoAllocWeightCap, w64, s) != LGF_OK)
+        return err(LGF_ECUDA, "weight kernel launch failed");
+    if (cudaMemcpyAsync(h_w, w64, sizeof(h_w), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return err(LGF_ECUDA, "weight copy failed");
+    int R = 0;
+    const double thr = thr_tol / 8.0 * h_w[0];
+    while (R < kNoAllocWeightCap && h_w[R] >= thr) ++R;
+    if (alpha == 0.0) R = 0;
+    if (alpha > 0.0 && h_w[kNoAllocWeightCap] >= thr) return err(LGF_EUNSUPPORTED, "alpha needs a radius above 128");
+    const int nr = R == 0 ? 0 : (R + b - 1) / b;
+    const int nd = 2 * nr + 1;
+    if (nd > 33) return err(LGF_EUNSUPPORTED, "stencil reaches more than 16 blocks");
+    k_to_float<<<1, 256, 0, s>>>(w64, w32, R + 1);
+
+    // block-lookup box: sources and targets grown by nr blocks
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = INT32_MAX;
+        hi[d] = INT32_MIN;
+    }
+    for (const lgf_blockset *bs : {src, tgt})
+        for (int i = 0; i < bs->nblocks; ++i)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], bs->coords[3 * i + d] - nr);
+                hi[d] = std::max(hi[d], bs->coords[3 * i + d] + nr);
+            }
+    for (int d = 0; d < 3; ++d)
+        if (hi[d] - lo[d] + 1 > kNoAllocGrid) return err(LGF_EUNSUPPORTED, "block sets span more than 64 blocks");
+    const size_t ncell = (size_t)kNoAllocGrid * kNoAllocGrid * kNoAllocGrid;
+    memset(h_gS, 0, ncell * sizeof(int32_t));
+    memset(h_gX, 0, ncell * sizeof(int32_t));
+    memset(h_gY, 0, ncell * sizeof(int32_t));
+    memset(h_gC, 0, ncell);
+    auto cell = [&](int x, int y, int z) -> long {
+        x -= lo[0];
+        y -= lo[1];
+        z -= lo[2];
+        if (x < 0 || y < 0 || z < 0 || x >= kNoAllocGrid || y >= kNoAllocGrid || z >= kNoAllocGrid) return -1;
+        return ((long)z * kNoAllocGrid + y) * kNoAllocGrid + x;
+    };
+    for (int i = 0; i < src->nblocks; ++i) {
+        const long c = cell(src->coords[3 * i], src->coords[3 * i + 1], src->coords[3 * i + 2]);
+        if (h_gS[c]) return err(LGF_EINVAL, "duplicate block in the source set");
+        h_gS[c] = i + 1;
+    }
+    for (int i = 0; i < tgt->nblocks; ++i) {
+        const int *t = tgt->coords + 3 * i;
+        const long c = cell(t[0], t[1], t[2]);
+        if (h_gC[c] & 2) return err(LGF_EINVAL, "duplicate block in the target set");
+        h_gC[c] |= 2;
+        for (int dz = -nr; dz <= nr; ++dz) h_gC[cell(t[0], t[1], t[2] + dz)] |= 1;   // y-pass candidates
+    }
+    int n1 = 0, n2 = 0;
+    for (int i = 0; i < src->nblocks; ++i)
+        for (int dx = -nr; dx <= nr; ++dx) {
+            const int x = src->coords[3 * i] + dx, y = src->coords[3 * i + 1], z = src->coords[3 * i + 2];
+            const long c = cell(x, y, z);
+            if (h_gX[c]) continue;
+            bool need = false;
+            for (int dy = -nr; dy <= nr && !need; ++dy) {
+                const long q = cell(x, y + dy, z);
+                need = q >= 0 && (h_gC[q] & 1);
+            }
+            if (!need) continue;
+            if (n1 >= kNoAllocMaxInter) return err(LGF_EUNSUPPORTED, "more than 8192 blocks after the x pass");
+            h_x1[3 * n1] = x;
+            h_x1[3 * n1 + 1] = y;
+            h_x1[3 * n1 + 2] = z;
+            h_gX[c] = ++n1;
+        }
+    for (int i = 0; i < tgt->nblocks; ++i)
+        for (int dz = -nr; dz <= nr; ++dz) {
+            const int x = tgt->coords[3 * i], y = tgt->coords[3 * i + 1], z = tgt->coords[3 * i + 2] + dz;
+            const long c = cell(x, y, z);
+            if (h_gY[c]) continue;
+            bool need = false;
+            for (int dy = -nr; dy <= nr && !need; ++dy) {
+                const long q = cell(x, y + dy, z);
+                need = q >= 0 && h_gX[q] > 0;
+            }
+            if (!need) continue;
+            if (n2 >= kNoAllocMaxInter) return err(LGF_EUNSUPPORTED, "more than 8192 blocks after the y pass");
+            h_y2[3 * n2] = x;
+            h_y2[3 * n2 + 1] = y;
+            h_y2[3 * n2 + 2] = z;
+            h_gY[c] = ++n2;
+        }
+    if (n2 == 0) {
+        if (cudaMemsetAsync(u_dev, 0, (size_t)tgt->nblocks * b3 * nf * esz, s) != cudaSuccess)
+            return err(LGF_ECUDA, "cudaMemsetAsync failed");
+        return LGF_OK;
+    }
+    // neighbour tables of the three passes, one after the other
+    const int nout[3] = {n1, n2, tgt->nblocks};
+    const int32_t *outs[3] = {h_x1, h_y2, tgt->coords};
+    const int32_t *grids[3] = {h_gS, h_gX, h_gY};
+    size_t off[3], nn = 0;
+    for (int p = 0; p < 3; ++p) {
+        off[p] = nn;
+        for (int o = 0; o < nout[p]; ++o)
+            for (int d = -nr; d <= nr; ++d) {
+                int c[3] = {outs[p][3 * o], outs[p][3 * o + 1], outs[p][3 * o + 2]};
+                c[p] += d;
+                const long q = cell(c[0], c[1], c[2]);
+                h_nbr[nn++] = q >= 0 ? grids[p][q] - 1 : -1;
+            }
+    }
+    const size_t nbr_bytes = nn * sizeof(int32_t);
+    const size_t x1_off = (4096 + nbr_bytes + 255) & ~size_t(255);
+    const size_t x1_bytes = (size_t)n1 * b3 * nf * esz;
+    const size_t y2_off = (x1_off + x1_bytes + 255) & ~size_t(255);
+    const size_t y2_bytes = (size_t)n2 * b3 * nf * esz;
+    if (y2_off + y2_bytes > kNoAllocBytes)
+        return err(LGF_EUNSUPPORTED, "intermediate fields exceed the 32 MiB scratch array");
+    if (cudaMemcpyAsync(nbr_dev, h_nbr, nbr_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return err(LGF_ECUDA, "neighbour table copy failed");
+    const int lb = log2i(b);
+    const int slab = slab_for(b, R);
+    const int nslab = (b + slab - 1) / slab;
+    const int ntgt = tgt->nblocks, nsrc = src->nblocks;
+    const int64_t istr[3] = {(int64_t)nsrc * (int64_t)b3, (int64_t)n1 * (int64_t)b3, (int64_t)n2 * (int64_t)b3};
+    const int64_t ostr[3] = {(int64_t)n1 * (int64_t)b3, (int64_t)n2 * (int64_t)b3, (int64_t)ntgt * (int64_t)b3};
+    for (int p = 0; p < 3; ++p) {
+        dim3 grid(nout[p], nslab, nf);
+        if (nout[p] == 0) continue;
+        if (prec == LGF_F64) {
+            const size_t smem = sizeof(double) * (((R + 1 + 3) & ~3) + (size_t)slab * b * (b + 2 * R));
+            cudaFuncSetAttribute(k_sep_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            const double *in = p == 0 ? (const double *)f_dev : (const double *)(base + (p == 1 ? x1_off : y2_off));
+            double *o = p == 2 ? (double *)u_dev : (double *)(base + (p == 0 ? x1_off : y2_off));
+            k_sep_pass<double><<<grid, kThreads, smem, s>>>(in, o, nbr_dev + off[p], w64, R, nr, b, lb, p, slab,
+                                                           istr[p], ostr[p]);
+        } else {
+            const size_t smem = sizeof(float) * (((R + 1 + 3) & ~3) + (size_t)slab * b * (b + 2 * R));
+            cudaFuncSetAttribute(k_sep_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            const float *in = p == 0 ? (const float *)f_dev : (const float *)(base + (p == 1 ? x1_off : y2_off));
+            float *o = p == 2 ? (float *)u_dev : (float *)(base + (p == 0 ? x1_off : y2_off));
+            k_sep_pass<float><<<grid, kThreads, smem, s>>>(in, o, nbr_dev + off[p], w32, R, nr, b, lb, p, slab,
+                                                          istr[p], ostr[p]);
+        }
+        if (cudaGetLastError() != cudaSuccess) return err(LGF_ECUDA, "pass kernel launch failed");
+    }
+    return LGF_OK;
+}
