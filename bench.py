@@ -158,9 +158,9 @@ def geometry(p):
     lo, hi = allc.min(0), allc.max(0)
     L = (hi - lo + 1) * b
     M = [32 * 2 ** max(0, math.ceil(math.log2(max(1, 2 * l - 1) / 32))) for l in L]
-    Ls = (p.src.max(0) - p.src.min(0) + 1) * b
-    Lt = (p.tgt.max(0) - p.tgt.min(0) + 1) * b
-    return M, Ls, Lt
+    Ls = [int(v) for v in (p.src.max(0) - p.src.min(0) + 1) * b]
+    Lt = [int(v) for v in (p.tgt.max(0) - p.tgt.min(0) + 1) * b]
+    return [int(m) for m in M], Ls, Lt
 
 
 def algorithmic_bytes(p, nfields: int) -> dict:
@@ -170,7 +170,7 @@ def algorithmic_bytes(p, nfields: int) -> dict:
     K = M[0] // 2 + 1
     c8 = 8  # complex64
     b3 = p.b ** 3
-    nsrc, ntgt = p.src.shape[0], p.tgt.shape[0]
+    nsrc, ntgt = int(p.src.shape[0]), int(p.tgt.shape[0])
     spec = (M[2] // 2 + 1) * (M[1] // 2 + 1) * K * 4
     by = {
         "poisson_x_forward": nfields * (nsrc * b3 * 4 + Ls[2] * Ls[1] * K * c8),
@@ -360,7 +360,7 @@ def run_ours(args, rank, world, dist):
                            kernels=kernels),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "alg_bytes_per_launch": alg[dom], "ms_per_launch": dom_ms,
+                         "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": dom_ms,
                          "traffic": load_traffic(dom)},
             "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks}

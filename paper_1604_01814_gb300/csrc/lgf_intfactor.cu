@@ -38,87 +38,132 @@ inline int64_t pack(int x, int y, int z)
     return (((int64_t)(x + (1 << 20))) << 42) | (((int64_t)(y + (1 << 20))) << 21) | (int64_t)(z + (1 << 20));
 }
 
-// One pass along `ax`.  in/out are field arrays on block sets (stride
-// in_stride / out_stride elements per field).  nbr[o][d] (d = 0..2nr) is the
-// input block at offset d - nr along ax from output block o, or -1.
+// Vectorised pass (block edge and axis fixed at compile time).  The staged
+// region covers the output slab plus a halo of HL >= R points along the
+// axis, HL a multiple of 4, read with 16-byte loads from the neighbour
+// blocks; every thread produces VEC consecutive x outputs with one 16-byte
+// store.  Region layouts (x fastest):
+//   AX 0: [ns][b][E]   AX 1: [ns][E][b]   AX 2: [E][ns][b],   E = b + 2 HL.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_sep_pass(const T *__restrict__ in, T *__restrict__ out,
-                                                        const int *__restrict__ nbr, const T *__restrict__ wg, int R,
-                                                        int nr, int b, int lb, int ax, int slab, int64_t in_stride,
-                                                        int64_t out_stride)
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using V = float4;
+    static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+    using V = double2;
+    static constexpr int N = 2;
+};
+
+template <typename T, int LB, int AX>
+__global__ void __launch_bounds__(kThreads) k_sep_vec(const T *__restrict__ in, T *__restrict__ out,
+                                                       const int *__restrict__ nbr, const T *__restrict__ wg, int R,
+                                                       int HL, int nr, int slab, int64_t in_stride, int64_t out_stride)
 {
+    constexpr int b = 1 << LB, bm = b - 1;
+    using V = typename Vec16<T>::V;
+    constexpr int NV = Vec16<T>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *w = reinterpret_cast<T *>(smem_raw);
     T *s = w + ((R + 1 + 3) & ~3);
     for (int i = threadIdx.x; i <= R; i += blockDim.x) w[i] = wg[i];
     const int o = blockIdx.x;
-    const int s0 = blockIdx.y * slab;            // first slab coordinate
+    const int s0 = blockIdx.y * slab;
     const int ns = min(slab, b - s0);
-    const int ext = b + 2 * R;
+    const int E = b + 2 * HL;
     const int nd = 2 * nr + 1;
     const int *nb = nbr + (int64_t)o * nd;
     const T *inf = in + blockIdx.z * in_stride;
     T *outf = out + blockIdx.z * out_stride;
-    const int bm = b - 1;
-    // Staged region, x fastest:
-    //   ax 0: [ns][b][ext]   (slab over z, lines along x)
-    //   ax 1: [ns][ext][b]   (slab over z, lines along y)
-    //   ax 2: [ext][ns][b]   (slab over y, lines along z)
-    const int total = ns * b * ext;
-    for (int it = threadIdx.x; it < total; it += blockDim.x) {
-        int x, y, z, e;  // e: extended coordinate along ax, in [-R, b + R)
-        if (ax == 0) {
-            e = it % ext - R;
-            y = (it / ext) % b;
-            z = s0 + it / (ext * b);
-            x = e;
-        } else if (ax == 1) {
-            x = it % b;
-            e = (it / b) % ext - R;
-            z = s0 + it / (b * ext);
-            y = e;
-        } else {
-            x = it % b;
-            y = s0 + (it / b) % ns;
-            e = it / (b * ns) - R;
-            z = e;
+    // ---- stage the region with 16-byte loads ----
+    const int rowlen = AX == 0 ? E : b;              // elements per staged row
+    const int nrows = AX == 0 ? ns * b : ns * E;
+    const int vpr = rowlen / NV;
+    const int total = nrows * vpr;
+    constexpr int U = 4;
+    for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+        V v[U];
+        int dst[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int it = base + u * blockDim.x;
+            dst[u] = -1;
+            v[u] = V{};
+            if (it >= total) continue;
+            const int row = it / vpr, cv = it - row * vpr;
+            int x, y, z, e;
+            if (AX == 0) {
+                e = cv * NV - HL;
+                y = row & bm;
+                z = s0 + (row >> LB);
+                x = e & bm;
+            } else if (AX == 1) {
+                x = cv * NV;
+                e = row % E - HL;
+                z = s0 + row / E;
+                y = e & bm;
+            } else {
+                x = cv * NV;
+                y = s0 + row % ns;
+                e = row / ns - HL;
+                z = e & bm;
+            }
+            dst[u] = it * NV;
+            const int bi = nb[(e + nr * b) >> LB];
+            if (bi >= 0)
+                v[u] = *reinterpret_cast<const V *>(inf + ((int64_t)bi << (3 * LB)) + (((z << LB) + y) << LB) + x);
         }
-        const int d = (e + nr * b) >> lb;        // neighbour slot 0..2nr
-        const int bi = nb[d];
-        T v = T(0);
-        if (bi >= 0) {
-            const int xl = ax == 0 ? (e & bm) : x;
-            const int yl = ax == 1 ? (e & bm) : y;
-            const int zl = ax == 2 ? (e & bm) : z;
-            v = inf[((int64_t)bi << (3 * lb)) + (((zl << lb) + yl) << lb) + xl];
-        }
-        s[it] = v;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (dst[u] >= 0) *reinterpret_cast<V *>(s + dst[u]) = v[u];
     }
     __syncthreads();
-    const int nout = ns * b * b;
+    // ---- stencil: NV consecutive x outputs per thread ----
+    const int nout = ns * b * (b / NV);
     for (int it = threadIdx.x; it < nout; it += blockDim.x) {
-        const int x = it & bm;
-        const int y2 = (it >> lb) & bm;          // second fastest output coordinate
-        const int sl = it >> (2 * lb);           // slab-local coordinate
-        int c, st;                               // centre index in s, stride along ax
-        int X, Y, Z;
-        if (ax == 0) {
-            X = x; Y = y2; Z = s0 + sl;
-            c = (sl * b + Y) * ext + (X + R);
+        const int xv = it % (b / NV), rest = it / (b / NV);
+        const int x = xv * NV;
+        const int y2 = rest & bm;          // y for AX 0/1, z for AX 2
+        const int sl = rest >> LB;         // slab-local coordinate
+        int c, st, X = x, Y, Z;
+        if (AX == 0) {
+            Y = y2; Z = s0 + sl;
+            c = (sl * b + Y) * E + (X + HL);
             st = 1;
-        } else if (ax == 1) {
-            X = x; Y = y2; Z = s0 + sl;
-            c = (sl * ext + (Y + R)) * b + X;
+        } else if (AX == 1) {
+            Y = y2; Z = s0 + sl;
+            c = (sl * E + (Y + HL)) * b + X;
             st = b;
         } else {
-            // slab over y: it -> (x, z, y_local)
-            X = x; Z = y2; Y = s0 + sl;
-            c = ((Z + R) * ns + sl) * b + X;
+            Z = y2; Y = s0 + sl;
+            c = ((Z + HL) * ns + sl) * b + X;
             st = ns * b;
         }
-        T acc = w[0] * s[c];
-        for (int k = 1; k <= R; ++k) acc += w[k] * (s[c - k * st] + s[c + k * st]);
-        outf[((int64_t)o << (3 * lb)) + (((Z << lb) + Y) << lb) + X] = acc;
+        T acc[NV];
+        const T w0 = w[0];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = w0 * s[c + v];
+        for (int k = 1; k <= R; ++k) {
+            const T wk = w[k];
+            if (AX == 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] += wk * (s[c + v - k] + s[c + v + k]);
+            } else {
+                const V lo = *reinterpret_cast<const V *>(s + c - k * st);
+                const V hi = *reinterpret_cast<const V *>(s + c + k * st);
+                const T *l = reinterpret_cast<const T *>(&lo);
+                const T *h = reinterpret_cast<const T *>(&hi);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] += wk * (l[v] + h[v]);
+            }
+        }
+        V r;
+        T *rr = reinterpret_cast<T *>(&r);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) rr[v] = acc[v];
+        *reinterpret_cast<V *>(outf + ((int64_t)o << (3 * LB)) + (((Z << LB) + Y) << LB) + X) = r;
     }
 }
 
@@ -126,19 +171,6 @@ __global__ void k_to_float(const double *a, float *b, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
-}
-
-int log2i(int v)
-{
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-}
-
-int slab_for(int b, int R)
-{
-    const int per = b * (b + 2 * R);
-    return std::max(1, std::min(b, kSlabElems / per));
 }
 
 }  // namespace
@@ -294,34 +326,85 @@ lgf_status intf_prepare_scratch(lgf_ctx *ctx, const IntfPlan *pl, int nfields)
     return ensure_scratch(ctx, &ctx->scrB, &ctx->scrB_bytes, std::max<size_t>(1, pl->n2) * b3 * nfields * esz);
 }
 
+// Region staging parameters shared by both launch paths.
+struct SepGeom {
+    int HL;      // halo, a multiple of 4 and >= R (<= nr * b)
+    int slab;    // slab extent (planes of the slab axis per CTA)
+    int nslab;
+};
+
+SepGeom sep_geom(int b, int R, int nr)
+{
+    SepGeom g;
+    g.HL = std::min(((R + 3) / 4) * 4, nr * b);
+    const int E = b + 2 * g.HL;
+    g.slab = std::max(1, std::min(b, kSlabElems / (b * E)));
+    g.nslab = (b + g.slab - 1) / g.slab;
+    return g;
+}
+
+template <typename T, int LB, int AX>
+lgf_status launch_sep_lb(lgf_ctx *ctx, dim3 grid, size_t smem, cudaStream_t s, const T *in, T *out, const int *nbr,
+                         const T *w, int R, int HL, int nr, int slab, int64_t istr, int64_t ostr)
+{
+    auto kern = k_sep_vec<T, LB, AX>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    }
+    kern<<<grid, kThreads, smem, s>>>(in, out, nbr, w, R, HL, nr, slab, istr, ostr);
+    return LGF_OK;
+}
+
+template <typename T, int AX>
+lgf_status launch_sep_ax(lgf_ctx *ctx, int b, dim3 grid, size_t smem, cudaStream_t s, const T *in, T *out,
+                         const int *nbr, const T *w, int R, int HL, int nr, int slab, int64_t istr, int64_t ostr)
+{
+    switch (b) {
+    case 4: return launch_sep_lb<T, 2, AX>(ctx, grid, smem, s, in, out, nbr, w, R, HL, nr, slab, istr, ostr);
+    case 8: return launch_sep_lb<T, 3, AX>(ctx, grid, smem, s, in, out, nbr, w, R, HL, nr, slab, istr, ostr);
+    case 16: return launch_sep_lb<T, 4, AX>(ctx, grid, smem, s, in, out, nbr, w, R, HL, nr, slab, istr, ostr);
+    case 32: return launch_sep_lb<T, 5, AX>(ctx, grid, smem, s, in, out, nbr, w, R, HL, nr, slab, istr, ostr);
+    default: return launch_sep_lb<T, 6, AX>(ctx, grid, smem, s, in, out, nbr, w, R, HL, nr, slab, istr, ostr);
+    }
+}
+
+// One separable pass along axis `ax` for `nout` output blocks.
+template <typename T>
+lgf_status launch_sep(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
+                      const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr)
+{
+    const SepGeom sg = sep_geom(b, R, nr);
+    const size_t smem = sizeof(T) * (((R + 1 + 3) & ~3) + (size_t)sg.slab * b * (b + 2 * sg.HL));
+    dim3 grid(nout, sg.nslab, nfields);
+    lgf_status st;
+    if (ax == 0) st = launch_sep_ax<T, 0>(ctx, b, grid, smem, s, in, out, nbr, w, R, sg.HL, nr, sg.slab, istr, ostr);
+    else if (ax == 1) st = launch_sep_ax<T, 1>(ctx, b, grid, smem, s, in, out, nbr, w, R, sg.HL, nr, sg.slab, istr, ostr);
+    else st = launch_sep_ax<T, 2>(ctx, b, grid, smem, s, in, out, nbr, w, R, sg.HL, nr, sg.slab, istr, ostr);
+    if (st != LGF_OK) return st;
+    LGF_CHECK_LAUNCH(ctx, "intfactor pass");
+    return LGF_OK;
+}
+
 template <typename T>
 static lgf_status run_sep(lgf_ctx *ctx, IntfPlan *pl, const T *w, int R, const T *f, T *u, int nfields,
                           cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
-        LGF_CUDA(ctx, cudaFuncSetAttribute(k_sep_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
-    const int b = pl->b, lb = log2i(b), nr = pl->nr;
+    const int b = pl->b, nr = pl->nr;
     const int64_t b3 = (int64_t)b * b * b;
-    const int slab = slab_for(b, R);
-    const int nslab = (b + slab - 1) / slab;
-    const size_t smem = sizeof(T) * (((R + 1 + 3) & ~3) + (size_t)slab * b * (b + 2 * R));
     const int nsrc = (int)(pl->src.size() / 3), ntgt = (int)(pl->tgt.size() / 3);
     T *X1 = (T *)ctx->scrA, *Y2 = (T *)ctx->scrB;
     const T *ins[3] = {f, X1, Y2};
     T *outs[3] = {X1, Y2, u};
     const int64_t istr[3] = {nsrc * b3, pl->n1 * b3, pl->n2 * b3};
     const int64_t ostr[3] = {pl->n1 * b3, pl->n2 * b3, ntgt * b3};
+    static const char *names[3] = {"intfactor_pass_x", "intfactor_pass_y", "intfactor_pass_z"};
     for (int p = 0; p < 3; ++p) {
         if (pl->pass[p].nout == 0) continue;
-        dim3 grid(pl->pass[p].nout, nslab, nfields);
-        static const char *names[3] = {"intfactor_pass_x", "intfactor_pass_y", "intfactor_pass_z"};
         const int ph = prof_begin(ctx, s, names[p]);
-        k_sep_pass<T><<<grid, kThreads, smem, s>>>(ins[p], outs[p], pl->pass[p].nbr_dev, w, R, nr, b, lb, p, slab,
-                                                   istr[p], ostr[p]);
-        LGF_CHECK_LAUNCH(ctx, "intfactor pass");
+        lgf_status st = launch_sep<T>(ctx, p, b, pl->pass[p].nout, nfields, s, ins[p], outs[p], pl->pass[p].nbr_dev, w,
+                                      R, nr, istr[p], ostr[p]);
+        if (st != LGF_OK) return st;
         prof_end(ctx, s, ph);
     }
     return LGF_OK;
@@ -555,31 +638,24 @@ extern "C" LGF_API lgf_status lgf_intfactor_apply_noalloc(int32_t prec, double t
         return err(LGF_EUNSUPPORTED, "intermediate fields exceed the 32 MiB scratch array");
     if (cudaMemcpyAsync(nbr_dev, h_nbr, nbr_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return err(LGF_ECUDA, "neighbour table copy failed");
-    const int lb = log2i(b);
-    const int slab = slab_for(b, R);
-    const int nslab = (b + slab - 1) / slab;
     const int ntgt = tgt->nblocks, nsrc = src->nblocks;
     const int64_t istr[3] = {(int64_t)nsrc * (int64_t)b3, (int64_t)n1 * (int64_t)b3, (int64_t)n2 * (int64_t)b3};
     const int64_t ostr[3] = {(int64_t)n1 * (int64_t)b3, (int64_t)n2 * (int64_t)b3, (int64_t)ntgt * (int64_t)b3};
     for (int p = 0; p < 3; ++p) {
-        dim3 grid(nout[p], nslab, nf);
         if (nout[p] == 0) continue;
+        lgf_status st;
         if (prec == LGF_F64) {
-            const size_t smem = sizeof(double) * (((R + 1 + 3) & ~3) + (size_t)slab * b * (b + 2 * R));
-            cudaFuncSetAttribute(k_sep_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             const double *in = p == 0 ? (const double *)f_dev : (const double *)(base + (p == 1 ? x1_off : y2_off));
             double *o = p == 2 ? (double *)u_dev : (double *)(base + (p == 0 ? x1_off : y2_off));
-            k_sep_pass<double><<<grid, kThreads, smem, s>>>(in, o, nbr_dev + off[p], w64, R, nr, b, lb, p, slab,
-                                                           istr[p], ostr[p]);
+            st = launch_sep<double>(nullptr, p, b, nout[p], nf, s, in, o, nbr_dev + off[p], w64, R, nr, istr[p],
+                                    ostr[p]);
         } else {
-            const size_t smem = sizeof(float) * (((R + 1 + 3) & ~3) + (size_t)slab * b * (b + 2 * R));
-            cudaFuncSetAttribute(k_sep_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             const float *in = p == 0 ? (const float *)f_dev : (const float *)(base + (p == 1 ? x1_off : y2_off));
             float *o = p == 2 ? (float *)u_dev : (float *)(base + (p == 0 ? x1_off : y2_off));
-            k_sep_pass<float><<<grid, kThreads, smem, s>>>(in, o, nbr_dev + off[p], w32, R, nr, b, lb, p, slab,
-                                                          istr[p], ostr[p]);
+            st = launch_sep<float>(nullptr, p, b, nout[p], nf, s, in, o, nbr_dev + off[p], w32, R, nr, istr[p],
+                                   ostr[p]);
         }
-        if (cudaGetLastError() != cudaSuccess) return err(LGF_ECUDA, "pass kernel launch failed");
+        if (st != LGF_OK) return err(LGF_ECUDA, "pass kernel launch failed");
     }
     return LGF_OK;
 }

@@ -25,7 +25,7 @@
 #include <cstring>
 #include <unordered_map>
 
-#include "lgf_internal.cuh"
+#include "lgf_poisson_kernels.cuh"
 
 namespace lgf {
 
@@ -61,11 +61,6 @@ PoissonPlan::~PoissonPlan()
 
 namespace {
 
-constexpr int kThreads = 256;
-
-// Elements (complex) a CTA keeps in shared memory for its lines.
-constexpr int kElemsPerCta = 4096;
-
 __global__ void k_twiddles(int M, void *out, int dbl)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,241 +71,6 @@ __global__ void k_twiddles(int M, void *out, int dbl)
         ((Cx<double> *)out)[m] = {c, s};
     } else {
         ((Cx<float> *)out)[m] = {(float)c, (float)s};
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ T fetch_src(const T *__restrict__ f, const PoissonGeom &g, int lb, int x, int y, int z,
-                                       int dense_ld)
-{
-    if (dense_ld) return f[((int64_t)z * g.M[1] + y) * dense_ld + x];
-    const int xr = x - g.s0[0], yr = y - g.s0[1], zr = z - g.s0[2];
-    const int bi = g.srcmap[((zr >> lb) * g.nbs[1] + (yr >> lb)) * g.nbs[0] + (xr >> lb)];
-    if (bi < 0) return T(0);
-    const int m = g.b - 1;
-    return f[((int64_t)bi << (3 * lb)) + ((((zr & m) << lb) + (yr & m)) << lb) + (xr & m)];
-}
-
-// X forward: rows (y, y+1) of plane z packed as one complex line of length Mx.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xfwd(const T *__restrict__ f, Cx<T> *__restrict__ A, PoissonGeom g,
-                                                    FftShape sh, const Cx<T> *__restrict__ twg, int lines,
-                                                    int npairs, int lb, int dense_ld)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *s = tw + sh.M;
-    const int M = sh.M;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = twg[i];
-    const T *ff = f + blockIdx.y * g.fstride;
-    Cx<T> *AA = A + blockIdx.y * g.Astride;
-    const int pair0 = blockIdx.x * lines;
-    const int nl = min(lines, npairs - pair0);
-    const RowAddr ad{M + M / 16};
-    const int hp = g.Ls[1] >> 1;
-    for (int it = threadIdx.x; it < lines * M; it += blockDim.x) {
-        const int l = it / M, x = it - l * M;
-        Cx<T> v{T(0), T(0)};
-        if (l < nl && x >= g.s0[0] && x < g.s0[0] + g.Ls[0]) {
-            const int p = pair0 + l, zi = p / hp, yi = 2 * (p - zi * hp);
-            const int y = g.s0[1] + yi, z = g.s0[2] + zi;
-            v.x = fetch_src(ff, g, lb, x, y, z, dense_ld);
-            v.y = fetch_src(ff, g, lb, x, y + 1, z, dense_ld);
-        }
-        s[ad(l, x)] = v;
-    }
-    __syncthreads();
-    fft_forward<false>(s, ad, lines, sh, tw);
-    const int K = g.Kx;
-    for (int it = threadIdx.x; it < nl * K; it += blockDim.x) {
-        const int l = it / K, k = it - l * K;
-        const Cx<T> zk = s[ad(l, pos_of_freq(k, sh))];
-        const Cx<T> zm = s[ad(l, pos_of_freq((M - k) & (M - 1), sh))];
-        // rows y and y+1: (Z[k] + conj Z[M-k]) / 2 and (Z[k] - conj Z[M-k]) / 2i
-        const Cx<T> f1{T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
-        const Cx<T> f2{T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
-        const int p = pair0 + l, zi = p / hp, yi = 2 * (p - zi * hp);
-        Cx<T> *row = AA + ((int64_t)zi * g.ldA_y + yi) * K;
-        row[k] = f1;
-        row[K + k] = f2;
-    }
-}
-
-// Y forward over the source z-planes, W columns of kx per CTA.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_yfwd(const Cx<T> *__restrict__ A, Cx<T> *__restrict__ B, PoissonGeom g,
-                                                    FftShape sh, const Cx<T> *__restrict__ twg, int W)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *s = tw + sh.M;
-    const int M = sh.M;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = twg[i];
-    const int zi = blockIdx.y;
-    const int kx0 = blockIdx.x * W;
-    const int K = g.Kx;
-    const Cx<T> *AA = A + blockIdx.z * g.Astride + (int64_t)zi * g.ldA_y * K;
-    Cx<T> *BB = B + blockIdx.z * g.Bstride + (int64_t)zi * M * K;
-    const ColAddr ad{W};
-    for (int it = threadIdx.x; it < W * M; it += blockDim.x) {
-        const int m = it / W, w = it - m * W;
-        const int kx = kx0 + w;
-        Cx<T> v{T(0), T(0)};
-        if (kx < K && m >= g.s0[1] && m < g.s0[1] + g.Ls[1]) v = AA[(int64_t)(m - g.s0[1]) * K + kx];
-        s[ad(w, m)] = v;
-    }
-    __syncthreads();
-    fft_forward<true>(s, ad, W, sh, tw);
-    for (int it = threadIdx.x; it < W * M; it += blockDim.x) {
-        const int ky = it / W, w = it - ky * W;
-        const int kx = kx0 + w;
-        if (kx < K) BB[(int64_t)ky * K + kx] = s[ad(w, pos_of_freq(ky, sh))];
-    }
-}
-
-// Z: forward along z, times the real even kernel spectrum, inverse along z.
-// mode 0: keep target planes (in place).  mode 1: spectrum build -- forward
-// only, every plane stored in natural order.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_zconv(Cx<T> *__restrict__ B, PoissonGeom g, FftShape sh,
-                                                     const Cx<T> *__restrict__ twg, const T *__restrict__ spec,
-                                                     int W, int mode)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *s = tw + sh.M;
-    const int M = sh.M;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = twg[i];
-    const int ky = blockIdx.y;
-    const int kx0 = blockIdx.x * W;
-    const int K = g.Kx;
-    const int My = g.M[1];
-    const int64_t plane = (int64_t)My * K;
-    Cx<T> *BB = B + blockIdx.z * g.Bstride + (int64_t)ky * K;
-    const ColAddr ad{W};
-    for (int it = threadIdx.x; it < W * M; it += blockDim.x) {
-        const int m = it / W, w = it - m * W;
-        const int kx = kx0 + w;
-        Cx<T> v{T(0), T(0)};
-        if (kx < K && m >= g.s0[2] && m < g.s0[2] + g.Ls[2]) v = BB[(int64_t)(m - g.s0[2]) * plane + kx];
-        s[ad(w, m)] = v;
-    }
-    __syncthreads();
-    fft_forward<true>(s, ad, W, sh, tw);
-    if (mode == 1) {
-        for (int it = threadIdx.x; it < W * M; it += blockDim.x) {
-            const int kz = it / W, w = it - kz * W;
-            const int kx = kx0 + w;
-            if (kx < K) BB[(int64_t)kz * plane + kx] = s[ad(w, pos_of_freq(kz, sh))];
-        }
-        return;
-    }
-    const int kyr = min(ky, My - ky);
-    const int Khy = My / 2 + 1, Khz = M / 2 + 1;
-    for (int it = threadIdx.x; it < W * M; it += blockDim.x) {
-        const int P = it / W, w = it - P * W;
-        const int kx = kx0 + w;
-        const int kz = freq_of_pos(P, sh);
-        const int kzr = min(kz, M - kz);
-        const T gk = (kx < K) ? spec[((int64_t)kzr * Khy + kyr) * K + kx] : T(0);
-        Cx<T> v = s[ad(w, P)];
-        v.x *= gk;
-        v.y *= gk;
-        s[ad(w, P)] = v;
-    }
-    (void)Khz;
-    __syncthreads();
-    fft_inverse<true>(s, ad, W, sh, tw);
-    for (int it = threadIdx.x; it < W * g.Lt[2]; it += blockDim.x) {
-        const int zi = it / W, w = it - zi * W;
-        const int kx = kx0 + w;
-        if (kx < K) BB[(int64_t)zi * plane + kx] = s[ad(w, g.t0[2] + zi)];
-    }
-}
-
-// Y inverse over the target z-planes, keeping the target rows.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_yinv(const Cx<T> *__restrict__ B, Cx<T> *__restrict__ A, PoissonGeom g,
-                                                    FftShape sh, const Cx<T> *__restrict__ twg, int W)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *s = tw + sh.M;
-    const int M = sh.M;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = twg[i];
-    const int zi = blockIdx.y;
-    const int kx0 = blockIdx.x * W;
-    const int K = g.Kx;
-    const Cx<T> *BB = B + blockIdx.z * g.Bstride + (int64_t)zi * M * K;
-    Cx<T> *AA = A + blockIdx.z * g.Astride + (int64_t)zi * g.ldA_y * K;
-    const ColAddr ad{W};
-    for (int it = threadIdx.x; it < W * M; it += blockDim.x) {
-        const int ky = it / W, w = it - ky * W;
-        const int kx = kx0 + w;
-        Cx<T> v{T(0), T(0)};
-        if (kx < K) v = BB[(int64_t)ky * K + kx];
-        s[ad(w, pos_of_freq(ky, sh))] = v;
-    }
-    __syncthreads();
-    fft_inverse<true>(s, ad, W, sh, tw);
-    for (int it = threadIdx.x; it < W * g.Lt[1]; it += blockDim.x) {
-        const int yi = it / W, w = it - yi * W;
-        const int kx = kx0 + w;
-        if (kx < K) AA[(int64_t)yi * K + kx] = s[ad(w, g.t0[1] + yi)];
-    }
-}
-
-// X inverse (C2R): rows (y, y+1) of the target region from one complex line.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xinv(const Cx<T> *__restrict__ A, T *__restrict__ u, PoissonGeom g,
-                                                    FftShape sh, const Cx<T> *__restrict__ twg, int lines,
-                                                    int npairs, int lb)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *s = tw + sh.M;
-    const int M = sh.M;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = twg[i];
-    const int K = g.Kx;
-    const Cx<T> *AA = A + blockIdx.y * g.Astride;
-    T *uu = u + blockIdx.y * g.ustride;
-    const int pair0 = blockIdx.x * lines;
-    const int nl = min(lines, npairs - pair0);
-    const RowAddr ad{M + M / 16};
-    const int hp = g.Lt[1] >> 1;
-    for (int it = threadIdx.x; it < lines * M; it += blockDim.x) {
-        const int l = it / M, k = it - l * M;
-        Cx<T> v{T(0), T(0)};
-        if (l < nl) {
-            const int p = pair0 + l, zi = p / hp, yi = 2 * (p - zi * hp);
-            const Cx<T> *row = AA + ((int64_t)zi * g.ldA_y + yi) * K;
-            if (k <= M / 2) {
-                Cx<T> g1 = row[k], g2 = row[K + k];
-                if (k == 0 || k == M / 2) {
-                    g1.y = T(0);
-                    g2.y = T(0);
-                }
-                v = {g1.x - g2.y, g1.y + g2.x};
-            } else {
-                const Cx<T> g1 = row[M - k], g2 = row[K + M - k];
-                v = {g1.x + g2.y, g2.x - g1.y};
-            }
-        }
-        s[ad(l, pos_of_freq(k, sh))] = v;
-    }
-    __syncthreads();
-    fft_inverse<false>(s, ad, lines, sh, tw);
-    const T sc = T(g.scale);
-    const int Lx = g.Lt[0];
-    const int m = g.b - 1;
-    for (int it = threadIdx.x; it < nl * 2 * Lx; it += blockDim.x) {
-        const int l = it / (2 * Lx), r = it - l * 2 * Lx;
-        const int half = r / Lx, xi = r - half * Lx;
-        const int p = pair0 + l, zi = p / hp, yi = 2 * (p - zi * hp) + half;
-        const int bi = g.tgtmap[((zi >> lb) * g.nbt[1] + (yi >> lb)) * g.nbt[0] + (xi >> lb)];
-        if (bi < 0) continue;
-        const Cx<T> v = s[ad(l, g.t0[0] + xi)];
-        uu[((int64_t)bi << (3 * lb)) + ((((zi & m) << lb) + (yi & m)) << lb) + (xi & m)] = sc * (half ? v.y : v.x);
     }
 }
 
@@ -337,48 +97,14 @@ int log2i(int v)
     return l;
 }
 
-struct LaunchCfg {
-    int lines_x;   // row lines per CTA (X passes)
-    int W;         // columns per CTA (Y, Z passes)
-};
-
-LaunchCfg cfg_for(int M)
-{
-    LaunchCfg c;
-    c.lines_x = std::max(1, kElemsPerCta / M);
-    c.W = std::min(16, std::max(4, kElemsPerCta / M));
-    return c;
-}
-
-template <typename T>
-size_t smem_rows(int M, int lines) { return sizeof(Cx<T>) * ((size_t)M + (size_t)lines * (M + M / 16)); }
-template <typename T>
-size_t smem_cols(int M, int W) { return sizeof(Cx<T>) * ((size_t)M + (size_t)W * M); }
-
-template <typename T>
-lgf_status set_smem_limits(lgf_ctx *ctx)
-{
-    static bool done = false;
-    if (done) return LGF_OK;
-    const int big = 200 * 1024;
-    LGF_CUDA(ctx, cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    LGF_CUDA(ctx, cudaFuncSetAttribute(k_yfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    LGF_CUDA(ctx, cudaFuncSetAttribute(k_zconv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    LGF_CUDA(ctx, cudaFuncSetAttribute(k_yinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    LGF_CUDA(ctx, cudaFuncSetAttribute(k_xinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    done = true;
-    return LGF_OK;
-}
-
-// Launch the five passes for `nfields` fields of one problem.
+// The five passes of one problem (all fields in each launch); in spectrum
+// mode only the forward transform of a dense box (x, y, then z in place).
 template <typename T>
 lgf_status run_passes(lgf_ctx *ctx, const PoissonGeom &g, const T *f, T *u, Cx<T> *A, Cx<T> *B, const T *spec,
-                      int nfields, int dense_ld, bool spectrum_mode, cudaStream_t s)
+                      int nf, int dense_ld, bool spectrum_mode, cudaStream_t s)
 {
-    lgf_status st = set_smem_limits<T>(ctx);
-    if (st != LGF_OK) return st;
     const bool dbl = sizeof(T) == 8;
-    const FftShape shx = make_fft_shape(g.M[0]), shy = make_fft_shape(g.M[1]), shz = make_fft_shape(g.M[2]);
+    lgf_status st = LGF_OK;
     const Cx<T> *twx = (const Cx<T> *)twiddles(ctx, g.M[0], dbl, &st);
     if (st != LGF_OK) return st;
     const Cx<T> *twy = (const Cx<T> *)twiddles(ctx, g.M[1], dbl, &st);
@@ -386,55 +112,21 @@ lgf_status run_passes(lgf_ctx *ctx, const PoissonGeom &g, const T *f, T *u, Cx<T
     const Cx<T> *twz = (const Cx<T> *)twiddles(ctx, g.M[2], dbl, &st);
     if (st != LGF_OK) return st;
     const int lb = log2i(g.b);
-    const LaunchCfg cx = cfg_for(g.M[0]), cy = cfg_for(g.M[1]), cz = cfg_for(g.M[2]);
-    const int K = g.Kx;
-
-    // X forward
-    {
-        const int npairs = (g.Ls[1] / 2) * g.Ls[2];
-        dim3 grid((npairs + cx.lines_x - 1) / cx.lines_x, nfields);
-        const int ph = prof_begin(ctx, s, "poisson_x_forward");
-        k_xfwd<T><<<grid, kThreads, smem_rows<T>(g.M[0], cx.lines_x), s>>>(f, A, g, shx, twx, cx.lines_x, npairs, lb,
-                                                                          dense_ld);
-        LGF_CHECK_LAUNCH(ctx, "poisson x-forward");
-        prof_end(ctx, s, ph);
-    }
-    // Y forward
-    {
-        dim3 grid((K + cy.W - 1) / cy.W, g.Ls[2], nfields);
-        const int ph = prof_begin(ctx, s, "poisson_y_forward");
-        k_yfwd<T><<<grid, kThreads, smem_cols<T>(g.M[1], cy.W), s>>>(A, B, g, shy, twy, cy.W);
-        LGF_CHECK_LAUNCH(ctx, "poisson y-forward");
-        prof_end(ctx, s, ph);
-    }
-    // Z forward, multiply, inverse
-    {
-        dim3 grid((K + cz.W - 1) / cz.W, g.M[1], nfields);
-        const int ph = prof_begin(ctx, s, spectrum_mode ? "spectrum_z_forward" : "poisson_z_convolve");
-        k_zconv<T><<<grid, kThreads, smem_cols<T>(g.M[2], cz.W), s>>>(B, g, shz, twz, spec, cz.W,
-                                                                      spectrum_mode ? 1 : 0);
-        LGF_CHECK_LAUNCH(ctx, "poisson z-convolve");
-        prof_end(ctx, s, ph);
-    }
-    if (spectrum_mode) return LGF_OK;
-    // Y inverse
-    {
-        dim3 grid((K + cy.W - 1) / cy.W, g.Lt[2], nfields);
-        const int ph = prof_begin(ctx, s, "poisson_y_inverse");
-        k_yinv<T><<<grid, kThreads, smem_cols<T>(g.M[1], cy.W), s>>>(B, A, g, shy, twy, cy.W);
-        LGF_CHECK_LAUNCH(ctx, "poisson y-inverse");
-        prof_end(ctx, s, ph);
-    }
-    // X inverse
-    {
-        const int npairs = (g.Lt[1] / 2) * g.Lt[2];
-        dim3 grid((npairs + cx.lines_x - 1) / cx.lines_x, nfields);
-        const int ph = prof_begin(ctx, s, "poisson_x_inverse");
-        k_xinv<T><<<grid, kThreads, smem_rows<T>(g.M[0], cx.lines_x), s>>>(A, u, g, shx, twx, cx.lines_x, npairs, lb);
-        LGF_CHECK_LAUNCH(ctx, "poisson x-inverse");
-        prof_end(ctx, s, ph);
-    }
-    return LGF_OK;
+    const int K = g.Kx, My = g.M[1], Mz = g.M[2];
+    const int64_t planeA = (int64_t)g.ldA_y * K, planeB = (int64_t)My * K;
+    if ((st = launch_row_forward<T>(ctx, g, f, A, twx, nf, lb, dense_ld, s)) != LGF_OK) return st;
+    if ((st = launch_col_forward<T>(ctx, My, K, g.Ls[2], nf, A, B, g.s0[1], g.Ls[1], K, K, planeA, planeB, g.Astride,
+                                    g.Bstride, twy, s, spectrum_mode ? "spectrum_y_forward" : "poisson_y_forward")) !=
+        LGF_OK)
+        return st;
+    if (spectrum_mode)
+        return launch_col_forward<T>(ctx, Mz, K, My, nf, B, B, 0, Mz, planeB, planeB, K, K, g.Bstride, g.Bstride, twz,
+                                     s, "spectrum_z_forward");
+    if ((st = launch_col_convolve<T>(ctx, g, B, spec, twz, nf, s)) != LGF_OK) return st;
+    if ((st = launch_col_inverse<T>(ctx, My, K, g.Lt[2], nf, B, A, g.t0[1], g.Lt[1], K, K, planeB, planeA, g.Bstride,
+                                    g.Astride, twy, s, "poisson_y_inverse")) != LGF_OK)
+        return st;
+    return launch_row_inverse<T>(ctx, g, A, u, twx, nf, lb, s);
 }
 
 }  // namespace

@@ -1,0 +1,742 @@
+// Pass kernels of the Poisson apply, specialised on the transform length.
+//
+// Every length M = 2^LOGM (32..4096) has a fixed plan of two or three DIF
+// stages (radix <= 16), see Plan below.  A line (a column of W adjacent kx
+// values, or one packed pair of x rows) is handled by TPC threads:
+//   - the first forward stage loads its operands straight from global memory
+//     into registers (all loads of a thread in flight together), does the
+//     butterflies and writes the stage result to shared memory;
+//   - the middle stage (three-stage plans only) works in shared memory;
+//   - the last forward stage reads shared memory into registers; its outputs
+//     are final spectrum values, stored straight to global memory (y pass) or
+//     multiplied by the kernel spectrum and sent straight into the first
+//     inverse stage (z pass).
+// The inverse sweep mirrors this (adjoint stages, conjugate twiddles).  One
+// shared-memory transpose per stage boundary, one __syncthreads per boundary.
+#pragma once
+#include "lgf_internal.cuh"
+
+namespace lgf {
+namespace pk {
+
+template <int LOGM>
+struct Plan {
+    static constexpr int M = 1 << LOGM;
+    static constexpr int NST = LOGM <= 8 ? 2 : 3;
+    static constexpr int LG0 = (LOGM == 5 || LOGM == 6 || LOGM == 9) ? 3 : 4;
+    static constexpr int LG1 = LOGM == 5 ? 2 : (LOGM == 6 || LOGM == 7 || LOGM == 9 || LOGM == 10) ? 3 : 4;
+    static constexpr int LG2 = NST == 3 ? LOGM - LG0 - LG1 : 0;
+    static constexpr int LGL = NST == 3 ? LG2 : LG1;             // last stage
+    static constexpr int LOGN1 = LOGM - LG0;                      // sub-problem size entering stage 1
+    static constexpr int G0 = M >> LG0, G1 = M >> LG1, G2 = NST == 3 ? (M >> LG2) : (1 << 30);
+    static constexpr int TPC = G0 < G1 ? (G0 < G2 ? G0 : G2) : (G1 < G2 ? G1 : G2);
+    static constexpr int GL = M >> LGL;                           // groups of the last stage
+    static_assert(LG0 + LG1 + LG2 == LOGM, "plan must cover the length");
+};
+
+// Position of frequency k after the forward sweep, and back.
+template <int LOGM>
+__device__ __forceinline__ int pos_of(int k)
+{
+    using P = Plan<LOGM>;
+    const int q0 = k & ((1 << P::LG0) - 1);
+    k >>= P::LG0;
+    const int q1 = k & ((1 << P::LG1) - 1);
+    k >>= P::LG1;
+    int pos = (q0 << (LOGM - P::LG0)) + (q1 << (LOGM - P::LG0 - P::LG1));
+    if (P::NST == 3) pos += k;   // k now holds q2
+    return pos;
+}
+
+template <int LOGM>
+__device__ __forceinline__ int freq_of(int pos)
+{
+    using P = Plan<LOGM>;
+    const int q0 = pos >> (LOGM - P::LG0);
+    const int r0 = pos & ((1 << (LOGM - P::LG0)) - 1);
+    const int q1 = r0 >> (LOGM - P::LG0 - P::LG1);
+    const int q2 = r0 & ((1 << (LOGM - P::LG0 - P::LG1)) - 1);
+    return q0 + (q1 << P::LG0) + (q2 << (P::LG0 + P::LG1));
+}
+
+// Forward butterfly of one group: DFT then twiddles w_N^{j q} (none when the
+// stage is the last one, N = R).
+template <int LOGM, int LOGN, int LOGR, typename T>
+__device__ __forceinline__ void dif_group(Cx<T> *a, int j, const Cx<T> *tw)
+{
+    constexpr int R = 1 << LOGR;
+    Dft<R, -1, T>::run(a);
+    if constexpr (LOGN > LOGR) {
+#pragma unroll
+        for (int q = 1; q < R; ++q) a[q] = cmul(a[q], tw[(j * q) << (LOGM - LOGN)]);
+    }
+}
+
+template <int LOGM, int LOGN, int LOGR, typename T>
+__device__ __forceinline__ void dit_group(Cx<T> *a, int j, const Cx<T> *tw)
+{
+    constexpr int R = 1 << LOGR;
+    if constexpr (LOGN > LOGR) {
+#pragma unroll
+        for (int q = 1; q < R; ++q) a[q] = cmulc(a[q], tw[(j * q) << (LOGM - LOGN)]);
+    }
+    Dft<R, 1, T>::run(a);
+}
+
+// Middle stage (three-stage plans): shared memory to shared memory.
+template <int LOGM, int DIR, typename T, class Addr>
+__device__ __forceinline__ void middle_stage(Cx<T> *s, const Addr &ad, int line, int t, const Cx<T> *tw)
+{
+    using P = Plan<LOGM>;
+    if constexpr (P::NST == 3) {
+        constexpr int LOGN = P::LOGN1, LOGR = P::LG1, R = 1 << LOGR;
+        constexpr int LOGNP = LOGN - LOGR;
+#pragma unroll
+        for (int g = t; g < P::G1; g += P::TPC) {
+            const int sub = g >> LOGNP, j = g & ((1 << LOGNP) - 1), o = sub << LOGN;
+            Cx<T> a[R];
+            if (DIR < 0) {
+#pragma unroll
+                for (int p = 0; p < R; ++p) a[p] = s[ad(line, o + j + (p << LOGNP))];
+                dif_group<LOGM, LOGN, LOGR>(a, j, tw);
+#pragma unroll
+                for (int q = 0; q < R; ++q) s[ad(line, o + (q << LOGNP) + j)] = a[q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < R; ++q) a[q] = s[ad(line, o + (q << LOGNP) + j)];
+                dit_group<LOGM, LOGN, LOGR>(a, j, tw);
+#pragma unroll
+                for (int p = 0; p < R; ++p) s[ad(line, o + j + (p << LOGNP))] = a[p];
+            }
+        }
+    }
+}
+
+// Shared-memory layouts.
+struct ColAddrW {   // element m of column w: m * W + w
+    int W;
+    __device__ __forceinline__ int operator()(int w, int m) const { return m * W + w; }
+};
+struct RowAddrP {   // element m of line l: l * ld + m + m / 16
+    int ld;
+    __device__ __forceinline__ int operator()(int l, int m) const { return l * ld + m + (m >> 4); }
+};
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(Cx<T> *tw, const Cx<T> *__restrict__ twg, int M)
+{
+    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = twg[i];
+}
+
+// ---------------------------------------------------------------------------
+// Column passes.  Data in global memory: rows of K complex values (kx), row
+// `r` of the current column set at base + r * rs.  A CTA owns W adjacent kx.
+// ---------------------------------------------------------------------------
+
+// Forward along the column: rows [lo, lo + n) hold data (row m at
+// in + (m - lo) * rs), others are zero; the spectrum (natural order) goes to
+// out + k * os.  Used by the y pass and by the spectrum build's z pass.
+template <typename T, int LOGM, int W>
+__global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
+                                                                     int K, int lo, int n, int64_t rs, int64_t os,
+                                                                     int64_t in_plane, int64_t out_plane,
+                                                                     int64_t in_field, int64_t out_field,
+                                                                     const Cx<T> *__restrict__ twg)
+{
+    using P = Plan<LOGM>;
+    constexpr int M = P::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *s = tw + M;
+    load_twiddles(tw, twg, M);
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int kx = blockIdx.x * W + w;
+    const bool live = kx < K;
+    const Cx<T> *ib = in + blockIdx.z * in_field + blockIdx.y * in_plane + kx;
+    Cx<T> *ob = out + blockIdx.z * out_field + blockIdx.y * out_plane + kx;
+    const ColAddrW ad{W};
+    constexpr int R0 = 1 << P::LG0;
+    constexpr int NG0 = P::G0 / P::TPC;
+    Cx<T> a[NG0][R0];
+#pragma unroll
+    for (int i = 0; i < NG0; ++i) {
+        const int g = t + i * P::TPC;
+#pragma unroll
+        for (int p = 0; p < R0; ++p) {
+            const int m = g + p * P::G0;
+            const bool ok = live && m >= lo && m < lo + n;
+            a[i][p] = ok ? ib[(int64_t)(m - lo) * rs] : Cx<T>{T(0), T(0)};
+        }
+    }
+    __syncthreads();   // twiddles
+#pragma unroll
+    for (int i = 0; i < NG0; ++i) {
+        const int g = t + i * P::TPC;
+        dif_group<LOGM, LOGM, P::LG0>(a[i], g, tw);
+#pragma unroll
+        for (int q = 0; q < R0; ++q) s[ad(w, q * P::G0 + g)] = a[i][q];
+    }
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        middle_stage<LOGM, -1>(s, ad, w, t, tw);
+        __syncthreads();
+    }
+    constexpr int RL = 1 << P::LGL;
+#pragma unroll
+    for (int g = t; g < P::GL; g += P::TPC) {
+        Cx<T> c[RL];
+#pragma unroll
+        for (int q = 0; q < RL; ++q) c[q] = s[ad(w, (g << P::LGL) + q)];
+        Dft<RL, -1, T>::run(c);
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < RL; ++q) ob[(int64_t)freq_of<LOGM>((g << P::LGL) + q) * os] = c[q];
+        }
+    }
+}
+
+// Inverse along the column: spectrum rows (natural order, row k at
+// in + k * rs) in; rows [lo, lo + n) of the result written to
+// out + (m - lo) * os.
+template <typename T, int LOGM, int W>
+__global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
+                                                                     int K, int lo, int n, int64_t rs, int64_t os,
+                                                                     int64_t in_plane, int64_t out_plane,
+                                                                     int64_t in_field, int64_t out_field,
+                                                                     const Cx<T> *__restrict__ twg)
+{
+    using P = Plan<LOGM>;
+    constexpr int M = P::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *s = tw + M;
+    load_twiddles(tw, twg, M);
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int kx = blockIdx.x * W + w;
+    const bool live = kx < K;
+    const Cx<T> *ib = in + blockIdx.z * in_field + blockIdx.y * in_plane + kx;
+    Cx<T> *ob = out + blockIdx.z * out_field + blockIdx.y * out_plane + kx;
+    const ColAddrW ad{W};
+    constexpr int RL = 1 << P::LGL;
+    constexpr int NGL = P::GL / P::TPC;
+    Cx<T> c[NGL][RL];
+#pragma unroll
+    for (int i = 0; i < NGL; ++i) {
+        const int g = t + i * P::TPC;
+#pragma unroll
+        for (int q = 0; q < RL; ++q)
+            c[i][q] = live ? ib[(int64_t)freq_of<LOGM>((g << P::LGL) + q) * rs] : Cx<T>{T(0), T(0)};
+    }
+#pragma unroll
+    for (int i = 0; i < NGL; ++i) {
+        const int g = t + i * P::TPC;
+        Dft<RL, 1, T>::run(c[i]);
+#pragma unroll
+        for (int q = 0; q < RL; ++q) s[ad(w, (g << P::LGL) + q)] = c[i][q];
+    }
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        middle_stage<LOGM, 1>(s, ad, w, t, tw);
+        __syncthreads();
+    }
+    constexpr int R0 = 1 << P::LG0;
+#pragma unroll
+    for (int g = t; g < P::G0; g += P::TPC) {
+        Cx<T> a[R0];
+#pragma unroll
+        for (int q = 0; q < R0; ++q) a[q] = s[ad(w, q * P::G0 + g)];
+        dit_group<LOGM, LOGM, P::LG0>(a, g, tw);
+        if (live) {
+#pragma unroll
+            for (int p = 0; p < R0; ++p) {
+                const int m = g + p * P::G0;
+                if (m >= lo && m < lo + n) ob[(int64_t)(m - lo) * os] = a[p];
+            }
+        }
+    }
+}
+
+// z pass: forward along z over the source planes, times the real even kernel
+// spectrum, inverse along z, target planes written back in place.
+template <typename T, int LOGM, int W>
+__global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__restrict__ B, const T *__restrict__ spec,
+                                                                      int K, int My, int s0, int ns, int t0, int nt,
+                                                                      int64_t field, const Cx<T> *__restrict__ twg)
+{
+    using P = Plan<LOGM>;
+    constexpr int M = P::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *s = tw + M;
+    load_twiddles(tw, twg, M);
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int kx = blockIdx.x * W + w;
+    const int ky = blockIdx.y;
+    const bool live = kx < K;
+    const int64_t plane = (int64_t)My * K;
+    Cx<T> *bb = B + blockIdx.z * field + (int64_t)ky * K + kx;
+    const ColAddrW ad{W};
+    constexpr int R0 = 1 << P::LG0;
+    constexpr int NG0 = P::G0 / P::TPC;
+    {
+        Cx<T> a[NG0][R0];
+#pragma unroll
+        for (int i = 0; i < NG0; ++i) {
+            const int g = t + i * P::TPC;
+#pragma unroll
+            for (int p = 0; p < R0; ++p) {
+                const int m = g + p * P::G0;
+                const bool ok = live && m >= s0 && m < s0 + ns;
+                a[i][p] = ok ? bb[(int64_t)(m - s0) * plane] : Cx<T>{T(0), T(0)};
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NG0; ++i) {
+            const int g = t + i * P::TPC;
+            dif_group<LOGM, LOGM, P::LG0>(a[i], g, tw);
+#pragma unroll
+            for (int q = 0; q < R0; ++q) s[ad(w, q * P::G0 + g)] = a[i][q];
+        }
+    }
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        middle_stage<LOGM, -1>(s, ad, w, t, tw);
+        __syncthreads();
+    }
+    constexpr int RL = 1 << P::LGL;
+    const int Khy = My / 2 + 1;
+    const int kyr = ky <= My - ky ? ky : My - ky;
+    const T *sp = spec + (int64_t)kyr * K + (live ? kx : 0);
+    const int64_t sp_plane = (int64_t)Khy * K;
+#pragma unroll
+    for (int g = t; g < P::GL; g += P::TPC) {
+        Cx<T> c[RL];
+        T gk[RL];
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+            const int kz = freq_of<LOGM>((g << P::LGL) + q);
+            const int kzr = kz <= M - kz ? kz : M - kz;
+            gk[q] = sp[kzr * sp_plane];
+            c[q] = s[ad(w, (g << P::LGL) + q)];
+        }
+        Dft<RL, -1, T>::run(c);
+#pragma unroll
+        for (int q = 0; q < RL; ++q) {
+            c[q].x *= gk[q];
+            c[q].y *= gk[q];
+        }
+        Dft<RL, 1, T>::run(c);
+#pragma unroll
+        for (int q = 0; q < RL; ++q) s[ad(w, (g << P::LGL) + q)] = c[q];
+    }
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        middle_stage<LOGM, 1>(s, ad, w, t, tw);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int g = t; g < P::G0; g += P::TPC) {
+        Cx<T> a[R0];
+#pragma unroll
+        for (int q = 0; q < R0; ++q) a[q] = s[ad(w, q * P::G0 + g)];
+        dit_group<LOGM, LOGM, P::LG0>(a, g, tw);
+        if (live) {
+#pragma unroll
+            for (int p = 0; p < R0; ++p) {
+                const int m = g + p * P::G0;
+                if (m >= t0 && m < t0 + nt) bb[(int64_t)(m - t0) * plane] = a[p];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row passes along x (real <-> half complex), two real rows per complex line.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T fetch_block(const T *__restrict__ f, const int *__restrict__ map, int nbx, int nby, int lb,
+                                         int xr, int yr, int zr)
+{
+    const int bi = map[((zr >> lb) * nby + (yr >> lb)) * nbx + (xr >> lb)];
+    if (bi < 0) return T(0);
+    const int m = (1 << lb) - 1;
+    return f[((int64_t)bi << (3 * lb)) + ((((zr & m) << lb) + (yr & m)) << lb) + (xr & m)];
+}
+
+// Forward: rows (y, y+1) of source plane z, x in [s0x, s0x + Lsx), from the
+// block layout (dense_ld == 0) or from a dense box with row length dense_ld.
+template <typename T, int LOGM, int LPC>
+__global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_forward(const T *__restrict__ f, Cx<T> *__restrict__ A,
+                                                                       PoissonGeom g, const Cx<T> *__restrict__ twg,
+                                                                       int npairs, int lb, int dense_ld)
+{
+    using P = Plan<LOGM>;
+    constexpr int M = P::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *s = tw + M;
+    load_twiddles(tw, twg, M);
+    const int t = threadIdx.x % P::TPC, l = threadIdx.x / P::TPC;
+    const int pr = blockIdx.x * LPC + l;
+    const bool live = pr < npairs;
+    const int hp = g.Ls[1] >> 1;
+    const int zi = live ? pr / hp : 0, yi = live ? 2 * (pr - zi * hp) : 0;
+    const T *ff = f + blockIdx.y * g.fstride;
+    const RowAddrP ad{M + M / 16};
+    constexpr int R0 = 1 << P::LG0;
+    constexpr int NG0 = P::G0 / P::TPC;
+    Cx<T> a[NG0][R0];
+#pragma unroll
+    for (int i = 0; i < NG0; ++i) {
+        const int gg = t + i * P::TPC;
+#pragma unroll
+        for (int p = 0; p < R0; ++p) {
+            const int x = gg + p * P::G0;
+            Cx<T> v{T(0), T(0)};
+            if (live && x >= g.s0[0] && x < g.s0[0] + g.Ls[0]) {
+                if (dense_ld) {
+                    const T *row = ff + ((int64_t)(g.s0[2] + zi) * g.M[1] + (g.s0[1] + yi)) * dense_ld;
+                    v.x = row[x];
+                    v.y = row[dense_ld + x];
+                } else {
+                    v.x = fetch_block(ff, g.srcmap, g.nbs[0], g.nbs[1], lb, x - g.s0[0], yi, zi);
+                    v.y = fetch_block(ff, g.srcmap, g.nbs[0], g.nbs[1], lb, x - g.s0[0], yi + 1, zi);
+                }
+            }
+            a[i][p] = v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NG0; ++i) {
+        const int gg = t + i * P::TPC;
+        dif_group<LOGM, LOGM, P::LG0>(a[i], gg, tw);
+#pragma unroll
+        for (int q = 0; q < R0; ++q) s[ad(l, q * P::G0 + gg)] = a[i][q];
+    }
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        middle_stage<LOGM, -1>(s, ad, l, t, tw);
+        __syncthreads();
+    }
+    constexpr int RL = 1 << P::LGL;
+#pragma unroll
+    for (int gg = t; gg < P::GL; gg += P::TPC) {
+        Cx<T> c[RL];
+#pragma unroll
+        for (int q = 0; q < RL; ++q) c[q] = s[ad(l, (gg << P::LGL) + q)];
+        Dft<RL, -1, T>::run(c);
+#pragma unroll
+        for (int q = 0; q < RL; ++q) s[ad(l, (gg << P::LGL) + q)] = c[q];
+    }
+    __syncthreads();
+    if (!live) return;
+    const int K = g.Kx;
+    Cx<T> *row = A + blockIdx.y * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
+    for (int k = t; k < K; k += P::TPC) {
+        const Cx<T> zk = s[ad(l, pos_of<LOGM>(k))];
+        const Cx<T> zm = s[ad(l, pos_of<LOGM>((M - k) & (M - 1)))];
+        row[k] = Cx<T>{T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
+        row[K + k] = Cx<T>{T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
+    }
+}
+
+// Inverse: rows (y, y+1) of target plane z from their half spectra; x in
+// [t0x, t0x + Ltx) scaled by dx^2 and scattered to the target block layout.
+template <typename T, int LOGM, int LPC>
+__global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_inverse(const Cx<T> *__restrict__ A, T *__restrict__ u,
+                                                                       PoissonGeom g, const Cx<T> *__restrict__ twg,
+                                                                       int npairs, int lb)
+{
+    using P = Plan<LOGM>;
+    constexpr int M = P::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *s = tw + M;
+    load_twiddles(tw, twg, M);
+    const int t = threadIdx.x % P::TPC, l = threadIdx.x / P::TPC;
+    const int pr = blockIdx.x * LPC + l;
+    const bool live = pr < npairs;
+    const int hp = g.Lt[1] >> 1;
+    const int zi = live ? pr / hp : 0, yi = live ? 2 * (pr - zi * hp) : 0;
+    const int K = g.Kx;
+    const Cx<T> *row = A + blockIdx.y * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
+    const RowAddrP ad{M + M / 16};
+    // Hermitian extension of the two half spectra, packed as Z = G1 + i G2,
+    // stored at the digit-reversed positions the inverse sweep expects.
+    constexpr int NPT = M / P::TPC;
+    Cx<T> g1[NPT], g2[NPT];
+#pragma unroll
+    for (int i = 0; i < NPT; ++i) {
+        const int k = t + i * P::TPC;
+        const int kk = k <= M / 2 ? k : M - k;
+        g1[i] = live ? row[kk] : Cx<T>{T(0), T(0)};
+        g2[i] = live ? row[K + kk] : Cx<T>{T(0), T(0)};
+    }
+#pragma unroll
+    for (int i = 0; i < NPT; ++i) {
+        const int k = t + i * P::TPC;
+        Cx<T> v;
+        if (k <= M / 2) {
+            if (k == 0 || k == M / 2) {
+                g1[i].y = T(0);
+                g2[i].y = T(0);
+            }
+            v = {g1[i].x - g2[i].y, g1[i].y + g2[i].x};
+        } else {
+            v = {g1[i].x + g2[i].y, g2[i].x - g1[i].y};
+        }
+        s[ad(l, pos_of<LOGM>(k))] = v;
+    }
+    __syncthreads();
+    constexpr int RL = 1 << P::LGL;
+#pragma unroll
+    for (int gg = t; gg < P::GL; gg += P::TPC) {
+        Cx<T> c[RL];
+#pragma unroll
+        for (int q = 0; q < RL; ++q) c[q] = s[ad(l, (gg << P::LGL) + q)];
+        Dft<RL, 1, T>::run(c);
+#pragma unroll
+        for (int q = 0; q < RL; ++q) s[ad(l, (gg << P::LGL) + q)] = c[q];
+    }
+    __syncthreads();
+    if constexpr (P::NST == 3) {
+        middle_stage<LOGM, 1>(s, ad, l, t, tw);
+        __syncthreads();
+    }
+    if (!live) return;
+    const T sc = T(g.scale);
+    T *uu = u + blockIdx.y * g.ustride;
+    const int bm = g.b - 1;
+    constexpr int R0 = 1 << P::LG0;
+#pragma unroll
+    for (int gg = t; gg < P::G0; gg += P::TPC) {
+        Cx<T> a[R0];
+#pragma unroll
+        for (int q = 0; q < R0; ++q) a[q] = s[ad(l, q * P::G0 + gg)];
+        dit_group<LOGM, LOGM, P::LG0>(a, gg, tw);
+#pragma unroll
+        for (int p = 0; p < R0; ++p) {
+            const int x = gg + p * P::G0;
+            const int xi = x - g.t0[0];
+            if (xi < 0 || xi >= g.Lt[0]) continue;
+            const int bi0 = g.tgtmap[((zi >> lb) * g.nbt[1] + (yi >> lb)) * g.nbt[0] + (xi >> lb)];
+            if (bi0 < 0) continue;
+            const int64_t base = ((int64_t)bi0 << (3 * lb)) + ((((zi & bm) << lb) + (yi & bm)) << lb) + (xi & bm);
+            uu[base] = sc * a[p].x;
+            uu[base + (1 << lb)] = sc * a[p].y;   // row y + 1 of the same block (y is even, b >= 2)
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers.
+// ---------------------------------------------------------------------------
+template <typename T, int LOGM>
+struct ColCfg {
+    static constexpr int TPC = Plan<LOGM>::TPC;
+    static constexpr int W0 = 256 / TPC < 8 ? 8 : (256 / TPC > 32 ? 32 : 256 / TPC);
+    static constexpr int WMAX = int(98304 / (sizeof(Cx<T>) << LOGM)) < 1 ? 1 : int(98304 / (sizeof(Cx<T>) << LOGM));
+    static constexpr int W = W0 < WMAX ? W0 : WMAX;
+    static constexpr size_t SMEM = sizeof(Cx<T>) * (((size_t)1 << LOGM) * (W + 1));
+};
+
+template <typename T, int LOGM>
+struct RowCfg {
+    static constexpr int TPC = Plan<LOGM>::TPC;
+    static constexpr int L0 = 256 / TPC < 1 ? 1 : (256 / TPC > 32 ? 32 : 256 / TPC);
+    static constexpr int LD = (1 << LOGM) + (1 << LOGM) / 16;
+    static constexpr int LMAX = int(98304 / (sizeof(Cx<T>) * LD)) < 1 ? 1 : int(98304 / (sizeof(Cx<T>) * LD));
+    static constexpr int LPC = L0 < LMAX ? L0 : LMAX;
+    static constexpr size_t SMEM = sizeof(Cx<T>) * (((size_t)1 << LOGM) + (size_t)LPC * LD);
+};
+
+}  // namespace pk
+
+// Launch entry points (one set per precision, instantiated in
+// lgf_poisson_f32.cu / lgf_poisson_f64.cu).
+template <typename T>
+lgf_status launch_row_forward(lgf_ctx *ctx, const PoissonGeom &g, const T *f, Cx<T> *A, const Cx<T> *tw, int nfields,
+                              int lb, int dense_ld, cudaStream_t s);
+template <typename T>
+lgf_status launch_row_inverse(lgf_ctx *ctx, const PoissonGeom &g, const Cx<T> *A, T *u, const Cx<T> *tw, int nfields,
+                              int lb, cudaStream_t s);
+template <typename T>
+lgf_status launch_col_forward(lgf_ctx *ctx, int M, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out,
+                              int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
+                              int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name);
+template <typename T>
+lgf_status launch_col_inverse(lgf_ctx *ctx, int M, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out,
+                              int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
+                              int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name);
+template <typename T>
+lgf_status launch_col_convolve(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw,
+                               int nfields, cudaStream_t s);
+
+}  // namespace lgf
+
+namespace lgf {
+namespace pk {
+
+template <class K>
+inline lgf_status set_smem(lgf_ctx *ctx, K kern, size_t smem)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    }
+    return LGF_OK;
+}
+
+template <typename T, int LOGM>
+lgf_status row_forward_m(lgf_ctx *ctx, const PoissonGeom &g, const T *f, Cx<T> *A, const Cx<T> *tw, int nfields,
+                         int lb, int dense_ld, cudaStream_t s)
+{
+    using C = RowCfg<T, LOGM>;
+    auto kern = k_row_forward<T, LOGM, C::LPC>;
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    const int npairs = (g.Ls[1] / 2) * g.Ls[2];
+    dim3 grid((npairs + C::LPC - 1) / C::LPC, nfields);
+    const int ph = prof_begin(ctx, s, dense_ld ? "spectrum_x_forward" : "poisson_x_forward");
+    kern<<<grid, C::LPC * C::TPC, C::SMEM, s>>>(f, A, g, tw, npairs, lb, dense_ld);
+    LGF_CHECK_LAUNCH(ctx, "poisson x-forward");
+    prof_end(ctx, s, ph);
+    return LGF_OK;
+}
+
+template <typename T, int LOGM>
+lgf_status row_inverse_m(lgf_ctx *ctx, const PoissonGeom &g, const Cx<T> *A, T *u, const Cx<T> *tw, int nfields,
+                         int lb, cudaStream_t s)
+{
+    using C = RowCfg<T, LOGM>;
+    auto kern = k_row_inverse<T, LOGM, C::LPC>;
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    const int npairs = (g.Lt[1] / 2) * g.Lt[2];
+    dim3 grid((npairs + C::LPC - 1) / C::LPC, nfields);
+    const int ph = prof_begin(ctx, s, "poisson_x_inverse");
+    kern<<<grid, C::LPC * C::TPC, C::SMEM, s>>>(A, u, g, tw, npairs, lb);
+    LGF_CHECK_LAUNCH(ctx, "poisson x-inverse");
+    prof_end(ctx, s, ph);
+    return LGF_OK;
+}
+
+template <typename T, int LOGM>
+lgf_status col_forward_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out, int lo, int n,
+                         int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane, int64_t in_field,
+                         int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
+{
+    using C = ColCfg<T, LOGM>;
+    auto kern = k_col_forward<T, LOGM, C::W>;
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    dim3 grid((K + C::W - 1) / C::W, nplanes, nfields);
+    const int ph = prof_begin(ctx, s, name);
+    kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(in, out, K, lo, n, rs, os, in_plane, out_plane, in_field, out_field,
+                                              tw);
+    LGF_CHECK_LAUNCH(ctx, name);
+    prof_end(ctx, s, ph);
+    return LGF_OK;
+}
+
+template <typename T, int LOGM>
+lgf_status col_inverse_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out, int lo, int n,
+                         int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane, int64_t in_field,
+                         int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
+{
+    using C = ColCfg<T, LOGM>;
+    auto kern = k_col_inverse<T, LOGM, C::W>;
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    dim3 grid((K + C::W - 1) / C::W, nplanes, nfields);
+    const int ph = prof_begin(ctx, s, name);
+    kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(in, out, K, lo, n, rs, os, in_plane, out_plane, in_field, out_field,
+                                              tw);
+    LGF_CHECK_LAUNCH(ctx, name);
+    prof_end(ctx, s, ph);
+    return LGF_OK;
+}
+
+template <typename T, int LOGM>
+lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw, int nfields,
+                          cudaStream_t s)
+{
+    using C = ColCfg<T, LOGM>;
+    auto kern = k_col_convolve<T, LOGM, C::W>;
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    dim3 grid((g.Kx + C::W - 1) / C::W, g.M[1], nfields);
+    const int ph = prof_begin(ctx, s, "poisson_z_convolve");
+    kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(B, spec, g.Kx, g.M[1], g.s0[2], g.Ls[2], g.t0[2], g.Lt[2], g.Bstride,
+                                              tw);
+    LGF_CHECK_LAUNCH(ctx, "poisson z-convolve");
+    prof_end(ctx, s, ph);
+    return LGF_OK;
+}
+
+inline int ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+#define LGF_DISPATCH_LOGM(LOGM_RT, CALL)                                        \
+    switch (LOGM_RT) {                                                          \
+    case 5: { constexpr int LM = 5; return CALL; }                              \
+    case 6: { constexpr int LM = 6; return CALL; }                              \
+    case 7: { constexpr int LM = 7; return CALL; }                              \
+    case 8: { constexpr int LM = 8; return CALL; }                              \
+    case 9: { constexpr int LM = 9; return CALL; }                              \
+    case 10: { constexpr int LM = 10; return CALL; }                            \
+    case 11: { constexpr int LM = 11; return CALL; }                            \
+    case 12: { constexpr int LM = 12; return CALL; }                            \
+    default: return fail(ctx, LGF_EUNSUPPORTED, "transform length outside 32..4096"); \
+    }
+
+}  // namespace pk
+
+template <typename T>
+lgf_status launch_row_forward(lgf_ctx *ctx, const PoissonGeom &g, const T *f, Cx<T> *A, const Cx<T> *tw, int nfields,
+                              int lb, int dense_ld, cudaStream_t s)
+{
+    LGF_DISPATCH_LOGM(pk::ilog2(g.M[0]), (pk::row_forward_m<T, LM>(ctx, g, f, A, tw, nfields, lb, dense_ld, s)));
+}
+
+template <typename T>
+lgf_status launch_row_inverse(lgf_ctx *ctx, const PoissonGeom &g, const Cx<T> *A, T *u, const Cx<T> *tw, int nfields,
+                              int lb, cudaStream_t s)
+{
+    LGF_DISPATCH_LOGM(pk::ilog2(g.M[0]), (pk::row_inverse_m<T, LM>(ctx, g, A, u, tw, nfields, lb, s)));
+}
+
+template <typename T>
+lgf_status launch_col_forward(lgf_ctx *ctx, int M, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out,
+                              int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
+                              int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
+{
+    LGF_DISPATCH_LOGM(pk::ilog2(M), (pk::col_forward_m<T, LM>(ctx, K, nplanes, nfields, in, out, lo, n, rs, os,
+                                                               in_plane, out_plane, in_field, out_field, tw, s,
+                                                               name)));
+}
+
+template <typename T>
+lgf_status launch_col_inverse(lgf_ctx *ctx, int M, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out,
+                              int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
+                              int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
+{
+    LGF_DISPATCH_LOGM(pk::ilog2(M), (pk::col_inverse_m<T, LM>(ctx, K, nplanes, nfields, in, out, lo, n, rs, os,
+                                                               in_plane, out_plane, in_field, out_field, tw, s,
+                                                               name)));
+}
+
+template <typename T>
+lgf_status launch_col_convolve(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw,
+                               int nfields, cudaStream_t s)
+{
+    LGF_DISPATCH_LOGM(pk::ilog2(g.M[2]), (pk::col_convolve_m<T, LM>(ctx, g, B, spec, tw, nfields, s)));
+}
+
+}  // namespace lgf
