@@ -23,6 +23,16 @@
 
 namespace lgf {
 
+// Register-window passes (lgf_intfactor_win.cuh, instantiated per precision).
+template <typename T>
+lgf_status launch_sep_window(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
+                             const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done);
+extern template lgf_status launch_sep_window<float>(lgf_ctx *, int, int, int, int, cudaStream_t, const float *, float *,
+                                                    const int *, const float *, int, int, int64_t, int64_t, bool *);
+extern template lgf_status launch_sep_window<double>(lgf_ctx *, int, int, int, int, cudaStream_t, const double *,
+                                                     double *, const int *, const double *, int, int, int64_t, int64_t,
+                                                     bool *);
+
 IntfPlan::~IntfPlan()
 {
     for (auto &p : pass) cudaFree(p.nbr_dev);
@@ -374,6 +384,13 @@ template <typename T>
 lgf_status launch_sep(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
                       const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr)
 {
+    bool done = false;
+    lgf_status wst = launch_sep_window<T>(ctx, ax, b, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr, &done);
+    if (wst != LGF_OK) return wst;
+    if (done) {
+        LGF_CHECK_LAUNCH(ctx, "intfactor pass");
+        return LGF_OK;
+    }
     const SepGeom sg = sep_geom(b, R, nr);
     const size_t smem = sizeof(T) * (((R + 1 + 3) & ~3) + (size_t)sg.slab * b * (b + 2 * sg.HL));
     dim3 grid(nout, sg.nslab, nfields);

@@ -1,0 +1,241 @@
+// Integrating-factor pass with a register window (radius bound RMAX fixed at
+// compile time, actual radius R <= RMAX at run time; weights past R are zero).
+//
+// A CTA stages one slab of an output block plus a halo of RMAX points along
+// the pass axis (16-byte loads from the neighbour blocks, zero where a block
+// is absent).  Each thread then produces V outputs along the axis for NV
+// adjacent x values: it streams the V + 2 RMAX staged inputs once, and every
+// input feeds the V accumulators it touches with the weight w(|d|) held in a
+// register (the distance d is a compile-time constant after unrolling).
+// Shared-memory traffic per output is (V + 2 RMAX) / V values instead of
+// 2R + 1.
+#pragma once
+#include "lgf_internal.cuh"
+
+namespace lgf {
+namespace win {
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    using V = float4;
+    static constexpr int N = 4;
+};
+template <>
+struct Vec<double> {
+    using V = double2;
+    static constexpr int N = 2;
+};
+
+constexpr int kV = 4;   // outputs per thread along the pass axis
+
+// Threads per CTA and slab extent for block edge b = 2^LB.
+template <typename T, int LB, int AX>
+struct Cfg {
+    static constexpr int b = 1 << LB;
+    static constexpr int NV = Vec<T>::N;
+    // threads needed for one plane of the slab axis
+    static constexpr int per_plane = AX == 0 ? b * (b / kV) : (b / NV) * (b / kV);
+    static constexpr int NS0 = 256 / per_plane;
+    static constexpr int NS = NS0 < 1 ? 1 : (NS0 > b ? b : NS0);
+    static constexpr int THREADS = NS * per_plane;
+};
+
+template <typename T, int LB, int AX, int RMAX>
+__global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
+    k_sep_win(const T *__restrict__ in, T *__restrict__ out, const int *__restrict__ nbr, const T *__restrict__ wg,
+              int R, int nr, int64_t in_stride, int64_t out_stride)
+{
+    using C = Cfg<T, LB, AX>;
+    using VT = typename Vec<T>::V;
+    constexpr int b = C::b, bm = b - 1, NV = C::NV, NS = C::NS, HL = RMAX, E = b + 2 * HL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s = reinterpret_cast<T *>(smem_raw);
+    const int o = blockIdx.x;
+    const int s0 = blockIdx.y * NS;
+    const int nd = 2 * nr + 1;
+    const int *nb = nbr + (int64_t)o * nd;
+    const T *inf = in + blockIdx.z * in_stride;
+    T *outf = out + blockIdx.z * out_stride;
+
+    // ---- stage [slab + halo] with 16-byte loads ----
+    constexpr int rowlen = AX == 0 ? E : b;
+    constexpr int nrows = AX == 0 ? NS * b : NS * E;
+    constexpr int vpr = rowlen / NV;
+    constexpr int total = nrows * vpr;
+    constexpr int U = 4;
+    for (int base = threadIdx.x; base < total; base += U * C::THREADS) {
+        VT v[U];
+        int dst[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int it = base + u * C::THREADS;
+            dst[u] = -1;
+            v[u] = VT{};
+            if (it >= total) continue;
+            const int row = it / vpr, cv = it - row * vpr;
+            int x, y, z, e;
+            if (AX == 0) {
+                e = cv * NV - HL;
+                y = row & bm;
+                z = s0 + (row >> LB);
+                x = e & bm;
+            } else if (AX == 1) {
+                x = cv * NV;
+                e = row % E - HL;
+                z = s0 + row / E;
+                y = e & bm;
+            } else {
+                x = cv * NV;
+                y = s0 + row % NS;
+                e = row / NS - HL;
+                z = e & bm;
+            }
+            dst[u] = it * NV;
+            const int bi = nb[(e + nr * b) >> LB];
+            if (bi >= 0)
+                v[u] = *reinterpret_cast<const VT *>(inf + ((int64_t)bi << (3 * LB)) + (((z << LB) + y) << LB) + x);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (dst[u] >= 0) *reinterpret_cast<VT *>(s + dst[u]) = v[u];
+    }
+    T w[RMAX + 1];
+#pragma unroll
+    for (int k = 0; k <= RMAX; ++k) w[k] = k <= R ? wg[k] : T(0);
+    __syncthreads();
+
+    // ---- stencil through the register window ----
+    const int tid = threadIdx.x;
+    if (AX == 0) {
+        // thread: kV consecutive x outputs of row (y, z)
+        const int xv = tid % (b / kV);
+        const int y = (tid / (b / kV)) & bm;
+        const int sl = tid / (b * (b / kV));
+        const int x0 = xv * kV;
+        const T *row = s + (sl * b + y) * E + x0;      // window starts at x0 - HL
+        T acc[kV];
+#pragma unroll
+        for (int v = 0; v < kV; ++v) acc[v] = T(0);
+#pragma unroll
+        for (int i = 0; i < (kV + 2 * RMAX) / NV; ++i) {
+            const VT val = *reinterpret_cast<const VT *>(row + i * NV);
+            const T *vs = reinterpret_cast<const T *>(&val);
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+                const int pos = i * NV + e;             // input at x0 - HL + pos
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    const int d = pos - HL - v;
+                    if (d >= -RMAX && d <= RMAX) acc[v] += w[d < 0 ? -d : d] * vs[e];
+                }
+            }
+        }
+        const int z = s0 + sl;
+#pragma unroll
+        for (int v = 0; v < kV; v += NV) {
+            VT r;
+            T *rr = reinterpret_cast<T *>(&r);
+#pragma unroll
+            for (int e = 0; e < NV; ++e) rr[e] = acc[v + e];
+            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((z << LB) + y) << LB) + x0 + v) = r;
+        }
+    } else {
+        // thread: NV adjacent x values, kV consecutive outputs along the axis
+        const int xv = tid % (b / NV);
+        const int av = (tid / (b / NV)) % (b / kV);
+        const int sl = tid / ((b / NV) * (b / kV));
+        const int x = xv * NV, a0 = av * kV;
+        // element (axis position p in [-HL, b + HL), slab-local sl, x)
+        const int st = AX == 1 ? b : NS * b;
+        const T *col = AX == 1 ? s + (sl * E + a0) * b + x : s + (a0 * NS + sl) * b + x;
+        T acc[kV][NV];
+#pragma unroll
+        for (int v = 0; v < kV; ++v)
+#pragma unroll
+            for (int e = 0; e < NV; ++e) acc[v][e] = T(0);
+#pragma unroll
+        for (int pos = 0; pos < kV + 2 * RMAX; ++pos) {
+            const VT val = *reinterpret_cast<const VT *>(col + pos * st);
+            const T *vs = reinterpret_cast<const T *>(&val);
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const int d = pos - HL - v;
+                if (d >= -RMAX && d <= RMAX) {
+#pragma unroll
+                    for (int e = 0; e < NV; ++e) acc[v][e] += w[d < 0 ? -d : d] * vs[e];
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            VT r;
+            T *rr = reinterpret_cast<T *>(&r);
+#pragma unroll
+            for (int e = 0; e < NV; ++e) rr[e] = acc[v][e];
+            const int Y = AX == 1 ? a0 + v : s0 + sl;
+            const int Z = AX == 1 ? s0 + sl : a0 + v;
+            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((Z << LB) + Y) << LB) + x) = r;
+        }
+    }
+}
+
+template <typename T, int LB, int AX, int RMAX>
+lgf_status launch_m(lgf_ctx *ctx, int nout, int nfields, cudaStream_t s, const T *in, T *out, const int *nbr,
+                    const T *w, int R, int nr, int64_t istr, int64_t ostr)
+{
+    using C = Cfg<T, LB, AX>;
+    constexpr int b = 1 << LB, E = b + 2 * RMAX;
+    constexpr size_t smem = sizeof(T) * (size_t)C::NS * b * E;
+    auto kern = k_sep_win<T, LB, AX, RMAX>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    }
+    dim3 grid(nout, b / C::NS, nfields);
+    kern<<<grid, C::THREADS, smem, s>>>(in, out, nbr, w, R, nr, istr, ostr);
+    return LGF_OK;
+}
+
+template <typename T, int LB, int AX>
+lgf_status launch_r(lgf_ctx *ctx, int rmax, int nout, int nfields, cudaStream_t s, const T *in, T *out,
+                    const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr)
+{
+    switch (rmax) {
+    case 4: return launch_m<T, LB, AX, 4>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    case 8: return launch_m<T, LB, AX, 8>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    default: return launch_m<T, LB, AX, 16>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    }
+}
+
+}  // namespace win
+
+// Window-kernel pass if (b, R, nr) qualify (b in {8, 16, 32}, R <= 16 and the
+// rounded radius within the staged neighbours); *done tells whether it ran.
+template <typename T>
+lgf_status launch_sep_window(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
+                             const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done)
+{
+    *done = false;
+    const int rmax = R <= 4 ? 4 : R <= 8 ? 8 : R <= 16 ? 16 : 0;
+    if (rmax == 0 || rmax > nr * b || (b != 8 && b != 16 && b != 32)) return LGF_OK;
+    *done = true;
+    const int lb = b == 8 ? 3 : b == 16 ? 4 : 5;
+#define LGF_WIN_AX(AXV)                                                                                       \
+    switch (lb) {                                                                                             \
+    case 3: return win::launch_r<T, 3, AXV>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr); \
+    case 4: return win::launch_r<T, 4, AXV>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr); \
+    default: return win::launch_r<T, 5, AXV>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr); \
+    }
+    if (ax == 0) {
+        LGF_WIN_AX(0)
+    } else if (ax == 1) {
+        LGF_WIN_AX(1)
+    } else {
+        LGF_WIN_AX(2)
+    }
+#undef LGF_WIN_AX
+}
+
+}  // namespace lgf
