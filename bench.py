@@ -180,7 +180,7 @@ def algorithmic_bytes(p, nfields: int) -> dict:
         "poisson_x_inverse": nfields * (Lt[2] * Lt[1] * K * c8 + ntgt * b3 * 4),
     }
     # integrating-factor passes on a dense box: every pass reads and writes the box once
-    for ax in "xyz":
+    for ax in ("x", "y", "z", "xy"):
         by[f"intfactor_pass_{ax}"] = nfields * 2 * ntgt * b3 * 4
     return by
 

@@ -68,6 +68,7 @@ struct IntfPlan {
     std::vector<int32_t> src, tgt;
     int n1 = 0, n2 = 0;       // sizes of the two intermediate block sets
     IntfPass pass[3];
+    int *nbr_xy_dev = nullptr; // [n2][(2nr+1)^2] source block at xy offset of each Y2 block, or -1
     ~IntfPlan();
 };
 

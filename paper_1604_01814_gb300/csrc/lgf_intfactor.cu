@@ -27,6 +27,13 @@ namespace lgf {
 template <typename T>
 lgf_status launch_sep_window(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
                              const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done);
+template <typename T>
+lgf_status launch_sep_xy(lgf_ctx *ctx, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
+                         const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done);
+extern template lgf_status launch_sep_xy<float>(lgf_ctx *, int, int, int, cudaStream_t, const float *, float *,
+                                                const int *, const float *, int, int, int64_t, int64_t, bool *);
+extern template lgf_status launch_sep_xy<double>(lgf_ctx *, int, int, int, cudaStream_t, const double *, double *,
+                                                 const int *, const double *, int, int, int64_t, int64_t, bool *);
 extern template lgf_status launch_sep_window<float>(lgf_ctx *, int, int, int, int, cudaStream_t, const float *, float *,
                                                     const int *, const float *, int, int, int64_t, int64_t, bool *);
 extern template lgf_status launch_sep_window<double>(lgf_ctx *, int, int, int, int, cudaStream_t, const double *,
@@ -36,6 +43,7 @@ extern template lgf_status launch_sep_window<double>(lgf_ctx *, int, int, int, i
 IntfPlan::~IntfPlan()
 {
     for (auto &p : pass) cudaFree(p.nbr_dev);
+    cudaFree(nbr_xy_dev);
 }
 
 namespace {
@@ -322,6 +330,21 @@ lgf_status intf_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *
     if ((st = build(0, x1, S, 0)) != LGF_OK) return st;
     if ((st = build(1, y2, X1, 1)) != LGF_OK) return st;
     if ((st = build(2, touts, Y2, 2)) != LGF_OK) return st;
+    {   // fused x+y pass: the source block at each xy offset of every Y2 block
+        const int nd2 = nd * nd;
+        std::vector<int> nxy((size_t)y2.size() * nd2, -1);
+        for (size_t o = 0; o < y2.size(); ++o)
+            for (int dy = -nr; dy <= nr; ++dy)
+                for (int dx = -nr; dx <= nr; ++dx) {
+                    auto it = S.find(pack(y2[o][0] + dx, y2[o][1] + dy, y2[o][2]));
+                    if (it != S.end()) nxy[o * nd2 + (dy + nr) * nd + (dx + nr)] = it->second;
+                }
+        if (!nxy.empty()) {
+            if (cudaMalloc(&plan->nbr_xy_dev, nxy.size() * sizeof(int)) != cudaSuccess)
+                return fail(ctx, LGF_ENOMEM, "intfactor: neighbour table allocation failed");
+            LGF_CUDA(ctx, cudaMemcpy(plan->nbr_xy_dev, nxy.data(), nxy.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
+    }
         ctx->iplans.push_back(std::move(plan));
     *out = ctx->iplans.back().get();
     return LGF_OK;
@@ -416,6 +439,24 @@ static lgf_status run_sep(lgf_ctx *ctx, IntfPlan *pl, const T *w, int R, const T
     const int64_t istr[3] = {nsrc * b3, pl->n1 * b3, pl->n2 * b3};
     const int64_t ostr[3] = {pl->n1 * b3, pl->n2 * b3, ntgt * b3};
     static const char *names[3] = {"intfactor_pass_x", "intfactor_pass_y", "intfactor_pass_z"};
+    if (pl->n2 > 0 && pl->pass[2].nout > 0) {   // fused x+y pass, then z, when the window kernels apply
+        const int ph = prof_begin(ctx, s, "intfactor_pass_xy");
+        bool done = false;
+        lgf_status st = launch_sep_xy<T>(ctx, b, pl->n2, nfields, s, f, Y2, pl->nbr_xy_dev, w, R, nr, istr[0], ostr[1],
+                                         &done);
+        if (st != LGF_OK) return st;
+        if (done) {
+            LGF_CHECK_LAUNCH(ctx, "intfactor xy pass");
+            prof_end(ctx, s, ph);
+            const int pz = prof_begin(ctx, s, names[2]);
+            st = launch_sep<T>(ctx, 2, b, pl->pass[2].nout, nfields, s, Y2, u, pl->pass[2].nbr_dev, w, R, nr, istr[2],
+                               ostr[2]);
+            if (st != LGF_OK) return st;
+            prof_end(ctx, s, pz);
+            return LGF_OK;
+        }
+        prof_end(ctx, s, ph);
+    }
     for (int p = 0; p < 3; ++p) {
         if (pl->pass[p].nout == 0) continue;
         const int ph = prof_begin(ctx, s, names[p]);

@@ -181,6 +181,162 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
     }
 }
 
+// Fused x and y passes: stage the (b + 2 RMAX)^2 neighbourhood of NS
+// z-planes of an output block from its 3x3 xy neighbours, run the x stencil
+// into an intermediate [NS][E][b] and then the y stencil to the output.
+template <typename T, int LB, int RMAX>
+struct XYCfg {
+    static constexpr int b = 1 << LB, E = b + 2 * RMAX;
+    static constexpr int per_plane = E * E + E * b;
+    static constexpr int NS0 = 12288 / per_plane;
+    static constexpr int NS = NS0 >= 8 ? 8 : NS0 >= 4 ? 4 : NS0 >= 2 ? 2 : 1;
+    static constexpr int NSB = NS > b ? b : NS;
+    static constexpr size_t SMEM = sizeof(T) * (size_t)NSB * per_plane;
+};
+
+template <typename T, int LB, int RMAX>
+__global__ void __launch_bounds__(256) k_sep_xy(const T *__restrict__ in, T *__restrict__ out,
+                                                 const int *__restrict__ nbr, const T *__restrict__ wg, int R, int nr,
+                                                 int64_t in_stride, int64_t out_stride)
+{
+    using C = XYCfg<T, LB, RMAX>;
+    using VT = typename Vec<T>::V;
+    constexpr int b = C::b, bm = b - 1, NV = Vec<T>::N, NS = C::NSB, HL = RMAX, E = C::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rg = reinterpret_cast<T *>(smem_raw);       // [NS][E][E]
+    T *im = rg + NS * E * E;                        // [NS][E][b]
+    const int o = blockIdx.x;
+    const int s0 = blockIdx.y * NS;
+    const int nd = 2 * nr + 1;
+    const int *nb = nbr + (int64_t)o * nd * nd;
+    const T *inf = in + blockIdx.z * in_stride;
+    T *outf = out + blockIdx.z * out_stride;
+    // ---- stage ----
+    constexpr int vpr = E / NV;
+    constexpr int total = NS * E * vpr;
+    constexpr int U = 4;
+    for (int base = threadIdx.x; base < total; base += U * 256) {
+        VT v[U];
+        int dst[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int it = base + u * 256;
+            dst[u] = -1;
+            v[u] = VT{};
+            if (it >= total) continue;
+            const int row = it / vpr, cv = it - row * vpr;
+            const int ex = cv * NV - HL, ey = row % E - HL, z = s0 + row / E;
+            dst[u] = it * NV;
+            const int bi = nb[((ey + nr * b) >> LB) * nd + ((ex + nr * b) >> LB)];
+            if (bi >= 0)
+                v[u] = *reinterpret_cast<const VT *>(inf + ((int64_t)bi << (3 * LB)) + (((z << LB) + (ey & bm)) << LB) +
+                                                     (ex & bm));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (dst[u] >= 0) *reinterpret_cast<VT *>(rg + dst[u]) = v[u];
+    }
+    T w[RMAX + 1];
+#pragma unroll
+    for (int k = 0; k <= RMAX; ++k) w[k] = k <= R ? wg[k] : T(0);
+    __syncthreads();
+    // ---- x stencil: every staged row, kV outputs per item ----
+    constexpr int xitems = NS * E * (b / kV);
+    for (int it = threadIdx.x; it < xitems; it += 256) {
+        const int xv = it % (b / kV), row = it / (b / kV);   // row = zl * E + y_ext + HL
+        const int x0 = xv * kV;
+        const T *r = rg + row * E + x0;                       // staged x_ext = x0 - HL ...
+        T acc[kV];
+#pragma unroll
+        for (int v = 0; v < kV; ++v) acc[v] = T(0);
+#pragma unroll
+        for (int i = 0; i < (kV + 2 * RMAX) / NV; ++i) {
+            const VT val = *reinterpret_cast<const VT *>(r + i * NV);
+            const T *vs = reinterpret_cast<const T *>(&val);
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+                const int pos = i * NV + e;
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    const int d = pos - HL - v;
+                    if (d >= -RMAX && d <= RMAX) acc[v] += w[d < 0 ? -d : d] * vs[e];
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kV; v += NV) {
+            VT q;
+            T *qq = reinterpret_cast<T *>(&q);
+#pragma unroll
+            for (int e = 0; e < NV; ++e) qq[e] = acc[v + e];
+            *reinterpret_cast<VT *>(im + row * b + x0 + v) = q;
+        }
+    }
+    __syncthreads();
+    // ---- y stencil: NV adjacent x, kV consecutive y outputs per item ----
+    constexpr int yitems = NS * (b / NV) * (b / kV);
+    for (int it = threadIdx.x; it < yitems; it += 256) {
+        const int xv = it % (b / NV);
+        const int yv = (it / (b / NV)) % (b / kV);
+        const int zl = it / ((b / NV) * (b / kV));
+        const int x = xv * NV, y0 = yv * kV;
+        const T *col = im + (zl * E + y0) * b + x;            // y_ext = y0 - HL ...
+        T acc[kV][NV];
+#pragma unroll
+        for (int v = 0; v < kV; ++v)
+#pragma unroll
+            for (int e = 0; e < NV; ++e) acc[v][e] = T(0);
+#pragma unroll
+        for (int pos = 0; pos < kV + 2 * RMAX; ++pos) {
+            const VT val = *reinterpret_cast<const VT *>(col + pos * b);
+            const T *vs = reinterpret_cast<const T *>(&val);
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const int d = pos - HL - v;
+                if (d >= -RMAX && d <= RMAX) {
+#pragma unroll
+                    for (int e = 0; e < NV; ++e) acc[v][e] += w[d < 0 ? -d : d] * vs[e];
+                }
+            }
+        }
+        const int z = s0 + zl;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            VT q;
+            T *qq = reinterpret_cast<T *>(&q);
+#pragma unroll
+            for (int e = 0; e < NV; ++e) qq[e] = acc[v][e];
+            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((z << LB) + y0 + v) << LB) + x) = q;
+        }
+    }
+}
+
+template <typename T, int LB, int RMAX>
+lgf_status launch_xy_m(lgf_ctx *ctx, int nout, int nfields, cudaStream_t s, const T *in, T *out, const int *nbr,
+                       const T *w, int R, int nr, int64_t istr, int64_t ostr)
+{
+    using C = XYCfg<T, LB, RMAX>;
+    auto kern = k_sep_xy<T, LB, RMAX>;
+    if (C::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    }
+    dim3 grid(nout, C::b / C::NSB, nfields);
+    kern<<<grid, 256, C::SMEM, s>>>(in, out, nbr, w, R, nr, istr, ostr);
+    return LGF_OK;
+}
+
+template <typename T, int LB>
+lgf_status launch_xy_r(lgf_ctx *ctx, int rmax, int nout, int nfields, cudaStream_t s, const T *in, T *out,
+                       const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr)
+{
+    switch (rmax) {
+    case 4: return launch_xy_m<T, LB, 4>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    case 8: return launch_xy_m<T, LB, 8>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    default: return launch_xy_m<T, LB, 16>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    }
+}
+
 template <typename T, int LB, int AX, int RMAX>
 lgf_status launch_m(lgf_ctx *ctx, int nout, int nfields, cudaStream_t s, const T *in, T *out, const int *nbr,
                     const T *w, int R, int nr, int64_t istr, int64_t ostr)
@@ -210,6 +366,23 @@ lgf_status launch_r(lgf_ctx *ctx, int rmax, int nout, int nfields, cudaStream_t 
 }
 
 }  // namespace win
+
+// Fused x+y pass (S -> Y2 with the (2nr+1)^2 xy neighbour table) under the same
+// eligibility as launch_sep_window.
+template <typename T>
+lgf_status launch_sep_xy(lgf_ctx *ctx, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
+                         const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done)
+{
+    *done = false;
+    const int rmax = R <= 4 ? 4 : R <= 8 ? 8 : R <= 16 ? 16 : 0;
+    if (rmax == 0 || rmax > nr * b || (b != 8 && b != 16 && b != 32)) return LGF_OK;
+    *done = true;
+    switch (b) {
+    case 8: return win::launch_xy_r<T, 3>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    case 16: return win::launch_xy_r<T, 4>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    default: return win::launch_xy_r<T, 5>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    }
+}
 
 // Window-kernel pass if (b, R, nr) qualify (b in {8, 16, 32}, R <= 16 and the
 // rounded radius within the staged neighbours); *done tells whether it ran.

@@ -4,4 +4,6 @@
 namespace lgf {
 template lgf_status launch_sep_window<float>(lgf_ctx *, int, int, int, int, cudaStream_t, const float *, float *, const int *,
                                          const float *, int, int, int64_t, int64_t, bool *);
+template lgf_status launch_sep_xy<float>(lgf_ctx *, int, int, int, cudaStream_t, const float *, float *, const int *,
+                                     const float *, int, int, int64_t, int64_t, bool *);
 }  // namespace lgf
