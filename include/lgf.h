@@ -163,12 +163,17 @@ typedef struct {
 } lgf_problem;
 
 /* Apply `nprob` independent problems (the per-stage right-hand sides of
-   Sec. 2.3 and many uneven block-adaptive problems) as one batch: problems
-   whose padded transform boxes share a shape run in the same launches, and
-   the whole batch is captured once into a CUDA graph that later calls with
-   an identical batch (same block lists, pointers, alphas) replay.  u buffers
-   must not alias f buffers of the same batch.  POISSON_THEN_INTFACTOR writes
-   E_alpha(G_L * f) into u_dev.  Errors: as the single applies. */
+   Sec. 2.3 and many uneven block-adaptive problems) as one batch.  All plans,
+   spectra and weights are prepared first; the Poisson parts run one problem
+   after another (all fields of a problem in each launch), then the
+   integrating factors: those on the same block sets with the same field
+   count form one group that runs as one launch per pass (up to 8 problems
+   per launch, different alphas and buffers allowed).  On a non-default
+   stream the whole batch is captured once into a CUDA graph, and later calls
+   with an identical batch (same block lists, pointers, alphas, stream)
+   replay it.  u buffers must not alias f buffers of the same batch.
+   POISSON_THEN_INTFACTOR writes E_alpha(G_L * f) into u_dev.  Results equal
+   those of the single applies bit for bit.  Errors: as the single applies. */
 LGF_API lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob, void *stream);
 
 /* FP64 residual check of the discrete Poisson problem (Sec. 2.2, Eq. dpoisson):

@@ -171,25 +171,37 @@ def spread_to_blocks(b: int, coords: np.ndarray, X: np.ndarray, F: np.ndarray) -
     """Spread marker forces F [nm][3] at positions X [nm][3] (cell units) onto
     the three face lattices, restricted to the given blocks: returns
     [3][nblk][b^3].  Points outside the block set are dropped."""
-    lut = {tuple(c): i for i, c in enumerate(coords.tolist())}
+    coords = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
     out = np.zeros((3, coords.shape[0], b ** 3))
+    if coords.shape[0] == 0:
+        return out
+    lo = coords.min(axis=0)
+    ext = coords.max(axis=0) - lo + 1
+    lut = -np.ones(tuple(ext[::-1]), dtype=np.int64)          # [z][y][x] -> block index
+    c = coords - lo
+    lut[c[:, 2], c[:, 1], c[:, 0]] = np.arange(coords.shape[0])
     for k, n, w, mi in support_points(X):
-        blk = np.floor_divide(n, b)
-        loc = n - blk * b
-        idx = np.array([lut.get(tuple(bb), -1) for bb in blk.tolist()])
+        blk = np.floor_divide(n, b) - lo
+        inside = np.all((blk >= 0) & (blk < ext), axis=1)
+        idx = -np.ones(n.shape[0], dtype=np.int64)
+        bi = blk[inside]
+        idx[inside] = lut[bi[:, 2], bi[:, 1], bi[:, 0]]
         ok = idx >= 0
-        lin = (loc[ok, 2] * b + loc[ok, 1]) * b + loc[ok, 0]
+        loc = n[ok] - np.floor_divide(n[ok], b) * b
+        lin = (loc[:, 2] * b + loc[:, 1]) * b + loc[:, 0]
         np.add.at(out[k], (idx[ok], lin), w[ok] * F[mi[ok], k])
     return out
 
 
 def blocks_touched(b: int, X: np.ndarray) -> np.ndarray:
     """Blocks holding any face-lattice point that gets a non-zero weight from X."""
-    s = set()
-    for _, n, _, _ in support_points(X):
-        for bb in np.unique(np.floor_divide(n, b), axis=0).tolist():
-            s.add(tuple(bb))
-    return np.array(sorted(s), dtype=np.int32).reshape(-1, 3)
+    parts = [np.floor_divide(n, b) for _, n, _, _ in support_points(X)]
+    if not parts:
+        return np.zeros((0, 3), dtype=np.int32)
+    allb = np.concatenate(parts) + (1 << 20)
+    key = np.unique((allb[:, 0] << 42) | (allb[:, 1] << 21) | allb[:, 2])   # sorted by (x, y, z)
+    u = np.stack([key >> 42, (key >> 21) & ((1 << 21) - 1), key & ((1 << 21) - 1)], axis=1) - (1 << 20)
+    return u.astype(np.int32).reshape(-1, 3)
 
 
 # ----------------------------------------------------------------------------
@@ -332,20 +344,37 @@ def wake_mask_blocks(nbx: int = 16, nby: int = 8, nbz: int = 8, frac: float = 0.
 
 def curl_blob_field(b: int, coords: np.ndarray, centres: np.ndarray, amps: np.ndarray, sigma: float) -> np.ndarray:
     """Face-lattice samples of curl(A), A = sum_j a_j exp(-|x - c_j|^2/(2 sigma^2))
-    (vector amplitudes a_j): returns [3][nblk][b^3]."""
-    pts = block_point_coords(b, coords).reshape(-1, 3).astype(np.float64)
-    out = np.zeros((3, pts.shape[0]))
+    (vector amplitudes a_j): returns [3][nblk][b^3].  Each Gaussian factorises
+    over the three axes, so it is evaluated as per-axis factors broadcast over
+    the blocks."""
+    coords = np.asarray(coords, dtype=np.int64)
+    nb = coords.shape[0]
+    r = np.arange(b, dtype=np.float64)
+    out = np.zeros((3, nb, b, b, b))
+    s2 = sigma * sigma
     for k in range(3):
-        P = pts + face_offset(k)
-        acc = np.zeros(P.shape[0])
+        off = face_offset(k)
+        # axis positions of every block: [nblk][b]
+        pos = [coords[:, ax:ax + 1] * b + r[None, :] + off[ax] for ax in range(3)]
+        i, j = (k + 1) % 3, (k + 2) % 3
         for c, a in zip(centres, amps):
-            d = P - c
-            g = np.exp(-(d ** 2).sum(axis=1) / (2.0 * sigma * sigma)) / (sigma * sigma)
-            # (curl A)_k = d_i A_j - d_j A_i with (k, i, j) cyclic;  d_i exp = -d_i/s^2 exp
-            i, j = (k + 1) % 3, (k + 2) % 3
-            acc += -d[:, i] * g * a[j] + d[:, j] * g * a[i]
-        out[k] = acc
-    return out.reshape(3, coords.shape[0], b ** 3)
+            # blocks farther than 10 sigma on some axis get less than e^-50: skip them
+            near = np.ones(nb, dtype=bool)
+            for ax in range(3):
+                near &= np.abs(pos[ax] - c[ax]).min(axis=1) < 10.0 * sigma
+            if not near.any():
+                continue
+            d = [pos[ax][near] - c[ax] for ax in range(3)]
+            g = [np.exp(-d[ax] ** 2 / (2.0 * s2)) for ax in range(3)]
+            # (curl A)_k = d_i A_j - d_j A_i,  d_i exp(...) = -(x_i - c_i)/sigma^2 exp(...)
+            term_i = [g[0], g[1], g[2]]
+            term_i[i] = -d[i] * g[i] / s2          # d_i of the Gaussian
+            term_j = [g[0], g[1], g[2]]
+            term_j[j] = -d[j] * g[j] / s2          # d_j of the Gaussian
+            ti = term_i[2][:, :, None, None] * term_i[1][:, None, :, None] * term_i[0][:, None, None, :]
+            tj = term_j[2][:, :, None, None] * term_j[1][:, None, :, None] * term_j[0][:, None, None, :]
+            out[k][near] += a[j] * ti - a[i] * tj
+    return out.reshape(3, nb, b ** 3)
 
 
 def wake_domain(seed: int = 4, b: int = 32, nrhs: int = 4, shape=(512, 256, 256), nblobs: int = 32,

@@ -150,7 +150,7 @@ lgf_status prepare_intf(lgf_ctx *ctx, double alpha, const lgf_blockset *src, con
     if (st != LGF_OK) return st;
     st = intf_plan(ctx, src, tgt, pi->w->R, &pi->plan);
     if (st != LGF_OK) return st;
-    return intf_prepare_scratch(ctx, pi->plan, nfields);
+    return intf_prepare_scratch(ctx, pi->plan, nfields, 1);
 }
 
 }  // namespace
@@ -432,24 +432,41 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         put(&p.alpha, 2 * sizeof(double));
     }
     put(&s, sizeof(s));
-    // 2. prepare every plan, spectrum, weight set and the largest scratch
-    struct Item {
-        PreparedPoisson pp;
-        PreparedIntf pi;
+    // 2. prepare every plan, spectrum, weight set and the largest scratch;
+    //    integrating factors on the same block sets (and field count) form one
+    //    group that runs as one launch per pass
+    std::vector<PreparedPoisson> pois(nprob);
+    struct Group {
+        IntfPlan *plan;
+        int nf;
+        std::vector<IntfJob> jobs;
     };
-    std::vector<Item> items(nprob);
+    std::vector<Group> groups;
     for (int i = 0; i < nprob; ++i) {
         const lgf_problem &p = probs[i];
         const int nf = p.ncomp * p.nrhs;
         if (p.tgt.nblocks == 0 || p.src.nblocks == 0) continue;
         if (p.op != LGF_OP_INTFACTOR)
-            if ((st = prepare_poisson(ctx, &p.src, &p.tgt, nf, s, &items[i].pp)) != LGF_OK) return st;
-        if (p.op == LGF_OP_INTFACTOR)
-            if ((st = prepare_intf(ctx, p.alpha, &p.src, &p.tgt, nf, s, &items[i].pi)) != LGF_OK) return st;
-        if (p.op == LGF_OP_POISSON_THEN_INTFACTOR)
-            if ((st = prepare_intf(ctx, p.alpha, &p.tgt, &p.tgt, nf, s, &items[i].pi)) != LGF_OK) return st;
+            if ((st = prepare_poisson(ctx, &p.src, &p.tgt, nf, s, &pois[i])) != LGF_OK) return st;
+        if (p.op == LGF_OP_POISSON) continue;
+        PreparedIntf pi;
+        const lgf_blockset *isrc = p.op == LGF_OP_INTFACTOR ? &p.src : &p.tgt;
+        if ((st = prepare_intf(ctx, p.alpha, isrc, &p.tgt, nf, s, &pi)) != LGF_OK) return st;
+        const void *in = p.op == LGF_OP_INTFACTOR ? p.f_dev : p.u_dev;
+        Group *g = nullptr;
+        for (auto &q : groups)
+            if (q.plan == pi.plan && q.nf == nf) g = &q;
+        if (!g) {
+            groups.push_back(Group{pi.plan, nf, {}});
+            g = &groups.back();
+        }
+        g->jobs.push_back(IntfJob{pi.w, in, p.u_dev});
     }
+    for (auto &g : groups)
+        if ((st = intf_prepare_scratch(ctx, g.plan, g.nf, (int)g.jobs.size())) != LGF_OK) return st;
     auto enqueue = [&]() -> lgf_status {
+        // Poisson parts first (POISSON_THEN_INTFACTOR reads them back), then the
+        // integrating-factor groups.
         for (int i = 0; i < nprob; ++i) {
             const lgf_problem &p = probs[i];
             const int nf = p.ncomp * p.nrhs;
@@ -459,14 +476,13 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
                 LGF_CUDA(ctx, cudaMemsetAsync(p.u_dev, 0, (size_t)p.tgt.nblocks * b3 * nf * elem_size(ctx), s));
                 continue;
             }
-            lgf_status e2;
-            if (p.op != LGF_OP_INTFACTOR)
-                if ((e2 = poisson_run(ctx, items[i].pp.plan, items[i].pp.spec, p.f_dev, p.u_dev, nf, p.dx, s)) != LGF_OK)
-                    return e2;
-            if (p.op == LGF_OP_INTFACTOR)
-                if ((e2 = intf_run(ctx, items[i].pi.plan, items[i].pi.w, p.f_dev, p.u_dev, nf, s)) != LGF_OK) return e2;
-            if (p.op == LGF_OP_POISSON_THEN_INTFACTOR)
-                if ((e2 = intf_run(ctx, items[i].pi.plan, items[i].pi.w, p.u_dev, p.u_dev, nf, s)) != LGF_OK) return e2;
+            if (p.op == LGF_OP_INTFACTOR) continue;
+            lgf_status e2 = poisson_run(ctx, pois[i].plan, pois[i].spec, p.f_dev, p.u_dev, nf, p.dx, s);
+            if (e2 != LGF_OK) return e2;
+        }
+        for (auto &g : groups) {
+            lgf_status e2 = intf_run_jobs(ctx, g.plan, g.jobs.data(), (int)g.jobs.size(), g.nf, s);
+            if (e2 != LGF_OK) return e2;
         }
         return LGF_OK;
     };

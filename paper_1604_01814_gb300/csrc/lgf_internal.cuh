@@ -169,7 +169,13 @@ lgf_status poisson_prepare_scratch(lgf_ctx *ctx, const PoissonPlan *pl, int nfie
 // Integrating factor (lgf_intfactor.cu)
 lgf_status intf_weights(lgf_ctx *ctx, double alpha, IntfWeights **out, cudaStream_t s);
 lgf_status intf_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, int R, IntfPlan **out);
-lgf_status intf_prepare_scratch(lgf_ctx *ctx, const IntfPlan *pl, int nfields);
+lgf_status intf_prepare_scratch(lgf_ctx *ctx, const IntfPlan *pl, int nfields, int njobs);
+struct IntfJob {
+    const IntfWeights *w;
+    const void *f;
+    void *u;
+};
+lgf_status intf_run_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, int njobs, int nfields, cudaStream_t s);
 lgf_status intf_run(lgf_ctx *ctx, IntfPlan *pl, const IntfWeights *w, const void *f, void *u, int nfields,
                     cudaStream_t s);
 

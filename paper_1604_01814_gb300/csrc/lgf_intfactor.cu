@@ -19,26 +19,20 @@
 #include <unordered_map>
 #include <unordered_set>
 
-#include "lgf_internal.cuh"
+#include "lgf_intfactor_win.cuh"
 
 namespace lgf {
 
-// Register-window passes (lgf_intfactor_win.cuh, instantiated per precision).
-template <typename T>
-lgf_status launch_sep_window(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
-                             const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done);
-template <typename T>
-lgf_status launch_sep_xy(lgf_ctx *ctx, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
-                         const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done);
-extern template lgf_status launch_sep_xy<float>(lgf_ctx *, int, int, int, cudaStream_t, const float *, float *,
-                                                const int *, const float *, int, int, int64_t, int64_t, bool *);
-extern template lgf_status launch_sep_xy<double>(lgf_ctx *, int, int, int, cudaStream_t, const double *, double *,
-                                                 const int *, const double *, int, int, int64_t, int64_t, bool *);
-extern template lgf_status launch_sep_window<float>(lgf_ctx *, int, int, int, int, cudaStream_t, const float *, float *,
-                                                    const int *, const float *, int, int, int64_t, int64_t, bool *);
-extern template lgf_status launch_sep_window<double>(lgf_ctx *, int, int, int, int, cudaStream_t, const double *,
-                                                     double *, const int *, const double *, int, int, int64_t, int64_t,
-                                                     bool *);
+// Register-window passes: templates in lgf_intfactor_win.cuh, instantiated
+// per precision in lgf_intfactor_win_f32.cu / lgf_intfactor_win_f64.cu.
+extern template lgf_status launch_sep_window<float>(lgf_ctx *, int, int, int, const SepJobs<float> &, cudaStream_t,
+                                                    const int *, int, bool *);
+extern template lgf_status launch_sep_window<double>(lgf_ctx *, int, int, int, const SepJobs<double> &, cudaStream_t,
+                                                     const int *, int, bool *);
+extern template lgf_status launch_sep_xy<float>(lgf_ctx *, int, int, const SepJobs<float> &, cudaStream_t, const int *,
+                                                int, bool *);
+extern template lgf_status launch_sep_xy<double>(lgf_ctx *, int, int, const SepJobs<double> &, cudaStream_t,
+                                                 const int *, int, bool *);
 
 IntfPlan::~IntfPlan()
 {
@@ -350,13 +344,14 @@ lgf_status intf_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *
     return LGF_OK;
 }
 
-lgf_status intf_prepare_scratch(lgf_ctx *ctx, const IntfPlan *pl, int nfields)
+lgf_status intf_prepare_scratch(lgf_ctx *ctx, const IntfPlan *pl, int nfields, int njobs)
 {
     const size_t esz = ctx->prec == LGF_F64 ? 8 : 4;
     const size_t b3 = (size_t)pl->b * pl->b * pl->b;
     lgf_status st = ensure_scratch(ctx, &ctx->scrA, &ctx->scrA_bytes, std::max<size_t>(1, pl->n1) * b3 * nfields * esz);
     if (st != LGF_OK) return st;
-    return ensure_scratch(ctx, &ctx->scrB, &ctx->scrB_bytes, std::max<size_t>(1, pl->n2) * b3 * nfields * esz);
+    return ensure_scratch(ctx, &ctx->scrB, &ctx->scrB_bytes,
+                          std::max<size_t>(1, pl->n2) * b3 * nfields * esz * (size_t)std::max(1, njobs));
 }
 
 // Region staging parameters shared by both launch paths.
@@ -408,7 +403,11 @@ lgf_status launch_sep(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaSt
                       const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr)
 {
     bool done = false;
-    lgf_status wst = launch_sep_window<T>(ctx, ax, b, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr, &done);
+    SepJobs<T> jobs{};
+    jobs.n = 1;
+    jobs.nf = nfields;
+    jobs.j[0] = SepJob<T>{in, out, w, R, 0, istr, ostr};
+    lgf_status wst = launch_sep_window<T>(ctx, ax, b, nout, jobs, s, nbr, nr, &done);
     if (wst != LGF_OK) return wst;
     if (done) {
         LGF_CHECK_LAUNCH(ctx, "intfactor pass");
@@ -426,64 +425,96 @@ lgf_status launch_sep(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaSt
     return LGF_OK;
 }
 
+// All jobs of one plan: fused x+y then z launches over the whole job list
+// (chunks of kMaxSepJobs) when the window kernels apply, else the three
+// generic passes job by job.
 template <typename T>
-static lgf_status run_sep(lgf_ctx *ctx, IntfPlan *pl, const T *w, int R, const T *f, T *u, int nfields,
-                          cudaStream_t s)
+static lgf_status run_sep_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, int njobs, int nfields,
+                               cudaStream_t s)
 {
     const int b = pl->b, nr = pl->nr;
     const int64_t b3 = (int64_t)b * b * b;
     const int nsrc = (int)(pl->src.size() / 3), ntgt = (int)(pl->tgt.size() / 3);
-    T *X1 = (T *)ctx->scrA, *Y2 = (T *)ctx->scrB;
-    const T *ins[3] = {f, X1, Y2};
-    T *outs[3] = {X1, Y2, u};
-    const int64_t istr[3] = {nsrc * b3, pl->n1 * b3, pl->n2 * b3};
-    const int64_t ostr[3] = {pl->n1 * b3, pl->n2 * b3, ntgt * b3};
-    static const char *names[3] = {"intfactor_pass_x", "intfactor_pass_y", "intfactor_pass_z"};
-    if (pl->n2 > 0 && pl->pass[2].nout > 0) {   // fused x+y pass, then z, when the window kernels apply
-        const int ph = prof_begin(ctx, s, "intfactor_pass_xy");
-        bool done = false;
-        lgf_status st = launch_sep_xy<T>(ctx, b, pl->n2, nfields, s, f, Y2, pl->nbr_xy_dev, w, R, nr, istr[0], ostr[1],
-                                         &done);
-        if (st != LGF_OK) return st;
-        if (done) {
+    const int64_t y2f = (int64_t)pl->n2 * b3;                       // Y2 elements per field
+    T *X1 = (T *)ctx->scrA, *Y2all = (T *)ctx->scrB;
+    auto wptr = [](const IntfJob &j) -> const T * {
+        return sizeof(T) == 8 ? (const T *)(const void *)j.w->w64 : (const T *)(const void *)j.w->w32;
+    };
+    int first_generic = 0;
+    if (pl->n2 > 0 && pl->pass[2].nout > 0) {
+        first_generic = njobs;
+        for (int c0 = 0; c0 < njobs; c0 += kMaxSepJobs) {
+            const int cn = std::min(kMaxSepJobs, njobs - c0);
+            SepJobs<T> jx{}, jz{};
+            jx.n = jz.n = cn;
+            jx.nf = jz.nf = nfields;
+            for (int i = 0; i < cn; ++i) {
+                const IntfJob &J = jobs[c0 + i];
+                T *y2 = Y2all + (int64_t)(c0 + i) * y2f * nfields;
+                jx.j[i] = SepJob<T>{(const T *)J.f, y2, wptr(J), J.w->R, 0, nsrc * b3, y2f};
+                jz.j[i] = SepJob<T>{y2, (T *)J.u, wptr(J), J.w->R, 0, y2f, ntgt * b3};
+            }
+            const int ph = prof_begin(ctx, s, "intfactor_pass_xy");
+            bool done = false;
+            lgf_status st = launch_sep_xy<T>(ctx, b, pl->n2, jx, s, pl->nbr_xy_dev, nr, &done);
+            if (st != LGF_OK) return st;
+            if (!done) {
+                prof_end(ctx, s, ph);
+                first_generic = c0;
+                break;
+            }
             LGF_CHECK_LAUNCH(ctx, "intfactor xy pass");
             prof_end(ctx, s, ph);
-            const int pz = prof_begin(ctx, s, names[2]);
-            st = launch_sep<T>(ctx, 2, b, pl->pass[2].nout, nfields, s, Y2, u, pl->pass[2].nbr_dev, w, R, nr, istr[2],
-                               ostr[2]);
+            const int pz = prof_begin(ctx, s, "intfactor_pass_z");
+            st = launch_sep_window<T>(ctx, 2, b, ntgt, jz, s, pl->pass[2].nbr_dev, nr, &done);
             if (st != LGF_OK) return st;
+            if (!done) return fail(ctx, LGF_ECUDA, "intfactor: z window pass unavailable after the xy pass");
+            LGF_CHECK_LAUNCH(ctx, "intfactor z pass");
             prof_end(ctx, s, pz);
-            return LGF_OK;
         }
-        prof_end(ctx, s, ph);
     }
-    for (int p = 0; p < 3; ++p) {
-        if (pl->pass[p].nout == 0) continue;
-        const int ph = prof_begin(ctx, s, names[p]);
-        lgf_status st = launch_sep<T>(ctx, p, b, pl->pass[p].nout, nfields, s, ins[p], outs[p], pl->pass[p].nbr_dev, w,
-                                      R, nr, istr[p], ostr[p]);
-        if (st != LGF_OK) return st;
-        prof_end(ctx, s, ph);
+    static const char *names[3] = {"intfactor_pass_x", "intfactor_pass_y", "intfactor_pass_z"};
+    for (int jb = first_generic; jb < njobs; ++jb) {
+        const IntfJob &J = jobs[jb];
+        T *Y2 = Y2all;
+        const T *ins[3] = {(const T *)J.f, X1, Y2};
+        T *outs[3] = {X1, Y2, (T *)J.u};
+        const int64_t istr[3] = {nsrc * b3, pl->n1 * b3, pl->n2 * b3};
+        const int64_t ostr[3] = {pl->n1 * b3, pl->n2 * b3, ntgt * b3};
+        for (int p = 0; p < 3; ++p) {
+            if (pl->pass[p].nout == 0) continue;
+            const int ph = prof_begin(ctx, s, names[p]);
+            lgf_status st = launch_sep<T>(ctx, p, b, pl->pass[p].nout, nfields, s, ins[p], outs[p],
+                                          pl->pass[p].nbr_dev, wptr(J), J.w->R, nr, istr[p], ostr[p]);
+            if (st != LGF_OK) return st;
+            prof_end(ctx, s, ph);
+        }
     }
     return LGF_OK;
 }
 
-lgf_status intf_run(lgf_ctx *ctx, IntfPlan *pl, const IntfWeights *w, const void *f, void *u, int nfields,
-                    cudaStream_t s)
+lgf_status intf_run_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, int njobs, int nfields, cudaStream_t s)
 {
-    lgf_status st = intf_prepare_scratch(ctx, pl, nfields);
+    lgf_status st = intf_prepare_scratch(ctx, pl, nfields, njobs);
     if (st != LGF_OK) return st;
     const int ntgt = (int)(pl->tgt.size() / 3);
     const size_t esz = ctx->prec == LGF_F64 ? 8 : 4;
     const size_t b3 = (size_t)pl->b * pl->b * pl->b;
     if (pl->pass[2].nout > 0 && pl->n2 == 0) {
-        // no source reaches any target: the result is zero
-        LGF_CUDA(ctx, cudaMemsetAsync(u, 0, (size_t)ntgt * b3 * nfields * esz, s));
+        // no source reaches any target: the results are zero
+        for (int j = 0; j < njobs; ++j)
+            LGF_CUDA(ctx, cudaMemsetAsync(jobs[j].u, 0, (size_t)ntgt * b3 * nfields * esz, s));
         return LGF_OK;
     }
-    if (ctx->prec == LGF_F64)
-        return run_sep<double>(ctx, pl, w->w64, w->R, (const double *)f, (double *)u, nfields, s);
-    return run_sep<float>(ctx, pl, w->w32, w->R, (const float *)f, (float *)u, nfields, s);
+    if (ctx->prec == LGF_F64) return run_sep_jobs<double>(ctx, pl, jobs, njobs, nfields, s);
+    return run_sep_jobs<float>(ctx, pl, jobs, njobs, nfields, s);
+}
+
+lgf_status intf_run(lgf_ctx *ctx, IntfPlan *pl, const IntfWeights *w, const void *f, void *u, int nfields,
+                    cudaStream_t s)
+{
+    const IntfJob job{w, f, u};
+    return intf_run_jobs(ctx, pl, &job, 1, nfields, s);
 }
 
 }  // namespace lgf

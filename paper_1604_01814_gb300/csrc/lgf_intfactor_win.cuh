@@ -30,6 +30,29 @@ struct Vec<double> {
 
 constexpr int kV = 4;   // outputs per thread along the pass axis
 
+}  // namespace win
+
+// One integrating-factor apply inside a grouped launch: its own input,
+// output, weights and radius; the block sets (neighbour tables) are shared.
+template <typename T>
+struct SepJob {
+    const T *in;
+    T *out;
+    const T *w;
+    int R;
+    int pad;
+    int64_t in_stride, out_stride;   // elements per field
+};
+constexpr int kMaxSepJobs = 8;
+template <typename T>
+struct SepJobs {
+    SepJob<T> j[kMaxSepJobs];
+    int n;    // jobs in this launch
+    int nf;   // fields per job (grid.z = n * nf)
+};
+
+namespace win {
+
 // Threads per CTA and slab extent for block edge b = 2^LB.
 template <typename T, int LB, int AX>
 struct Cfg {
@@ -44,9 +67,12 @@ struct Cfg {
 
 template <typename T, int LB, int AX, int RMAX>
 __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
-    k_sep_win(const T *__restrict__ in, T *__restrict__ out, const int *__restrict__ nbr, const T *__restrict__ wg,
-              int R, int nr, int64_t in_stride, int64_t out_stride)
+    k_sep_win(const SepJobs<T> jobs, const int *__restrict__ nbr, int nr)
 {
+    const SepJob<T> &J = jobs.j[blockIdx.z / jobs.nf];
+    const int field = blockIdx.z % jobs.nf;
+    const T *__restrict__ wg = J.w;
+    const int R = J.R;
     using C = Cfg<T, LB, AX>;
     using VT = typename Vec<T>::V;
     constexpr int b = C::b, bm = b - 1, NV = C::NV, NS = C::NS, HL = RMAX, E = b + 2 * HL;
@@ -56,8 +82,8 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
     const int s0 = blockIdx.y * NS;
     const int nd = 2 * nr + 1;
     const int *nb = nbr + (int64_t)o * nd;
-    const T *inf = in + blockIdx.z * in_stride;
-    T *outf = out + blockIdx.z * out_stride;
+    const T *inf = J.in + field * J.in_stride;
+    T *outf = J.out + field * J.out_stride;
 
     // ---- stage [slab + halo] with 16-byte loads ----
     constexpr int rowlen = AX == 0 ? E : b;
@@ -195,10 +221,12 @@ struct XYCfg {
 };
 
 template <typename T, int LB, int RMAX>
-__global__ void __launch_bounds__(256) k_sep_xy(const T *__restrict__ in, T *__restrict__ out,
-                                                 const int *__restrict__ nbr, const T *__restrict__ wg, int R, int nr,
-                                                 int64_t in_stride, int64_t out_stride)
+__global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int *__restrict__ nbr, int nr)
 {
+    const SepJob<T> &J = jobs.j[blockIdx.z / jobs.nf];
+    const int field = blockIdx.z % jobs.nf;
+    const T *__restrict__ wg = J.w;
+    const int R = J.R;
     using C = XYCfg<T, LB, RMAX>;
     using VT = typename Vec<T>::V;
     constexpr int b = C::b, bm = b - 1, NV = Vec<T>::N, NS = C::NSB, HL = RMAX, E = C::E;
@@ -209,8 +237,8 @@ __global__ void __launch_bounds__(256) k_sep_xy(const T *__restrict__ in, T *__r
     const int s0 = blockIdx.y * NS;
     const int nd = 2 * nr + 1;
     const int *nb = nbr + (int64_t)o * nd * nd;
-    const T *inf = in + blockIdx.z * in_stride;
-    T *outf = out + blockIdx.z * out_stride;
+    const T *inf = J.in + field * J.in_stride;
+    T *outf = J.out + field * J.out_stride;
     // ---- stage ----
     constexpr int vpr = E / NV;
     constexpr int total = NS * E * vpr;
@@ -312,8 +340,7 @@ __global__ void __launch_bounds__(256) k_sep_xy(const T *__restrict__ in, T *__r
 }
 
 template <typename T, int LB, int RMAX>
-lgf_status launch_xy_m(lgf_ctx *ctx, int nout, int nfields, cudaStream_t s, const T *in, T *out, const int *nbr,
-                       const T *w, int R, int nr, int64_t istr, int64_t ostr)
+lgf_status launch_xy_m(lgf_ctx *ctx, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr, int nr)
 {
     using C = XYCfg<T, LB, RMAX>;
     auto kern = k_sep_xy<T, LB, RMAX>;
@@ -321,25 +348,24 @@ lgf_status launch_xy_m(lgf_ctx *ctx, int nout, int nfields, cudaStream_t s, cons
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
     }
-    dim3 grid(nout, C::b / C::NSB, nfields);
-    kern<<<grid, 256, C::SMEM, s>>>(in, out, nbr, w, R, nr, istr, ostr);
+    dim3 grid(nout, C::b / C::NSB, jobs.n * jobs.nf);
+    kern<<<grid, 256, C::SMEM, s>>>(jobs, nbr, nr);
     return LGF_OK;
 }
 
 template <typename T, int LB>
-lgf_status launch_xy_r(lgf_ctx *ctx, int rmax, int nout, int nfields, cudaStream_t s, const T *in, T *out,
-                       const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr)
+lgf_status launch_xy_r(lgf_ctx *ctx, int rmax, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr,
+                       int nr)
 {
     switch (rmax) {
-    case 4: return launch_xy_m<T, LB, 4>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
-    case 8: return launch_xy_m<T, LB, 8>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
-    default: return launch_xy_m<T, LB, 16>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    case 4: return launch_xy_m<T, LB, 4>(ctx, nout, jobs, s, nbr, nr);
+    case 8: return launch_xy_m<T, LB, 8>(ctx, nout, jobs, s, nbr, nr);
+    default: return launch_xy_m<T, LB, 16>(ctx, nout, jobs, s, nbr, nr);
     }
 }
 
 template <typename T, int LB, int AX, int RMAX>
-lgf_status launch_m(lgf_ctx *ctx, int nout, int nfields, cudaStream_t s, const T *in, T *out, const int *nbr,
-                    const T *w, int R, int nr, int64_t istr, int64_t ostr)
+lgf_status launch_m(lgf_ctx *ctx, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr, int nr)
 {
     using C = Cfg<T, LB, AX>;
     constexpr int b = 1 << LB, E = b + 2 * RMAX;
@@ -349,57 +375,64 @@ lgf_status launch_m(lgf_ctx *ctx, int nout, int nfields, cudaStream_t s, const T
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
     }
-    dim3 grid(nout, b / C::NS, nfields);
-    kern<<<grid, C::THREADS, smem, s>>>(in, out, nbr, w, R, nr, istr, ostr);
+    dim3 grid(nout, b / C::NS, jobs.n * jobs.nf);
+    kern<<<grid, C::THREADS, smem, s>>>(jobs, nbr, nr);
     return LGF_OK;
 }
 
 template <typename T, int LB, int AX>
-lgf_status launch_r(lgf_ctx *ctx, int rmax, int nout, int nfields, cudaStream_t s, const T *in, T *out,
-                    const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr)
+lgf_status launch_r(lgf_ctx *ctx, int rmax, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr, int nr)
 {
     switch (rmax) {
-    case 4: return launch_m<T, LB, AX, 4>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
-    case 8: return launch_m<T, LB, AX, 8>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
-    default: return launch_m<T, LB, AX, 16>(ctx, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    case 4: return launch_m<T, LB, AX, 4>(ctx, nout, jobs, s, nbr, nr);
+    case 8: return launch_m<T, LB, AX, 8>(ctx, nout, jobs, s, nbr, nr);
+    default: return launch_m<T, LB, AX, 16>(ctx, nout, jobs, s, nbr, nr);
     }
 }
 
 }  // namespace win
 
-// Fused x+y pass (S -> Y2 with the (2nr+1)^2 xy neighbour table) under the same
-// eligibility as launch_sep_window.
+// Largest radius of a job list, rounded up to a window bound (0: none fits).
 template <typename T>
-lgf_status launch_sep_xy(lgf_ctx *ctx, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
-                         const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done)
+inline int window_rmax(const SepJobs<T> &jobs, int b, int nr)
 {
-    *done = false;
+    int R = 0;
+    for (int i = 0; i < jobs.n; ++i) R = jobs.j[i].R > R ? jobs.j[i].R : R;
     const int rmax = R <= 4 ? 4 : R <= 8 ? 8 : R <= 16 ? 16 : 0;
-    if (rmax == 0 || rmax > nr * b || (b != 8 && b != 16 && b != 32)) return LGF_OK;
-    *done = true;
+    if (rmax == 0 || rmax > nr * b || (b != 8 && b != 16 && b != 32)) return 0;
+    return rmax;
+}
+
+// Fused x+y pass (S -> Y2 with the (2nr+1)^2 xy neighbour table) for a job list;
+// *done tells whether the window kernels applied.
+template <typename T>
+lgf_status launch_sep_xy(lgf_ctx *ctx, int b, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr,
+                         int nr, bool *done)
+{
+    const int rmax = window_rmax(jobs, b, nr);
+    *done = rmax > 0;
+    if (!*done) return LGF_OK;
     switch (b) {
-    case 8: return win::launch_xy_r<T, 3>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
-    case 16: return win::launch_xy_r<T, 4>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
-    default: return win::launch_xy_r<T, 5>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr);
+    case 8: return win::launch_xy_r<T, 3>(ctx, rmax, nout, jobs, s, nbr, nr);
+    case 16: return win::launch_xy_r<T, 4>(ctx, rmax, nout, jobs, s, nbr, nr);
+    default: return win::launch_xy_r<T, 5>(ctx, rmax, nout, jobs, s, nbr, nr);
     }
 }
 
-// Window-kernel pass if (b, R, nr) qualify (b in {8, 16, 32}, R <= 16 and the
-// rounded radius within the staged neighbours); *done tells whether it ran.
+// Single-axis window pass for a job list.
 template <typename T>
-lgf_status launch_sep_window(lgf_ctx *ctx, int ax, int b, int nout, int nfields, cudaStream_t s, const T *in, T *out,
-                             const int *nbr, const T *w, int R, int nr, int64_t istr, int64_t ostr, bool *done)
+lgf_status launch_sep_window(lgf_ctx *ctx, int ax, int b, int nout, const SepJobs<T> &jobs, cudaStream_t s,
+                             const int *nbr, int nr, bool *done)
 {
-    *done = false;
-    const int rmax = R <= 4 ? 4 : R <= 8 ? 8 : R <= 16 ? 16 : 0;
-    if (rmax == 0 || rmax > nr * b || (b != 8 && b != 16 && b != 32)) return LGF_OK;
-    *done = true;
+    const int rmax = window_rmax(jobs, b, nr);
+    *done = rmax > 0;
+    if (!*done) return LGF_OK;
     const int lb = b == 8 ? 3 : b == 16 ? 4 : 5;
-#define LGF_WIN_AX(AXV)                                                                                       \
-    switch (lb) {                                                                                             \
-    case 3: return win::launch_r<T, 3, AXV>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr); \
-    case 4: return win::launch_r<T, 4, AXV>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr); \
-    default: return win::launch_r<T, 5, AXV>(ctx, rmax, nout, nfields, s, in, out, nbr, w, R, nr, istr, ostr); \
+#define LGF_WIN_AX(AXV)                                                                           \
+    switch (lb) {                                                                                 \
+    case 3: return win::launch_r<T, 3, AXV>(ctx, rmax, nout, jobs, s, nbr, nr);                   \
+    case 4: return win::launch_r<T, 4, AXV>(ctx, rmax, nout, jobs, s, nbr, nr);                   \
+    default: return win::launch_r<T, 5, AXV>(ctx, rmax, nout, jobs, s, nbr, nr);                  \
     }
     if (ax == 0) {
         LGF_WIN_AX(0)

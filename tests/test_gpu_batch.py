@@ -73,3 +73,27 @@ def test_batch_on_default_stream_runs_without_graph(ctx32):
     torch.cuda.synchronize()
     for q, r in zip(batch, ref):
         assert torch.equal(q["u"], r)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_grouped_integrating_factors_equal_single_applies(prec, ctx32, ctx64):
+    """Integrating factors on the same block sets run as one grouped launch
+    per pass; each result equals its single apply bit for bit."""
+    ctx = ctx32 if prec == "f32" else ctx64
+    p = li.random_sparse(31, b=16, nsrc=5, ntgt=6, extent=(3, 3, 2), ncomp=2)
+    alphas = [0.05, 0.3, 0.5, 1.0, 2.0, 0.01, 0.7, 1.5, 0.2, 0.4]   # more than 8: two launches per pass
+    rng = np.random.default_rng(9)
+    batch, ref = [], []
+    for a in alphas:
+        f = torch.tensor(rng.uniform(-1, 1, p.f.size), dtype=ctx.dtype, device="cuda")
+        u = torch.full((p.ncomp * p.tgt.shape[0] * p.b ** 3,), float("nan"), dtype=ctx.dtype, device="cuda")
+        batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, op=lgf.LGF_OP_INTFACTOR, alpha=a))
+        r = torch.empty_like(u)
+        ctx.intfactor_apply(a, p.b, p.src, p.tgt, f, r, ncomp=p.ncomp)
+        ref.append(r)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx.batch_apply(batch, stream=s)
+    s.synchronize()
+    for q, r in zip(batch, ref):
+        assert torch.equal(q["u"], r)
