@@ -227,6 +227,10 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
     cudaFree(ctx->scrA);
     cudaFree(ctx->scrB);
     cudaFree(ctx->scrC);
+    cudaFree(ctx->scrD);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     cudaFree(ctx->red_dev);
     for (auto &r : ctx->prof_pending) {
         cudaEventDestroy(r.a);
@@ -439,6 +443,7 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     struct Group {
         IntfPlan *plan;
         int nf;
+        bool after_poisson;   // reads outputs of the batch's Poisson parts
         std::vector<IntfJob> jobs;
     };
     std::vector<Group> groups;
@@ -453,20 +458,41 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         const lgf_blockset *isrc = p.op == LGF_OP_INTFACTOR ? &p.src : &p.tgt;
         if ((st = prepare_intf(ctx, p.alpha, isrc, &p.tgt, nf, s, &pi)) != LGF_OK) return st;
         const void *in = p.op == LGF_OP_INTFACTOR ? p.f_dev : p.u_dev;
+        const bool after = p.op == LGF_OP_POISSON_THEN_INTFACTOR;
         Group *g = nullptr;
         for (auto &q : groups)
-            if (q.plan == pi.plan && q.nf == nf) g = &q;
+            if (q.plan == pi.plan && q.nf == nf && q.after_poisson == after) g = &q;
         if (!g) {
-            groups.push_back(Group{pi.plan, nf, {}});
+            groups.push_back(Group{pi.plan, nf, after, {}});
             g = &groups.back();
         }
         g->jobs.push_back(IntfJob{pi.w, in, p.u_dev});
     }
     for (auto &g : groups)
         if ((st = intf_prepare_scratch(ctx, g.plan, g.nf, (int)g.jobs.size())) != LGF_OK) return st;
+    bool any_poisson = false, any_free = false;
+    for (int i = 0; i < nprob; ++i) any_poisson |= pois[i].plan != nullptr;
+    for (auto &g : groups) any_free |= !g.after_poisson;
+    const bool fork = any_poisson && any_free && !ctx->prof;   // profiling times kernels one at a time
+    if (fork && !ctx->side) {
+        LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
     auto enqueue = [&]() -> lgf_status {
-        // Poisson parts first (POISSON_THEN_INTFACTOR reads them back), then the
-        // integrating-factor groups.
+        // Integrating factors that read only batch inputs run on a second
+        // branch, concurrent with the Poisson parts (separate scratch); those
+        // that read Poisson outputs run after the join.
+        if (fork) {
+            LGF_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+            LGF_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+            for (auto &g : groups) {
+                if (g.after_poisson) continue;
+                lgf_status e2 = intf_run_jobs(ctx, g.plan, g.jobs.data(), (int)g.jobs.size(), g.nf, ctx->side);
+                if (e2 != LGF_OK) return e2;
+            }
+            LGF_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+        }
         for (int i = 0; i < nprob; ++i) {
             const lgf_problem &p = probs[i];
             const int nf = p.ncomp * p.nrhs;
@@ -480,7 +506,9 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
             lgf_status e2 = poisson_run(ctx, pois[i].plan, pois[i].spec, p.f_dev, p.u_dev, nf, p.dx, s);
             if (e2 != LGF_OK) return e2;
         }
+        if (fork) LGF_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
         for (auto &g : groups) {
+            if (fork && !g.after_poisson) continue;
             lgf_status e2 = intf_run_jobs(ctx, g.plan, g.jobs.data(), (int)g.jobs.size(), g.nf, s);
             if (e2 != LGF_OK) return e2;
         }

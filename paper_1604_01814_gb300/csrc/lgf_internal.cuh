@@ -106,9 +106,15 @@ struct lgf_ctx {
     std::vector<std::unique_ptr<lgf::IntfPlan>> iplans;
     std::vector<std::unique_ptr<lgf::IntfWeights>> weights;
 
-    // grow-only scratch
-    void *scrA = nullptr, *scrB = nullptr, *scrC = nullptr;
-    size_t scrA_bytes = 0, scrB_bytes = 0, scrC_bytes = 0;
+    // grow-only scratch: A, B for the Poisson passes; C, D for the integrating
+    // factor (so that the two can run on concurrent graph branches)
+    void *scrA = nullptr, *scrB = nullptr, *scrC = nullptr, *scrD = nullptr;
+    size_t scrA_bytes = 0, scrB_bytes = 0, scrC_bytes = 0, scrD_bytes = 0;
+
+    // second stream for the concurrent branch of lgf_batch_apply, and the
+    // fork/join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // batch graph cache
     std::vector<unsigned char> graph_key;

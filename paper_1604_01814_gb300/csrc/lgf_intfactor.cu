@@ -348,9 +348,9 @@ lgf_status intf_prepare_scratch(lgf_ctx *ctx, const IntfPlan *pl, int nfields, i
 {
     const size_t esz = ctx->prec == LGF_F64 ? 8 : 4;
     const size_t b3 = (size_t)pl->b * pl->b * pl->b;
-    lgf_status st = ensure_scratch(ctx, &ctx->scrA, &ctx->scrA_bytes, std::max<size_t>(1, pl->n1) * b3 * nfields * esz);
+    lgf_status st = ensure_scratch(ctx, &ctx->scrC, &ctx->scrC_bytes, std::max<size_t>(1, pl->n1) * b3 * nfields * esz);
     if (st != LGF_OK) return st;
-    return ensure_scratch(ctx, &ctx->scrB, &ctx->scrB_bytes,
+    return ensure_scratch(ctx, &ctx->scrD, &ctx->scrD_bytes,
                           std::max<size_t>(1, pl->n2) * b3 * nfields * esz * (size_t)std::max(1, njobs));
 }
 
@@ -436,20 +436,28 @@ static lgf_status run_sep_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, 
     const int64_t b3 = (int64_t)b * b * b;
     const int nsrc = (int)(pl->src.size() / 3), ntgt = (int)(pl->tgt.size() / 3);
     const int64_t y2f = (int64_t)pl->n2 * b3;                       // Y2 elements per field
-    T *X1 = (T *)ctx->scrA, *Y2all = (T *)ctx->scrB;
+    T *X1 = (T *)ctx->scrC, *Y2all = (T *)ctx->scrD;
     auto wptr = [](const IntfJob &j) -> const T * {
         return sizeof(T) == 8 ? (const T *)(const void *)j.w->w64 : (const T *)(const void *)j.w->w32;
     };
+    // jobs in order of their window class, so that a launch never pays for a
+    // larger radius than its own jobs need
+    std::vector<int> order(njobs);
+    for (int i = 0; i < njobs; ++i) order[i] = i;
+    auto cls_key = [&](int i) { const int c = window_class(jobs[i].w->R); return c == 0 ? 1 << 20 : c; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cls_key(a) < cls_key(c); });
     int first_generic = 0;
     if (pl->n2 > 0 && pl->pass[2].nout > 0) {
         first_generic = njobs;
-        for (int c0 = 0; c0 < njobs; c0 += kMaxSepJobs) {
-            const int cn = std::min(kMaxSepJobs, njobs - c0);
+        for (int c0 = 0; c0 < njobs;) {
+            int cn = 0;
+            const int cls = window_class(jobs[order[c0]].w->R);
+            while (c0 + cn < njobs && cn < kMaxSepJobs && window_class(jobs[order[c0 + cn]].w->R) == cls) ++cn;
             SepJobs<T> jx{}, jz{};
             jx.n = jz.n = cn;
             jx.nf = jz.nf = nfields;
             for (int i = 0; i < cn; ++i) {
-                const IntfJob &J = jobs[c0 + i];
+                const IntfJob &J = jobs[order[c0 + i]];
                 T *y2 = Y2all + (int64_t)(c0 + i) * y2f * nfields;
                 jx.j[i] = SepJob<T>{(const T *)J.f, y2, wptr(J), J.w->R, 0, nsrc * b3, y2f};
                 jz.j[i] = SepJob<T>{y2, (T *)J.u, wptr(J), J.w->R, 0, y2f, ntgt * b3};
@@ -460,7 +468,7 @@ static lgf_status run_sep_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, 
             if (st != LGF_OK) return st;
             if (!done) {
                 prof_end(ctx, s, ph);
-                first_generic = c0;
+                first_generic = c0;   // (classes only grow: every later chunk falls back too)
                 break;
             }
             LGF_CHECK_LAUNCH(ctx, "intfactor xy pass");
@@ -471,11 +479,12 @@ static lgf_status run_sep_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, 
             if (!done) return fail(ctx, LGF_ECUDA, "intfactor: z window pass unavailable after the xy pass");
             LGF_CHECK_LAUNCH(ctx, "intfactor z pass");
             prof_end(ctx, s, pz);
+            c0 += cn;
         }
     }
     static const char *names[3] = {"intfactor_pass_x", "intfactor_pass_y", "intfactor_pass_z"};
-    for (int jb = first_generic; jb < njobs; ++jb) {
-        const IntfJob &J = jobs[jb];
+    for (int jo = first_generic; jo < njobs; ++jo) {
+        const IntfJob &J = jobs[order[jo]];
         T *Y2 = Y2all;
         const T *ins[3] = {(const T *)J.f, X1, Y2};
         T *outs[3] = {X1, Y2, (T *)J.u};

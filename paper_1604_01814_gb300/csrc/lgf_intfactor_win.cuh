@@ -360,6 +360,7 @@ lgf_status launch_xy_r(lgf_ctx *ctx, int rmax, int nout, const SepJobs<T> &jobs,
     switch (rmax) {
     case 4: return launch_xy_m<T, LB, 4>(ctx, nout, jobs, s, nbr, nr);
     case 8: return launch_xy_m<T, LB, 8>(ctx, nout, jobs, s, nbr, nr);
+    case 12: return launch_xy_m<T, LB, 12>(ctx, nout, jobs, s, nbr, nr);
     default: return launch_xy_m<T, LB, 16>(ctx, nout, jobs, s, nbr, nr);
     }
 }
@@ -386,11 +387,17 @@ lgf_status launch_r(lgf_ctx *ctx, int rmax, int nout, const SepJobs<T> &jobs, cu
     switch (rmax) {
     case 4: return launch_m<T, LB, AX, 4>(ctx, nout, jobs, s, nbr, nr);
     case 8: return launch_m<T, LB, AX, 8>(ctx, nout, jobs, s, nbr, nr);
+    case 12:
+        if constexpr (AX == 2) return launch_m<T, LB, AX, 12>(ctx, nout, jobs, s, nbr, nr);
+        return launch_m<T, LB, AX, 16>(ctx, nout, jobs, s, nbr, nr);
     default: return launch_m<T, LB, AX, 16>(ctx, nout, jobs, s, nbr, nr);
     }
 }
 
 }  // namespace win
+
+// Window bound for a radius: the smallest of 4, 8, 12, 16 that covers it (0: none).
+inline int window_class(int R) { return R <= 4 ? 4 : R <= 8 ? 8 : R <= 12 ? 12 : R <= 16 ? 16 : 0; }
 
 // Largest radius of a job list, rounded up to a window bound (0: none fits).
 template <typename T>
@@ -398,7 +405,7 @@ inline int window_rmax(const SepJobs<T> &jobs, int b, int nr)
 {
     int R = 0;
     for (int i = 0; i < jobs.n; ++i) R = jobs.j[i].R > R ? jobs.j[i].R : R;
-    const int rmax = R <= 4 ? 4 : R <= 8 ? 8 : R <= 16 ? 16 : 0;
+    const int rmax = window_class(R);
     if (rmax == 0 || rmax > nr * b || (b != 8 && b != 16 && b != 32)) return 0;
     return rmax;
 }
