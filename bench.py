@@ -381,6 +381,26 @@ def run_ours(args, rank, world, dist):
     return line
 
 
+def run_ncu_case(args):
+    """The bench step (one lgf_batch_apply on the legacy stream) run `--steps`
+    times untimed: the small, short case that ncu captures."""
+    import torch
+    import paper_1604_01814_gb300 as lgf
+    p, _ = make_workload(args.workload)
+    ctx = lgf.Context("f32")
+    ctx.table_build(48)
+    f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
+    outs = [torch.empty_like(f) for _ in range(1 + len(ALPHAS))]
+    batch = [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=outs[0], op=lgf.LGF_OP_POISSON)]
+    batch += [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=o, op=lgf.LGF_OP_INTFACTOR, alpha=a)
+              for a, o in zip(ALPHAS, outs[1:])]
+    for _ in range(args.steps):
+        ctx.batch_apply(batch, stream=0)
+    torch.cuda.synchronize()
+    print("ncu case done:", [float(o.abs().max()) for o in outs], flush=True)
+    ctx.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,10 +411,14 @@ def main(argv=None):
     ap.add_argument("--cpu-points", type=int, default=3072)
     ap.add_argument("--ref-points", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true", help="run the step --steps times untimed (for ncu)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, _ = dist_env()
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
     else:
