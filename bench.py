@@ -332,29 +332,65 @@ def run_ours(args, rank, world, dist):
                for k, (n, t) in stats.items()}
 
     # ---- end to end: pinned host input -> apply -> outputs back to host ----
-    outs_host = [torch.empty(n_out, dtype=torch.float32).pin_memory() for _ in range(1 + len(ALPHAS))]
-    e2e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-    with torch.cuda.stream(s):
-        for _ in range(2):
-            f.copy_(f_host, non_blocking=True)
-            ctx.batch_apply(batch, stream=s)
-            for o, d in zip(outs_host, [u] + vs):
-                o.copy_(d, non_blocking=True)
-        s.synchronize()
-        for a, b in e2e_evs:
-            flush.zero_()
-            a.record(s)
-            f.copy_(f_host, non_blocking=True)
-            ctx.batch_apply(batch, stream=s)
-            for o, d in zip(outs_host, [u] + vs):
-                o.copy_(d, non_blocking=True)
-            b.record(s)
-    s.synchronize()
-    e2e_ms = reduce_max(float(np.mean([a.elapsed_time(b) for a, b in e2e_evs])), dist)
+    # A streaming pipeline with two device buffer sets: the host->device copy
+    # of step k+1 and the device->host copy of step k-1 run on their own
+    # streams while step k computes.  Every step still copies its whole input
+    # from pinned host memory and all four output fields back to pinned host
+    # memory; the time is first copy-in start to last copy-out end over K steps.
+    n_out_fields = 1 + len(ALPHAS)
+    sets = []
+    for j in range(2):
+        fj = torch.empty_like(f)
+        oj = [torch.empty(n_out, dtype=torch.float32, device=dev) for _ in range(n_out_fields)]
+        bj = [dict(b=p.b, src=p.src, tgt=p.tgt, f=fj, u=oj[0], op=lgf.LGF_OP_POISSON, dx=1.0)]
+        bj += [dict(b=p.b, src=p.src, tgt=p.tgt, f=fj, u=o, op=lgf.LGF_OP_INTFACTOR, alpha=a)
+               for a, o in zip(ALPHAS, oj[1:])]
+        hj = [torch.empty(n_out, dtype=torch.float32).pin_memory() for _ in range(n_out_fields)]
+        sets.append((fj, oj, bj, hj))
+    s_in = torch.cuda.Stream(device=dev)
+    s_out = torch.cuda.Stream(device=dev)
+
+    def pipeline(nsteps, t0=None, t1=None):
+        comp = [torch.cuda.Event() for _ in range(nsteps)]
+        d2h = [torch.cuda.Event() for _ in range(nsteps)]
+        if t0 is not None:
+            t0.record(s_in)
+        for k in range(nsteps):
+            fj, oj, bj, hj = sets[k % 2]
+            if k >= 2:
+                s_in.wait_event(comp[k - 2])          # step k-2 no longer reads f_j
+            with torch.cuda.stream(s_in):
+                fj.copy_(f_host, non_blocking=True)
+            h2d = torch.cuda.Event()
+            h2d.record(s_in)
+            s.wait_event(h2d)
+            if k >= 2:
+                s.wait_event(d2h[k - 2])              # step k-2's outputs are on the host
+            ctx.batch_apply(bj, stream=s)
+            comp[k].record(s)
+            s_out.wait_event(comp[k])
+            with torch.cuda.stream(s_out):
+                for o, d in zip(hj, oj):
+                    o.copy_(d, non_blocking=True)
+            d2h[k].record(s_out)
+        if t1 is not None:
+            t1.record(s_out)
+        torch.cuda.synchronize()
+
+    pipeline(4)                                        # warm-up (captures both graphs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    pipeline(args.steps, e0, e1)
+    e2e_ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist)
     e2e = {"value": job_throughput(points, e2e_ms, world), "unit": "points/s",
-           "h2d_bytes_per_step": int(f.numel() * 4), "d2h_bytes_per_step": int(n_out * 4 * (1 + len(ALPHAS))),
-           "ms_per_step": e2e_ms}
+           "h2d_bytes_per_step": int(f.numel() * 4), "d2h_bytes_per_step": int(n_out * 4 * n_out_fields),
+           "ms_per_step": e2e_ms,
+           "how": "two buffer sets; copy-in of step k+1 and copy-out of step k-1 overlap step k; "
+                  "no L2 flush (every input is re-copied from the host)"}
+    # the end-to-end results must be the device-timed results
+    for o, d in zip(sets[(args.steps - 1) % 2][3], [u] + vs):
+        assert torch.equal(o, d.cpu()), "end-to-end output differs from the device-timed output"
 
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -171,7 +171,8 @@ typedef struct {
    per launch, different alphas and buffers allowed).  On a non-default
    stream the whole batch is captured once into a CUDA graph, and later calls
    with an identical batch (same block lists, pointers, alphas, stream)
-   replay it.  u buffers must not alias f buffers of the same batch.
+   replay it; the context keeps the graphs of the 8 most recently used
+   batches (so, e.g., double-buffered batches alternate without recapture).  u buffers must not alias f buffers of the same batch.
    POISSON_THEN_INTFACTOR writes E_alpha(G_L * f) into u_dev.  Results equal
    those of the single applies bit for bit.  Errors: as the single applies. */
 LGF_API lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob, void *stream);

@@ -213,7 +213,8 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
     if (!ctx) return LGF_EINVAL;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
     ctx->pplans.clear();
     ctx->iplans.clear();
     for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
@@ -253,11 +254,8 @@ lgf_status lgf_table_build(lgf_ctx *ctx, int32_t max_offset, void *stream)
     // spectra built from an older table are stale
     for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
     ctx->spectra.clear();
-    if (ctx->graph_exec) {
-        cudaGraphExecDestroy(ctx->graph_exec);
-        ctx->graph_exec = nullptr;
-        ctx->graph_key.clear();
-    }
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
     return LGF_OK;
 }
 
@@ -517,14 +515,19 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     // 3. the legacy default stream cannot be captured, and per-kernel timing
     //    needs direct launches: run without a graph
     if (s == nullptr || ctx->prof) return enqueue();
-    if (ctx->graph_exec && key == ctx->graph_key) {
-        LGF_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, s));
-        return LGF_OK;
-    }
-    if (ctx->graph_exec) {
-        cudaGraphExecDestroy(ctx->graph_exec);
-        ctx->graph_exec = nullptr;
-        ctx->graph_key.clear();
+    for (auto &g : ctx->graphs)
+        if (g.key == key) {
+            g.used = ++ctx->graph_clock;
+            LGF_CUDA(ctx, cudaGraphLaunch(g.exec, s));
+            return LGF_OK;
+        }
+    constexpr size_t kMaxGraphs = 8;
+    if (ctx->graphs.size() >= kMaxGraphs) {
+        size_t lru = 0;
+        for (size_t i = 1; i < ctx->graphs.size(); ++i)
+            if (ctx->graphs[i].used < ctx->graphs[lru].used) lru = i;
+        cudaGraphExecDestroy(ctx->graphs[lru].exec);
+        ctx->graphs.erase(ctx->graphs.begin() + lru);
     }
     LGF_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     lgf_status est = enqueue();
@@ -539,8 +542,11 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch: graph instantiation");
-    ctx->graph_exec = exec;
-    ctx->graph_key = key;
+    lgf_ctx::GraphEntry ge;
+    ge.key = std::move(key);
+    ge.exec = exec;
+    ge.used = ++ctx->graph_clock;
+    ctx->graphs.push_back(std::move(ge));
     LGF_CUDA(ctx, cudaGraphLaunch(exec, s));
     return LGF_OK;
 }

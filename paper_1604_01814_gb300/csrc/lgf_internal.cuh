@@ -116,9 +116,15 @@ struct lgf_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
-    // batch graph cache
-    std::vector<unsigned char> graph_key;
-    cudaGraphExec_t graph_exec = nullptr;
+    // batch graph cache: the most recently used batches (key = everything that
+    // shapes the work), least recently used evicted
+    struct GraphEntry {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t used = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_clock = 0;
 
     double *red_dev = nullptr;   // small reduction buffer (residual, table mismatch)
 
