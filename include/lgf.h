@@ -164,17 +164,23 @@ typedef struct {
 
 /* Apply `nprob` independent problems (the per-stage right-hand sides of
    Sec. 2.3 and many uneven block-adaptive problems) as one batch.  All plans,
-   spectra and weights are prepared first; the Poisson parts run one problem
-   after another (all fields of a problem in each launch), then the
-   integrating factors: those on the same block sets with the same field
-   count form one group that runs as one launch per pass (up to 8 problems
-   per launch, different alphas and buffers allowed).  On a non-default
-   stream the whole batch is captured once into a CUDA graph, and later calls
-   with an identical batch (same block lists, pointers, alphas, stream)
-   replay it; the context keeps the graphs of the 8 most recently used
-   batches (so, e.g., double-buffered batches alternate without recapture).  u buffers must not alias f buffers of the same batch.
-   POISSON_THEN_INTFACTOR writes E_alpha(G_L * f) into u_dev.  Results equal
-   those of the single applies bit for bit.  Errors: as the single applies. */
+   spectra and weights are prepared first.  Integrating factors on the same
+   block sets with the same field count form one group that runs as one
+   launch per pass (up to 8 problems per launch, different alphas and buffers
+   allowed).  The Poisson parts (each with its own integrating factor when no
+   other problem shares its group) and the groups that read only batch inputs
+   are independent units: they are spread over up to 4 concurrent branches
+   (the caller's stream and 3 context streams, each with its own scratch),
+   longest first onto the least loaded branch; groups of several
+   POISSON_THEN_INTFACTOR problems run after the branches join.  On a
+   non-default stream the whole batch is captured once into a CUDA graph,
+   and later calls with an identical batch (same block lists, pointers,
+   alphas, stream) replay it; the context keeps the graphs of the 8 most
+   recently used batches (so, e.g., double-buffered batches alternate
+   without recapture).  u buffers must not alias one another or any f
+   buffer of the same batch.  POISSON_THEN_INTFACTOR writes
+   E_alpha(G_L * f) into u_dev.  Results equal those of the single applies
+   bit for bit.  Errors: as the single applies. */
 LGF_API lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob, void *stream);
 
 /* FP64 residual check of the discrete Poisson problem (Sec. 2.2, Eq. dpoisson):

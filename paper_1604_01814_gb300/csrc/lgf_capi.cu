@@ -1,5 +1,6 @@
 // C ABI of the library: argument checking, context life cycle, plan and
 // spectrum caches, the batched path and its CUDA-graph cache.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -99,6 +100,7 @@ lgf_status enter(lgf_ctx *ctx)
 {
     if (!ctx) return LGF_EINVAL;
     ctx->last_error.clear();
+    ctx->cur = &ctx->scr[0];
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     return LGF_OK;
@@ -225,13 +227,17 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
         cudaFree(w->w32);
     }
     cudaFree(ctx->table_dev);
-    cudaFree(ctx->scrA);
-    cudaFree(ctx->scrB);
-    cudaFree(ctx->scrC);
-    cudaFree(ctx->scrD);
-    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (auto &sc : ctx->scr) {
+        cudaFree(sc.A);
+        cudaFree(sc.B);
+        cudaFree(sc.C);
+        cudaFree(sc.D);
+    }
+    for (int b = 0; b < kBranches; ++b) {
+        if (ctx->br[b]) cudaStreamDestroy(ctx->br[b]);
+        if (ctx->ev_join[b]) cudaEventDestroy(ctx->ev_join[b]);
+    }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     cudaFree(ctx->red_dev);
     for (auto &r : ctx->prof_pending) {
         cudaEventDestroy(r.a);
@@ -443,6 +449,7 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         int nf;
         bool after_poisson;   // reads outputs of the batch's Poisson parts
         std::vector<IntfJob> jobs;
+        std::vector<int> prob;    // problem of each job
     };
     std::vector<Group> groups;
     for (int i = 0; i < nprob; ++i) {
@@ -461,52 +468,128 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         for (auto &q : groups)
             if (q.plan == pi.plan && q.nf == nf && q.after_poisson == after) g = &q;
         if (!g) {
-            groups.push_back(Group{pi.plan, nf, after, {}});
+            groups.push_back(Group{pi.plan, nf, after, {}, {}});
             g = &groups.back();
         }
         g->jobs.push_back(IntfJob{pi.w, in, p.u_dev});
+        g->prob.push_back(i);
     }
-    for (auto &g : groups)
-        if ((st = intf_prepare_scratch(ctx, g.plan, g.nf, (int)g.jobs.size())) != LGF_OK) return st;
-    bool any_poisson = false, any_free = false;
-    for (int i = 0; i < nprob; ++i) any_poisson |= pois[i].plan != nullptr;
-    for (auto &g : groups) any_free |= !g.after_poisson;
-    const bool fork = any_poisson && any_free && !ctx->prof;   // profiling times kernels one at a time
-    if (fork && !ctx->side) {
-        LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
-        LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-        LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    // 3. units of concurrent work: every Poisson part (with its dependent
+    //    integrating factor when no other problem shares that group) and every
+    //    integrating-factor group that reads only batch inputs.  Dependent
+    //    groups of several problems run after the join.  Units go to up to
+    //    kBranches branches (longest first onto the least loaded), each branch
+    //    with its own stream and scratch.
+    struct Unit {
+        int prob = -1, grp = -1, dep = -1, branch = 0;
+        double cost = 0.0;
+    };
+    std::vector<Unit> units;
+    std::vector<int> prob_unit(nprob, -1), post;
+    auto grp_cost = [&](const Group &g) {
+        const double b3 = (double)g.plan->b * g.plan->b * g.plan->b;
+        return 8.0 * g.jobs.size() * g.nf * b3 * ((double)g.plan->n2 + (double)g.plan->tgt.size() / 3);
+    };
+    for (int i = 0; i < nprob; ++i) {
+        if (!pois[i].plan) continue;
+        const int *M = pois[i].plan->g.M;
+        Unit u;
+        u.prob = i;
+        u.cost = 3.0 * (double)M[0] * M[1] * M[2] * probs[i].ncomp * probs[i].nrhs;
+        prob_unit[i] = (int)units.size();
+        units.push_back(u);
+    }
+    for (size_t k = 0; k < groups.size(); ++k) {
+        const Group &g = groups[k];
+        if (!g.after_poisson) {
+            Unit u;
+            u.grp = (int)k;
+            u.cost = grp_cost(g);
+            units.push_back(u);
+        } else if (g.jobs.size() == 1 && prob_unit[g.prob[0]] >= 0) {
+            Unit &u = units[prob_unit[g.prob[0]]];
+            u.dep = (int)k;
+            u.cost += grp_cost(g);
+        } else {
+            post.push_back((int)k);
+        }
+    }
+    const int nb = ctx->prof ? 1 : std::min<int>(kBranches, std::max<int>(1, (int)units.size()));
+    {
+        std::vector<int> order(units.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return units[a].cost > units[c].cost; });
+        double load[kBranches] = {0, 0, 0, 0};
+        for (int i : order) {
+            int best = 0;
+            for (int b = 1; b < nb; ++b)
+                if (load[b] < load[best]) best = b;
+            units[i].branch = best;
+            load[best] += units[i].cost;
+        }
+    }
+    for (auto &u : units) {
+        ctx->cur = &ctx->scr[u.branch];
+        const int i = u.prob;
+        if (i >= 0 && (st = poisson_prepare_scratch(ctx, pois[i].plan, probs[i].ncomp * probs[i].nrhs)) != LGF_OK)
+            return st;
+        for (int k : {u.grp, u.dep}) {
+            if (k < 0) continue;
+            const Group &g = groups[k];
+            if ((st = intf_prepare_scratch(ctx, g.plan, g.nf, (int)g.jobs.size())) != LGF_OK) return st;
+        }
+    }
+    ctx->cur = &ctx->scr[0];
+    for (int k : post)
+        if ((st = intf_prepare_scratch(ctx, groups[k].plan, groups[k].nf, (int)groups[k].jobs.size())) != LGF_OK)
+            return st;
+    if (nb > 1) {
+        if (!ctx->ev_fork) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        for (int b = 1; b < nb; ++b) {
+            if (!ctx->br[b]) LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->br[b], cudaStreamNonBlocking));
+            if (!ctx->ev_join[b]) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming));
+        }
     }
     auto enqueue = [&]() -> lgf_status {
-        // Integrating factors that read only batch inputs run on a second
-        // branch, concurrent with the Poisson parts (separate scratch); those
-        // that read Poisson outputs run after the join.
-        if (fork) {
-            LGF_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
-            LGF_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-            for (auto &g : groups) {
-                if (g.after_poisson) continue;
-                lgf_status e2 = intf_run_jobs(ctx, g.plan, g.jobs.data(), (int)g.jobs.size(), g.nf, ctx->side);
-                if (e2 != LGF_OK) return e2;
-            }
-            LGF_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
-        }
+        // problems with no source blocks: zero output
         for (int i = 0; i < nprob; ++i) {
             const lgf_problem &p = probs[i];
-            const int nf = p.ncomp * p.nrhs;
             const size_t b3 = (size_t)p.src.b * p.src.b * p.src.b;
-            if (p.tgt.nblocks == 0) continue;
-            if (p.src.nblocks == 0) {
-                LGF_CUDA(ctx, cudaMemsetAsync(p.u_dev, 0, (size_t)p.tgt.nblocks * b3 * nf * elem_size(ctx), s));
-                continue;
-            }
-            if (p.op == LGF_OP_INTFACTOR) continue;
-            lgf_status e2 = poisson_run(ctx, pois[i].plan, pois[i].spec, p.f_dev, p.u_dev, nf, p.dx, s);
-            if (e2 != LGF_OK) return e2;
+            if (p.tgt.nblocks > 0 && p.src.nblocks == 0)
+                LGF_CUDA(ctx, cudaMemsetAsync(p.u_dev, 0,
+                                              (size_t)p.tgt.nblocks * b3 * p.ncomp * p.nrhs * elem_size(ctx), s));
         }
-        if (fork) LGF_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
-        for (auto &g : groups) {
-            if (fork && !g.after_poisson) continue;
+        if (nb > 1) {
+            LGF_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+            for (int b = 1; b < nb; ++b) LGF_CUDA(ctx, cudaStreamWaitEvent(ctx->br[b], ctx->ev_fork, 0));
+        }
+        for (auto &u : units) {
+            cudaStream_t us = u.branch == 0 ? s : ctx->br[u.branch];
+            ctx->cur = &ctx->scr[u.branch];
+            lgf_status e2 = LGF_OK;
+            if (u.prob >= 0) {
+                const lgf_problem &p = probs[u.prob];
+                e2 = poisson_run(ctx, pois[u.prob].plan, pois[u.prob].spec, p.f_dev, p.u_dev, p.ncomp * p.nrhs, p.dx,
+                                 us);
+            }
+            for (int k : {u.dep, u.grp}) {
+                if (e2 != LGF_OK || k < 0) continue;
+                const Group &g = groups[k];
+                e2 = intf_run_jobs(ctx, g.plan, g.jobs.data(), (int)g.jobs.size(), g.nf, us);
+            }
+            if (e2 != LGF_OK) {
+                ctx->cur = &ctx->scr[0];
+                return e2;
+            }
+        }
+        ctx->cur = &ctx->scr[0];
+        if (nb > 1)
+            for (int b = 1; b < nb; ++b) {
+                LGF_CUDA(ctx, cudaEventRecord(ctx->ev_join[b], ctx->br[b]));
+                LGF_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join[b], 0));
+            }
+        for (int k : post) {
+            const Group &g = groups[k];
             lgf_status e2 = intf_run_jobs(ctx, g.plan, g.jobs.data(), (int)g.jobs.size(), g.nf, s);
             if (e2 != LGF_OK) return e2;
         }

@@ -84,6 +84,14 @@ struct Spectrum {
     void *dev = nullptr;      // (Mz/2+1)(My/2+1)(Mx/2+1) reals, context precision, scaled by 1/(MxMyMz)
 };
 
+// Grow-only scratch buffers: A, B for the Poisson passes, C, D for the
+// integrating factor (separate, so the two may run on concurrent branches).
+struct Scratch {
+    void *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr;
+    size_t a = 0, b = 0, c = 0, d = 0;
+};
+constexpr int kBranches = 4;   // concurrent branches of a batch
+
 }  // namespace lgf
 
 struct lgf_ctx {
@@ -106,15 +114,17 @@ struct lgf_ctx {
     std::vector<std::unique_ptr<lgf::IntfPlan>> iplans;
     std::vector<std::unique_ptr<lgf::IntfWeights>> weights;
 
-    // grow-only scratch: A, B for the Poisson passes; C, D for the integrating
-    // factor (so that the two can run on concurrent graph branches)
-    void *scrA = nullptr, *scrB = nullptr, *scrC = nullptr, *scrD = nullptr;
-    size_t scrA_bytes = 0, scrB_bytes = 0, scrC_bytes = 0, scrD_bytes = 0;
+    // grow-only scratch, one set per concurrent branch of lgf_batch_apply
+    // (branch 0 also serves the single applies); `cur` is the set the next
+    // enqueued work uses
+    lgf::Scratch scr[lgf::kBranches];
+    lgf::Scratch *cur = &scr[0];
 
-    // second stream for the concurrent branch of lgf_batch_apply, and the
+    // streams of branches 1.. (branch 0 is the caller's stream) and the
     // fork/join events
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t br[lgf::kBranches] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[lgf::kBranches] = {};
 
     // batch graph cache: the most recently used batches (key = everything that
     // shapes the work), least recently used evicted

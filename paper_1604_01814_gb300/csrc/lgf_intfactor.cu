@@ -348,9 +348,9 @@ lgf_status intf_prepare_scratch(lgf_ctx *ctx, const IntfPlan *pl, int nfields, i
 {
     const size_t esz = ctx->prec == LGF_F64 ? 8 : 4;
     const size_t b3 = (size_t)pl->b * pl->b * pl->b;
-    lgf_status st = ensure_scratch(ctx, &ctx->scrC, &ctx->scrC_bytes, std::max<size_t>(1, pl->n1) * b3 * nfields * esz);
+    lgf_status st = ensure_scratch(ctx, &ctx->cur->C, &ctx->cur->c, std::max<size_t>(1, pl->n1) * b3 * nfields * esz);
     if (st != LGF_OK) return st;
-    return ensure_scratch(ctx, &ctx->scrD, &ctx->scrD_bytes,
+    return ensure_scratch(ctx, &ctx->cur->D, &ctx->cur->d,
                           std::max<size_t>(1, pl->n2) * b3 * nfields * esz * (size_t)std::max(1, njobs));
 }
 
@@ -436,7 +436,7 @@ static lgf_status run_sep_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, 
     const int64_t b3 = (int64_t)b * b * b;
     const int nsrc = (int)(pl->src.size() / 3), ntgt = (int)(pl->tgt.size() / 3);
     const int64_t y2f = (int64_t)pl->n2 * b3;                       // Y2 elements per field
-    T *X1 = (T *)ctx->scrC, *Y2all = (T *)ctx->scrD;
+    T *X1 = (T *)ctx->cur->C, *Y2all = (T *)ctx->cur->D;
     auto wptr = [](const IntfJob &j) -> const T * {
         return sizeof(T) == 8 ? (const T *)(const void *)j.w->w64 : (const T *)(const void *)j.w->w32;
     };

@@ -302,9 +302,9 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], Spectrum **out, cudaSt
 lgf_status poisson_prepare_scratch(lgf_ctx *ctx, const PoissonPlan *pl, int nfields)
 {
     const size_t csz = ctx->prec == LGF_F64 ? 16 : 8;
-    lgf_status st = ensure_scratch(ctx, &ctx->scrA, &ctx->scrA_bytes, (size_t)pl->A_elems * nfields * csz);
+    lgf_status st = ensure_scratch(ctx, &ctx->cur->A, &ctx->cur->a, (size_t)pl->A_elems * nfields * csz);
     if (st != LGF_OK) return st;
-    return ensure_scratch(ctx, &ctx->scrB, &ctx->scrB_bytes, (size_t)pl->B_elems * nfields * csz);
+    return ensure_scratch(ctx, &ctx->cur->B, &ctx->cur->b, (size_t)pl->B_elems * nfields * csz);
 }
 
 lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const void *f, void *u, int nfields,
@@ -317,9 +317,9 @@ lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const 
     g.Bstride = pl->B_elems;
     g.scale = dx * dx;
     if (ctx->prec == LGF_F64)
-        return run_passes<double>(ctx, g, (const double *)f, (double *)u, (Cx<double> *)ctx->scrA,
-                                  (Cx<double> *)ctx->scrB, (const double *)sp->dev, nfields, 0, false, s);
-    return run_passes<float>(ctx, g, (const float *)f, (float *)u, (Cx<float> *)ctx->scrA, (Cx<float> *)ctx->scrB,
+        return run_passes<double>(ctx, g, (const double *)f, (double *)u, (Cx<double> *)ctx->cur->A,
+                                  (Cx<double> *)ctx->cur->B, (const double *)sp->dev, nfields, 0, false, s);
+    return run_passes<float>(ctx, g, (const float *)f, (float *)u, (Cx<float> *)ctx->cur->A, (Cx<float> *)ctx->cur->B,
                              (const float *)sp->dev, nfields, 0, false, s);
 }
 

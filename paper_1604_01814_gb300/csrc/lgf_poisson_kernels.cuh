@@ -257,7 +257,10 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T>
 }
 
 // z pass: forward along z over the source planes, times the real even kernel
-// spectrum, inverse along z, target planes written back in place.
+// spectrum, inverse along z, target planes written back in place.  The field
+// is the fastest grid index (blockIdx.x), so the CTAs of every field of one
+// column set run back to back and read that part of the spectrum from L2:
+// for big boxes the spectrum is larger than L2.
 template <typename T, int LOGM, int W>
 __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__restrict__ B, const T *__restrict__ spec,
                                                                       int K, int My, int s0, int ns, int t0, int nt,
@@ -270,11 +273,11 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__r
     Cx<T> *s = tw + M;
     load_twiddles(tw, twg, M);
     const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int kx = blockIdx.x * W + w;
-    const int ky = blockIdx.y;
+    const int kx = blockIdx.y * W + w;
+    const int ky = blockIdx.z;
     const bool live = kx < K;
     const int64_t plane = (int64_t)My * K;
-    Cx<T> *bb = B + blockIdx.z * field + (int64_t)ky * K + kx;
+    Cx<T> *bb = B + blockIdx.x * field + (int64_t)ky * K + kx;
     const ColAddrW ad{W};
     constexpr int R0 = 1 << P::LG0;
     constexpr int NG0 = P::G0 / P::TPC;
@@ -667,7 +670,7 @@ lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T 
     auto kern = k_col_convolve<T, LOGM, C::W>;
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
-    dim3 grid((g.Kx + C::W - 1) / C::W, g.M[1], nfields);
+    dim3 grid(nfields, (g.Kx + C::W - 1) / C::W, g.M[1]);
     const int ph = prof_begin(ctx, s, "poisson_z_convolve");
     kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(B, spec, g.Kx, g.M[1], g.s0[2], g.Ls[2], g.t0[2], g.Lt[2], g.Bstride,
                                               tw);

@@ -97,3 +97,56 @@ def test_grouped_integrating_factors_equal_single_applies(prec, ctx32, ctx64):
     s.synchronize()
     for q, r in zip(batch, ref):
         assert torch.equal(q["u"], r)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_branches_and_shared_dependent_groups(prec, ctx32, ctx64):
+    """A batch whose Poisson parts spread over concurrent branches while an
+    integrating-factor group shared by several Poisson-then-E problems runs
+    after the join: every result equals its single applies bit for bit, with
+    the graph, on replay, and with profiling on (serial, no graph)."""
+    ctx = ctx32 if prec == "f32" else ctx64
+    shared = li.random_sparse(41, b=16, nsrc=4, ntgt=5, extent=(3, 3, 2), ncomp=1)
+    others = make_problems(5, seed=4)
+    rng = np.random.default_rng(5)
+    batch, ref = [], []
+
+    def add(p, op, alpha):
+        f = torch.tensor(rng.uniform(-1, 1, p.f.size), dtype=ctx.dtype, device="cuda")
+        u = torch.full((p.ncomp * p.tgt.shape[0] * p.b ** 3,), float("nan"), dtype=ctx.dtype, device="cuda")
+        batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, op=op, alpha=alpha, dx=0.5))
+        r = torch.empty_like(u)
+        if op == lgf.LGF_OP_POISSON:
+            ctx.poisson_apply(p.b, p.src, p.tgt, f, r, ncomp=p.ncomp, dx=0.5)
+        elif op == lgf.LGF_OP_INTFACTOR:
+            ctx.intfactor_apply(alpha, p.b, p.src, p.tgt, f, r, ncomp=p.ncomp)
+        else:
+            tmp = torch.empty_like(r)
+            ctx.poisson_apply(p.b, p.src, p.tgt, f, tmp, ncomp=p.ncomp, dx=0.5)
+            ctx.intfactor_apply(alpha, p.b, p.tgt, p.tgt, tmp, r, ncomp=p.ncomp)
+        ref.append(r)
+
+    for a in (0.1, 0.6, 1.3):
+        add(shared, lgf.LGF_OP_POISSON_THEN_INTFACTOR, a)
+    for i, p in enumerate(others):
+        add(p, (lgf.LGF_OP_POISSON, lgf.LGF_OP_INTFACTOR, lgf.LGF_OP_POISSON_THEN_INTFACTOR)[i % 3], 0.25 + 0.2 * i)
+    s = torch.cuda.Stream()
+    for _ in range(2):   # capture, then replay
+        for q in batch:
+            q["u"].fill_(float("nan"))
+        with torch.cuda.stream(s):
+            ctx.batch_apply(batch, stream=s)
+        s.synchronize()
+        for q, r in zip(batch, ref):
+            assert torch.equal(q["u"], r)
+    ctx.profile_enable(True)
+    try:
+        for q in batch:
+            q["u"].fill_(float("nan"))
+        with torch.cuda.stream(s):
+            ctx.batch_apply(batch, stream=s)
+        s.synchronize()
+        for q, r in zip(batch, ref):
+            assert torch.equal(q["u"], r)
+    finally:
+        ctx.profile_enable(False)
