@@ -461,15 +461,24 @@ def run_ncu_case(args):
     """The bench step (one lgf_batch_apply on the legacy stream) run `--steps`
     times untimed: the small, short case that ncu captures."""
     import torch
+    import lgf_inputs as li
     import paper_1604_01814_gb300 as lgf
-    p, _ = make_workload(args.workload)
     ctx = lgf.Context("f32")
     ctx.table_build(48)
-    f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
-    outs = [torch.empty_like(f) for _ in range(1 + len(ALPHAS))]
-    batch = [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=outs[0], op=lgf.LGF_OP_POISSON)]
-    batch += [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=o, op=lgf.LGF_OP_INTFACTOR, alpha=a)
-              for a, o in zip(ALPHAS, outs[1:])]
+    if args.workload == "wake512":
+        # one right-hand side (3 fields, about 3 GB on the device): the wake
+        # domain's transform shape at a size a full capture handles
+        p = li.wake_domain(nrhs=1)
+        f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
+        outs = [torch.empty(f.numel(), dtype=torch.float32, device="cuda")]
+        batch = [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=outs[0], ncomp=3, nrhs=1, op=lgf.LGF_OP_POISSON)]
+    else:
+        p, _ = make_workload(args.workload)
+        f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
+        outs = [torch.empty_like(f) for _ in range(1 + len(ALPHAS))]
+        batch = [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=outs[0], op=lgf.LGF_OP_POISSON)]
+        batch += [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=o, op=lgf.LGF_OP_INTFACTOR, alpha=a)
+                  for a, o in zip(ALPHAS, outs[1:])]
     for _ in range(args.steps):
         ctx.batch_apply(batch, stream=0)
     torch.cuda.synchronize()

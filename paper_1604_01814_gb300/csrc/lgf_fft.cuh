@@ -99,6 +99,57 @@ struct Dft<1, DIR, T> {
     static __device__ __forceinline__ void run(Cx<T> *) {}
 };
 
+// DFT of R points whose upper half a[R/2..R) is zero (only a[0..R/2) is
+// read): the even outputs are the (R/2)-point DFT of a[p], the odd ones the
+// (R/2)-point DFT of a[p] w_R^p.  Saves the first butterfly layer.
+template <int R, int DIR, typename T, int P = 0>
+__device__ __forceinline__ void twist_half(Cx<T> *o, const Cx<T> *a)
+{
+    if constexpr (P < R / 2) {
+        o[P] = rot<R, P, DIR, T>(a[P]);
+        twist_half<R, DIR, T, P + 1>(o, a);
+    }
+}
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_half_in(Cx<T> *a)
+{
+    Cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+    for (int p = 0; p < R / 2; ++p) e[p] = a[p];
+    twist_half<R, DIR, T>(o, a);
+    Dft<R / 2, DIR, T>::run(e);
+    Dft<R / 2, DIR, T>::run(o);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+        a[2 * k] = e[k];
+        a[2 * k + 1] = o[k];
+    }
+}
+
+// DFT of R points of which only the outputs a[0..R/2) are wanted: the last
+// butterfly layer keeps its sums and drops its differences.
+template <int R, int DIR, typename T, int K = 0>
+__device__ __forceinline__ void combine_low(Cx<T> *a, const Cx<T> *e, const Cx<T> *o)
+{
+    if constexpr (K < R / 2) {
+        a[K] = cadd(e[K], rot<R, K, DIR, T>(o[K]));
+        combine_low<R, DIR, T, K + 1>(a, e, o);
+    }
+}
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void dft_half_out(Cx<T> *a)
+{
+    Cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+        e[k] = a[2 * k];
+        o[k] = a[2 * k + 1];
+    }
+    Dft<R / 2, DIR, T>::run(e);
+    Dft<R / 2, DIR, T>::run(o);
+    combine_low<R, DIR, T>(a, e, o);
+}
+
 // Shared-memory addressing of lines.
 // Rows: line-major, each line contiguous, one padding slot per 16 elements
 // (keeps stride-R accesses of late stages off a single bank).

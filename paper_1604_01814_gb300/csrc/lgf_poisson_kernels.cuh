@@ -61,18 +61,23 @@ __device__ __forceinline__ int freq_of(int pos)
 
 // Forward butterfly of one group: DFT then twiddles w_N^{j q} (none when the
 // stage is the last one, N = R).
-template <int LOGM, int LOGN, int LOGR, typename T>
+// HALF: the inputs a[R/2..R) are zero (not read).
+template <int LOGM, int LOGN, int LOGR, bool HALF = false, typename T>
 __device__ __forceinline__ void dif_group(Cx<T> *a, int j, const Cx<T> *tw)
 {
     constexpr int R = 1 << LOGR;
-    Dft<R, -1, T>::run(a);
+    if constexpr (HALF)
+        dft_half_in<R, -1, T>(a);
+    else
+        Dft<R, -1, T>::run(a);
     if constexpr (LOGN > LOGR) {
 #pragma unroll
         for (int q = 1; q < R; ++q) a[q] = cmul(a[q], tw[(j * q) << (LOGM - LOGN)]);
     }
 }
 
-template <int LOGM, int LOGN, int LOGR, typename T>
+// HALF: only the outputs a[0..R/2) are formed.
+template <int LOGM, int LOGN, int LOGR, bool HALF = false, typename T>
 __device__ __forceinline__ void dit_group(Cx<T> *a, int j, const Cx<T> *tw)
 {
     constexpr int R = 1 << LOGR;
@@ -80,7 +85,10 @@ __device__ __forceinline__ void dit_group(Cx<T> *a, int j, const Cx<T> *tw)
 #pragma unroll
         for (int q = 1; q < R; ++q) a[q] = cmulc(a[q], tw[(j * q) << (LOGM - LOGN)]);
     }
-    Dft<R, 1, T>::run(a);
+    if constexpr (HALF)
+        dft_half_out<R, 1, T>(a);
+    else
+        Dft<R, 1, T>::run(a);
 }
 
 // Middle stage (three-stage plans): shared memory to shared memory.
@@ -130,16 +138,54 @@ __device__ __forceinline__ void load_twiddles(Cx<T> *tw, const Cx<T> *__restrict
 
 // ---------------------------------------------------------------------------
 // Column passes.  Data in global memory: rows of K complex values (kx), row
-// `r` of the current column set at base + r * rs.  A CTA owns W adjacent kx.
+// `r` of the current column set at base + r * rs.  Most CTAs own W adjacent
+// kx of one plane; the K mod W leftover kx of every plane (the Nyquist column
+// kx = M/2 when K = M/2 + 1) are packed W (plane, kx) pairs per CTA, so no
+// CTA runs mostly empty columns.  Those CTAs come first in the grid: their
+// scattered accesses are slower, and they then overlap the rest instead of
+// trailing it.
 // ---------------------------------------------------------------------------
+template <int W>
+__host__ __device__ __forceinline__ int col_ctas(int K, int nplanes)
+{
+    const int nfull = K / W, rem = K - nfull * W;
+    return nfull * nplanes + (rem * nplanes + W - 1) / W;
+}
+
+// Column (kx, plane) of lane w of CTA `cta`; false for padding lanes of the
+// last packed CTA (kx, plane set to 0 so that addresses stay in range).
+template <int W>
+__device__ __forceinline__ bool column_of(int cta, int w, int K, int nplanes, int &kx, int &pl)
+{
+    const int nfull = K / W, rem = K - nfull * W;
+    const int ntail = (rem * nplanes + W - 1) / W;
+    if (cta >= ntail) {
+        const int c = cta - ntail;
+        pl = c / nfull;
+        kx = (c - pl * nfull) * W + w;
+        return true;
+    }
+    const int i = cta * W + w;
+    pl = i / rem;
+    kx = nfull * W + (i - pl * rem);
+    if (pl < nplanes) return true;
+    pl = 0;
+    kx = 0;
+    return false;
+}
 
 // Forward along the column: rows [lo, lo + n) hold data (row m at
 // in + (m - lo) * rs), others are zero; the spectrum (natural order) goes to
 // out + k * os.  Used by the y pass and by the spectrum build's z pass.
-template <typename T, int LOGM, int W>
+// HALF: the data rows lie in [0, M/2), which holds for every pass of an
+// apply (the transform length is at least twice the box), so the first
+// stage's upper inputs are zero at compile time and its first butterfly
+// layer is skipped.  Row addresses advance by a fixed stride per radix digit
+// (the last stage's digit is the top digit of the frequency).
+template <typename T, int LOGM, int W, bool HALF>
 __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
-                                                                     int K, int lo, int n, int64_t rs, int64_t os,
-                                                                     int64_t in_plane, int64_t out_plane,
+                                                                     int K, int nplanes, int lo, int n, int64_t rs,
+                                                                     int64_t os, int64_t in_plane, int64_t out_plane,
                                                                      int64_t in_field, int64_t out_field,
                                                                      const Cx<T> *__restrict__ twg)
 {
@@ -150,29 +196,32 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T>
     Cx<T> *s = tw + M;
     load_twiddles(tw, twg, M);
     const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int kx = blockIdx.x * W + w;
-    const bool live = kx < K;
-    const Cx<T> *ib = in + blockIdx.z * in_field + blockIdx.y * in_plane + kx;
-    Cx<T> *ob = out + blockIdx.z * out_field + blockIdx.y * out_plane + kx;
+    int kx, pl;
+    const bool live = column_of<W>(blockIdx.x, w, K, nplanes, kx, pl);
+    const Cx<T> *ib = in + blockIdx.y * in_field + pl * in_plane + kx;
+    Cx<T> *ob = out + blockIdx.y * out_field + pl * out_plane + kx;
     const ColAddrW ad{W};
     constexpr int R0 = 1 << P::LG0;
     constexpr int NG0 = P::G0 / P::TPC;
+    constexpr int NP = HALF ? R0 / 2 : R0;
+    const int64_t istep = (int64_t)P::G0 * rs;
     Cx<T> a[NG0][R0];
 #pragma unroll
     for (int i = 0; i < NG0; ++i) {
-        const int g = t + i * P::TPC;
+        const int r = t + i * P::TPC - lo;   // data row of digit p = 0
+        int64_t off = (int64_t)r * rs;
 #pragma unroll
-        for (int p = 0; p < R0; ++p) {
-            const int m = g + p * P::G0;
-            const bool ok = live && m >= lo && m < lo + n;
-            a[i][p] = ok ? ib[(int64_t)(m - lo) * rs] : Cx<T>{T(0), T(0)};
+        for (int p = 0; p < NP; ++p) {
+            const bool ok = live && (unsigned)(r + p * P::G0) < (unsigned)n;
+            a[i][p] = ok ? ib[off] : Cx<T>{T(0), T(0)};
+            off += istep;
         }
     }
     __syncthreads();   // twiddles
 #pragma unroll
     for (int i = 0; i < NG0; ++i) {
         const int g = t + i * P::TPC;
-        dif_group<LOGM, LOGM, P::LG0>(a[i], g, tw);
+        dif_group<LOGM, LOGM, P::LG0, HALF>(a[i], g, tw);
 #pragma unroll
         for (int q = 0; q < R0; ++q) s[ad(w, q * P::G0 + g)] = a[i][q];
     }
@@ -182,6 +231,7 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T>
         __syncthreads();
     }
     constexpr int RL = 1 << P::LGL;
+    const int64_t ostep = (int64_t)(M / RL) * os;
 #pragma unroll
     for (int g = t; g < P::GL; g += P::TPC) {
         Cx<T> c[RL];
@@ -189,19 +239,24 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T>
         for (int q = 0; q < RL; ++q) c[q] = s[ad(w, (g << P::LGL) + q)];
         Dft<RL, -1, T>::run(c);
         if (live) {
+            int64_t off = (int64_t)freq_of<LOGM>(g << P::LGL) * os;
 #pragma unroll
-            for (int q = 0; q < RL; ++q) ob[(int64_t)freq_of<LOGM>((g << P::LGL) + q) * os] = c[q];
+            for (int q = 0; q < RL; ++q) {
+                ob[off] = c[q];
+                off += ostep;
+            }
         }
     }
 }
 
 // Inverse along the column: spectrum rows (natural order, row k at
 // in + k * rs) in; rows [lo, lo + n) of the result written to
-// out + (m - lo) * os.
+// out + (m - lo) * os.  The written rows lie in [0, M/2), so the last stage
+// forms only the lower half of its outputs.
 template <typename T, int LOGM, int W>
 __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
-                                                                     int K, int lo, int n, int64_t rs, int64_t os,
-                                                                     int64_t in_plane, int64_t out_plane,
+                                                                     int K, int nplanes, int lo, int n, int64_t rs,
+                                                                     int64_t os, int64_t in_plane, int64_t out_plane,
                                                                      int64_t in_field, int64_t out_field,
                                                                      const Cx<T> *__restrict__ twg)
 {
@@ -212,20 +267,24 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T>
     Cx<T> *s = tw + M;
     load_twiddles(tw, twg, M);
     const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int kx = blockIdx.x * W + w;
-    const bool live = kx < K;
-    const Cx<T> *ib = in + blockIdx.z * in_field + blockIdx.y * in_plane + kx;
-    Cx<T> *ob = out + blockIdx.z * out_field + blockIdx.y * out_plane + kx;
+    int kx, pl;
+    const bool live = column_of<W>(blockIdx.x, w, K, nplanes, kx, pl);
+    const Cx<T> *ib = in + blockIdx.y * in_field + pl * in_plane + kx;
+    Cx<T> *ob = out + blockIdx.y * out_field + pl * out_plane + kx;
     const ColAddrW ad{W};
     constexpr int RL = 1 << P::LGL;
     constexpr int NGL = P::GL / P::TPC;
+    const int64_t istep = (int64_t)(M / RL) * rs;
     Cx<T> c[NGL][RL];
 #pragma unroll
     for (int i = 0; i < NGL; ++i) {
         const int g = t + i * P::TPC;
+        int64_t off = (int64_t)freq_of<LOGM>(g << P::LGL) * rs;
 #pragma unroll
-        for (int q = 0; q < RL; ++q)
-            c[i][q] = live ? ib[(int64_t)freq_of<LOGM>((g << P::LGL) + q) * rs] : Cx<T>{T(0), T(0)};
+        for (int q = 0; q < RL; ++q) {
+            c[i][q] = live ? ib[off] : Cx<T>{T(0), T(0)};
+            off += istep;
+        }
     }
 #pragma unroll
     for (int i = 0; i < NGL; ++i) {
@@ -240,17 +299,20 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T>
         __syncthreads();
     }
     constexpr int R0 = 1 << P::LG0;
+    const int64_t ostep = (int64_t)P::G0 * os;
 #pragma unroll
     for (int g = t; g < P::G0; g += P::TPC) {
         Cx<T> a[R0];
 #pragma unroll
         for (int q = 0; q < R0; ++q) a[q] = s[ad(w, q * P::G0 + g)];
-        dit_group<LOGM, LOGM, P::LG0>(a, g, tw);
+        dit_group<LOGM, LOGM, P::LG0, true>(a, g, tw);
         if (live) {
+            const int r = g - lo;
+            int64_t off = (int64_t)r * os;
 #pragma unroll
-            for (int p = 0; p < R0; ++p) {
-                const int m = g + p * P::G0;
-                if (m >= lo && m < lo + n) ob[(int64_t)(m - lo) * os] = a[p];
+            for (int p = 0; p < R0 / 2; ++p) {
+                if ((unsigned)(r + p * P::G0) < (unsigned)n) ob[off] = a[p];
+                off += ostep;
             }
         }
     }
@@ -258,9 +320,11 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T>
 
 // z pass: forward along z over the source planes, times the real even kernel
 // spectrum, inverse along z, target planes written back in place.  The field
-// is the fastest grid index (blockIdx.x), so the CTAs of every field of one
+// is the fastest part of the CTA index, so the CTAs of every field of one
 // column set run back to back and read that part of the spectrum from L2:
-// for big boxes the spectrum is larger than L2.
+// for big boxes the spectrum is larger than L2.  Source and target planes
+// lie in [0, M/2): the first stage skips its zero upper inputs and the last
+// stage forms only its lower outputs.
 template <typename T, int LOGM, int W>
 __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__restrict__ B, const T *__restrict__ spec,
                                                                       int K, int My, int s0, int ns, int t0, int nt,
@@ -273,31 +337,34 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__r
     Cx<T> *s = tw + M;
     load_twiddles(tw, twg, M);
     const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int kx = blockIdx.y * W + w;
-    const int ky = blockIdx.z;
-    const bool live = kx < K;
+    int kx, ky;
+    const int nf = gridDim.x / col_ctas<W>(K, My);
+    const int field_i = blockIdx.x % nf;
+    const bool live = column_of<W>(blockIdx.x / nf, w, K, My, kx, ky);
     const int64_t plane = (int64_t)My * K;
-    Cx<T> *bb = B + blockIdx.x * field + (int64_t)ky * K + kx;
+    Cx<T> *bb = B + field_i * field + (int64_t)ky * K + kx;
     const ColAddrW ad{W};
     constexpr int R0 = 1 << P::LG0;
     constexpr int NG0 = P::G0 / P::TPC;
+    const int64_t step0 = (int64_t)P::G0 * plane;
     {
         Cx<T> a[NG0][R0];
 #pragma unroll
         for (int i = 0; i < NG0; ++i) {
-            const int g = t + i * P::TPC;
+            const int r = t + i * P::TPC - s0;
+            int64_t off = (int64_t)r * plane;
 #pragma unroll
-            for (int p = 0; p < R0; ++p) {
-                const int m = g + p * P::G0;
-                const bool ok = live && m >= s0 && m < s0 + ns;
-                a[i][p] = ok ? bb[(int64_t)(m - s0) * plane] : Cx<T>{T(0), T(0)};
+            for (int p = 0; p < R0 / 2; ++p) {
+                const bool ok = live && (unsigned)(r + p * P::G0) < (unsigned)ns;
+                a[i][p] = ok ? bb[off] : Cx<T>{T(0), T(0)};
+                off += step0;
             }
         }
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < NG0; ++i) {
             const int g = t + i * P::TPC;
-            dif_group<LOGM, LOGM, P::LG0>(a[i], g, tw);
+            dif_group<LOGM, LOGM, P::LG0, true>(a[i], g, tw);
 #pragma unroll
             for (int q = 0; q < R0; ++q) s[ad(w, q * P::G0 + g)] = a[i][q];
         }
@@ -308,19 +375,22 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__r
         __syncthreads();
     }
     constexpr int RL = 1 << P::LGL;
+    constexpr int S = M / RL;   // frequency step of the last stage's digit
     const int Khy = My / 2 + 1;
     const int kyr = ky <= My - ky ? ky : My - ky;
-    const T *sp = spec + (int64_t)kyr * K + (live ? kx : 0);
+    const T *sp = spec + (int64_t)kyr * K + kx;
     const int64_t sp_plane = (int64_t)Khy * K;
 #pragma unroll
     for (int g = t; g < P::GL; g += P::TPC) {
+        // frequency of digit q: kb + q S; its mirror M - kb - q S once past M/2
+        const int kb = freq_of<LOGM>(g << P::LGL);
+        const T *spl = sp + (int64_t)kb * sp_plane;
+        const T *sph = sp + (int64_t)(M - kb) * sp_plane;
         Cx<T> c[RL];
         T gk[RL];
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
-            const int kz = freq_of<LOGM>((g << P::LGL) + q);
-            const int kzr = kz <= M - kz ? kz : M - kz;
-            gk[q] = sp[kzr * sp_plane];
+            gk[q] = q < RL / 2 ? spl[(int64_t)(q * S) * sp_plane] : sph[-(int64_t)(q * S) * sp_plane];
             c[q] = s[ad(w, (g << P::LGL) + q)];
         }
         Dft<RL, -1, T>::run(c);
@@ -338,17 +408,20 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__r
         middle_stage<LOGM, 1>(s, ad, w, t, tw);
         __syncthreads();
     }
+    const int64_t step1 = (int64_t)P::G0 * plane;
 #pragma unroll
     for (int g = t; g < P::G0; g += P::TPC) {
         Cx<T> a[R0];
 #pragma unroll
         for (int q = 0; q < R0; ++q) a[q] = s[ad(w, q * P::G0 + g)];
-        dit_group<LOGM, LOGM, P::LG0>(a, g, tw);
+        dit_group<LOGM, LOGM, P::LG0, true>(a, g, tw);
         if (live) {
+            const int r = g - t0;
+            int64_t off = (int64_t)r * plane;
 #pragma unroll
-            for (int p = 0; p < R0; ++p) {
-                const int m = g + p * P::G0;
-                if (m >= t0 && m < t0 + nt) bb[(int64_t)(m - t0) * plane] = a[p];
+            for (int p = 0; p < R0 / 2; ++p) {
+                if ((unsigned)(r + p * P::G0) < (unsigned)nt) bb[off] = a[p];
+                off += step1;
             }
         }
     }
@@ -357,19 +430,11 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__r
 // ---------------------------------------------------------------------------
 // Row passes along x (real <-> half complex), two real rows per complex line.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T fetch_block(const T *__restrict__ f, const int *__restrict__ map, int nbx, int nby, int lb,
-                                         int xr, int yr, int zr)
-{
-    const int bi = map[((zr >> lb) * nby + (yr >> lb)) * nbx + (xr >> lb)];
-    if (bi < 0) return T(0);
-    const int m = (1 << lb) - 1;
-    return f[((int64_t)bi << (3 * lb)) + ((((zr & m) << lb) + (yr & m)) << lb) + (xr & m)];
-}
-
 // Forward: rows (y, y+1) of source plane z, x in [s0x, s0x + Lsx), from the
-// block layout (dense_ld == 0) or from a dense box with row length dense_ld.
-template <typename T, int LOGM, int LPC>
+// block layout (HALF: the apply, where the row lies in [0, M/2) so the first
+// stage's upper inputs are zero at compile time) or from a dense box with row
+// length dense_ld (the spectrum build, full rows).
+template <typename T, int LOGM, int LPC, bool HALF>
 __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_forward(const T *__restrict__ f, Cx<T> *__restrict__ A,
                                                                        PoissonGeom g, const Cx<T> *__restrict__ twg,
                                                                        int npairs, int lb, int dense_ld)
@@ -390,31 +455,52 @@ __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_forward(const T *
     constexpr int R0 = 1 << P::LG0;
     constexpr int NG0 = P::G0 / P::TPC;
     Cx<T> a[NG0][R0];
+    if constexpr (HALF) {
+        // the block-map row and the in-block offset of rows (y, y+1) are
+        // fixed per line; y is even and b >= 2, so both rows share a block
+        const int bm = (1 << lb) - 1;
+        const int *mrow = g.srcmap + ((zi >> lb) * g.nbs[1] + (yi >> lb)) * g.nbs[0];
+        const int inner = (((zi & bm) << lb) + (yi & bm)) << lb;
 #pragma unroll
-    for (int i = 0; i < NG0; ++i) {
-        const int gg = t + i * P::TPC;
+        for (int i = 0; i < NG0; ++i) {
+            const int xr = t + i * P::TPC - g.s0[0];
 #pragma unroll
-        for (int p = 0; p < R0; ++p) {
-            const int x = gg + p * P::G0;
-            Cx<T> v{T(0), T(0)};
-            if (live && x >= g.s0[0] && x < g.s0[0] + g.Ls[0]) {
-                if (dense_ld) {
-                    const T *row = ff + ((int64_t)(g.s0[2] + zi) * g.M[1] + (g.s0[1] + yi)) * dense_ld;
+            for (int p = 0; p < R0 / 2; ++p) {
+                const int x = xr + p * P::G0;
+                Cx<T> v{T(0), T(0)};
+                if (live && (unsigned)x < (unsigned)g.Ls[0]) {
+                    const int bi = mrow[x >> lb];
+                    if (bi >= 0) {
+                        const T *q = ff + ((int64_t)bi << (3 * lb)) + inner + (x & bm);
+                        v.x = q[0];
+                        v.y = q[1 << lb];
+                    }
+                }
+                a[i][p] = v;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NG0; ++i) {
+            const int gg = t + i * P::TPC;
+            const T *row = ff + ((int64_t)(g.s0[2] + zi) * g.M[1] + (g.s0[1] + yi)) * dense_ld;
+#pragma unroll
+            for (int p = 0; p < R0; ++p) {
+                const int x = gg + p * P::G0;
+                Cx<T> v{T(0), T(0)};
+                if (live && x >= g.s0[0] && x < g.s0[0] + g.Ls[0]) {
                     v.x = row[x];
                     v.y = row[dense_ld + x];
-                } else {
-                    v.x = fetch_block(ff, g.srcmap, g.nbs[0], g.nbs[1], lb, x - g.s0[0], yi, zi);
-                    v.y = fetch_block(ff, g.srcmap, g.nbs[0], g.nbs[1], lb, x - g.s0[0], yi + 1, zi);
                 }
+                a[i][p] = v;
             }
-            a[i][p] = v;
         }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < NG0; ++i) {
         const int gg = t + i * P::TPC;
-        dif_group<LOGM, LOGM, P::LG0>(a[i], gg, tw);
+        dif_group<LOGM, LOGM, P::LG0, HALF>(a[i], gg, tw);
 #pragma unroll
         for (int q = 0; q < R0; ++q) s[ad(l, q * P::G0 + gg)] = a[i][q];
     }
@@ -512,23 +598,26 @@ __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_inverse(const Cx<
     const T sc = T(g.scale);
     T *uu = u + blockIdx.y * g.ustride;
     const int bm = g.b - 1;
+    const int *mrow = g.tgtmap + ((zi >> lb) * g.nbt[1] + (yi >> lb)) * g.nbt[0];
+    const int inner = (((zi & bm) << lb) + (yi & bm)) << lb;
     constexpr int R0 = 1 << P::LG0;
+    // target x lies in [0, M/2): only the lower half of the last outputs
 #pragma unroll
     for (int gg = t; gg < P::G0; gg += P::TPC) {
         Cx<T> a[R0];
 #pragma unroll
         for (int q = 0; q < R0; ++q) a[q] = s[ad(l, q * P::G0 + gg)];
-        dit_group<LOGM, LOGM, P::LG0>(a, gg, tw);
+        dit_group<LOGM, LOGM, P::LG0, true>(a, gg, tw);
+        const int xr = gg - g.t0[0];
 #pragma unroll
-        for (int p = 0; p < R0; ++p) {
-            const int x = gg + p * P::G0;
-            const int xi = x - g.t0[0];
-            if (xi < 0 || xi >= g.Lt[0]) continue;
-            const int bi0 = g.tgtmap[((zi >> lb) * g.nbt[1] + (yi >> lb)) * g.nbt[0] + (xi >> lb)];
+        for (int p = 0; p < R0 / 2; ++p) {
+            const int xi = xr + p * P::G0;
+            if ((unsigned)xi >= (unsigned)g.Lt[0]) continue;
+            const int bi0 = mrow[xi >> lb];
             if (bi0 < 0) continue;
-            const int64_t base = ((int64_t)bi0 << (3 * lb)) + ((((zi & bm) << lb) + (yi & bm)) << lb) + (xi & bm);
-            uu[base] = sc * a[p].x;
-            uu[base + (1 << lb)] = sc * a[p].y;   // row y + 1 of the same block (y is even, b >= 2)
+            T *q = uu + ((int64_t)bi0 << (3 * lb)) + inner + (xi & bm);
+            q[0] = sc * a[p].x;
+            q[1 << lb] = sc * a[p].y;   // row y + 1 of the same block (y is even, b >= 2)
         }
     }
 }
@@ -597,7 +686,16 @@ lgf_status row_forward_m(lgf_ctx *ctx, const PoissonGeom &g, const T *f, Cx<T> *
                          int lb, int dense_ld, cudaStream_t s)
 {
     using C = RowCfg<T, LOGM>;
-    auto kern = k_row_forward<T, LOGM, C::LPC>;
+    auto kern = k_row_forward<T, LOGM, C::LPC, true>;
+    if (dense_ld) {
+        // full dense rows: only the FP64 spectrum build
+        if constexpr (sizeof(T) == 8)
+            kern = k_row_forward<T, LOGM, C::LPC, false>;
+        else
+            return fail(ctx, LGF_EINVAL, "row forward: FP32 dense rows");
+    } else if (g.s0[0] < 0 || 2 * (g.s0[0] + g.Ls[0]) > g.M[0]) {
+        return fail(ctx, LGF_EINVAL, "row forward: source beyond half the transform length");
+    }
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
     const int npairs = (g.Ls[1] / 2) * g.Ls[2];
@@ -615,6 +713,8 @@ lgf_status row_inverse_m(lgf_ctx *ctx, const PoissonGeom &g, const Cx<T> *A, T *
 {
     using C = RowCfg<T, LOGM>;
     auto kern = k_row_inverse<T, LOGM, C::LPC>;
+    if (g.t0[0] < 0 || 2 * (g.t0[0] + g.Lt[0]) > g.M[0])
+        return fail(ctx, LGF_EINVAL, "row inverse: target beyond half the transform length");
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
     const int npairs = (g.Lt[1] / 2) * g.Lt[2];
@@ -632,13 +732,20 @@ lgf_status col_forward_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx
                          int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
 {
     using C = ColCfg<T, LOGM>;
-    auto kern = k_col_forward<T, LOGM, C::W>;
+    auto kern = k_col_forward<T, LOGM, C::W, true>;
+    if (lo + n > (1 << LOGM) / 2) {
+        // full-length input: only the FP64 spectrum build's z pass
+        if constexpr (sizeof(T) == 8)
+            kern = k_col_forward<T, LOGM, C::W, false>;
+        else
+            return fail(ctx, LGF_EINVAL, "column forward: FP32 input beyond half the transform length");
+    }
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
-    dim3 grid((K + C::W - 1) / C::W, nplanes, nfields);
+    dim3 grid(col_ctas<C::W>(K, nplanes), nfields);
     const int ph = prof_begin(ctx, s, name);
-    kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(in, out, K, lo, n, rs, os, in_plane, out_plane, in_field, out_field,
-                                              tw);
+    kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(in, out, K, nplanes, lo, n, rs, os, in_plane, out_plane, in_field,
+                                              out_field, tw);
     LGF_CHECK_LAUNCH(ctx, name);
     prof_end(ctx, s, ph);
     return LGF_OK;
@@ -651,12 +758,13 @@ lgf_status col_inverse_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx
 {
     using C = ColCfg<T, LOGM>;
     auto kern = k_col_inverse<T, LOGM, C::W>;
+    if (lo < 0 || lo + n > (1 << LOGM) / 2) return fail(ctx, LGF_EINVAL, "column inverse: rows beyond half the length");
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
-    dim3 grid((K + C::W - 1) / C::W, nplanes, nfields);
+    dim3 grid(col_ctas<C::W>(K, nplanes), nfields);
     const int ph = prof_begin(ctx, s, name);
-    kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(in, out, K, lo, n, rs, os, in_plane, out_plane, in_field, out_field,
-                                              tw);
+    kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(in, out, K, nplanes, lo, n, rs, os, in_plane, out_plane, in_field,
+                                              out_field, tw);
     LGF_CHECK_LAUNCH(ctx, name);
     prof_end(ctx, s, ph);
     return LGF_OK;
@@ -668,9 +776,11 @@ lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T 
 {
     using C = ColCfg<T, LOGM>;
     auto kern = k_col_convolve<T, LOGM, C::W>;
+    if (g.s0[2] < 0 || g.t0[2] < 0 || 2 * (g.s0[2] + g.Ls[2]) > g.M[2] || 2 * (g.t0[2] + g.Lt[2]) > g.M[2])
+        return fail(ctx, LGF_EINVAL, "z pass: planes beyond half the transform length");
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
-    dim3 grid(nfields, (g.Kx + C::W - 1) / C::W, g.M[1]);
+    dim3 grid(nfields * col_ctas<C::W>(g.Kx, g.M[1]));
     const int ph = prof_begin(ctx, s, "poisson_z_convolve");
     kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(B, spec, g.Kx, g.M[1], g.s0[2], g.Ls[2], g.t0[2], g.Lt[2], g.Bstride,
                                               tw);
