@@ -170,8 +170,10 @@ typedef struct {
    allowed).  The Poisson parts (each with its own integrating factor when no
    other problem shares its group) and the groups that read only batch inputs
    are independent units: they are spread over up to 4 concurrent branches
-   (the caller's stream and 3 context streams, each with its own scratch),
-   longest first onto the least loaded branch; groups of several
+   (context streams forked from and joined back to the caller's stream, each
+   with its own scratch), longest first onto the least loaded branch; the
+   branch with the longest unit runs at the greatest stream priority so that
+   the critical path is scheduled first.  Groups of several
    POISSON_THEN_INTFACTOR problems run after the branches join.  On a
    non-default stream the whole batch is captured once into a CUDA graph,
    and later calls with an identical batch (same block lists, pointers,

@@ -544,9 +544,15 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         if ((st = intf_prepare_scratch(ctx, groups[k].plan, groups[k].nf, (int)groups[k].jobs.size())) != LGF_OK)
             return st;
     if (nb > 1) {
+        // branch 0 carries the longest unit (the critical path): its stream
+        // has the greatest priority, so its CTAs are scheduled first and the
+        // other branches fill the SMs it leaves idle
         if (!ctx->ev_fork) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-        for (int b = 1; b < nb; ++b) {
-            if (!ctx->br[b]) LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->br[b], cudaStreamNonBlocking));
+        int least = 0, greatest = 0;
+        LGF_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        for (int b = 0; b < nb; ++b) {
+            if (!ctx->br[b])
+                LGF_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->br[b], cudaStreamNonBlocking, b == 0 ? greatest : least));
             if (!ctx->ev_join[b]) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming));
         }
     }
@@ -561,10 +567,10 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         }
         if (nb > 1) {
             LGF_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
-            for (int b = 1; b < nb; ++b) LGF_CUDA(ctx, cudaStreamWaitEvent(ctx->br[b], ctx->ev_fork, 0));
+            for (int b = 0; b < nb; ++b) LGF_CUDA(ctx, cudaStreamWaitEvent(ctx->br[b], ctx->ev_fork, 0));
         }
         for (auto &u : units) {
-            cudaStream_t us = u.branch == 0 ? s : ctx->br[u.branch];
+            cudaStream_t us = nb > 1 ? ctx->br[u.branch] : s;
             ctx->cur = &ctx->scr[u.branch];
             lgf_status e2 = LGF_OK;
             if (u.prob >= 0) {
@@ -584,7 +590,7 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         }
         ctx->cur = &ctx->scr[0];
         if (nb > 1)
-            for (int b = 1; b < nb; ++b) {
+            for (int b = 0; b < nb; ++b) {
                 LGF_CUDA(ctx, cudaEventRecord(ctx->ev_join[b], ctx->br[b]));
                 LGF_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join[b], 0));
             }

@@ -325,8 +325,15 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T>
 // for big boxes the spectrum is larger than L2.  Source and target planes
 // lie in [0, M/2): the first stage skips its zero upper inputs and the last
 // stage forms only its lower outputs.
+// Resident CTAs per SM that the register allocation must allow (FP32 at the
+// common lengths 256 and 512: 32 and 24 warps).
+template <typename T, int LOGM>
+struct ConvOcc {
+    static constexpr int value = sizeof(T) == 4 ? (LOGM == 8 ? 4 : LOGM == 9 ? 3 : 1) : 1;
+};
+
 template <typename T, int LOGM, int W>
-__global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_convolve(Cx<T> *__restrict__ B, const T *__restrict__ spec,
+__global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) k_col_convolve(Cx<T> *__restrict__ B, const T *__restrict__ spec,
                                                                       int K, int My, int s0, int ns, int t0, int nt,
                                                                       int64_t field, const Cx<T> *__restrict__ twg)
 {
