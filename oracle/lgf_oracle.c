@@ -20,6 +20,10 @@
  *   - u = E(alpha) f with E(n) = prod_i e^{-2 alpha} I_{|n_i|}(2 alpha),
  *     untruncated, as three exact one-dimensional sums over a dense box.
  *                                    [Sec. 2.3 footnote; App. A, Eq. lgf_intfac]
+ *   - G_K(alpha)(n) = -int_alpha^inf prod_i e^{-2t} I_{|n_i|}(2t) dt, split as
+ *     G_L(n) + R(alpha)(n) with R(alpha)(n) = int_0^alpha (same integrand) dt
+ *     by adaptive Gauss-Kronrod (7/15) on unit panels of [0, alpha].
+ *                               [App. A, Eq. lgf_iflap and the partition of G_K]
  *
  * Parity pins for every function live in tests/test_oracle_pins.py.
  */
@@ -193,6 +197,37 @@ double orc_lgf_quad(int n1, int n2, int n3)
 }
 
 /* ------------------------------------------------------------------------ */
+/* G_K(alpha) = G_L + R(alpha), R(alpha)(n) = int_0^alpha G_E(t)(n) dt.      */
+/* ------------------------------------------------------------------------ */
+double orc_lgf_r(double alpha, int n1, int n2, int n3)
+{
+    if (!(alpha >= 0.0) || isinf(alpha)) return NAN;
+    if (alpha == 0.0) return 0.0;
+    lgf_q q;
+    q.n[0] = abs(n1); q.n[1] = abs(n2); q.n[2] = abs(n3);
+    q.nmax = q.n[0];
+    if (q.n[1] > q.nmax) q.nmax = q.n[1];
+    if (q.n[2] > q.nmax) q.nmax = q.n[2];
+    q.buf = (double *)malloc(sizeof(double) * (q.nmax + 1));
+    if (!q.buf) return NAN;
+    /* same absolute scale as the G_L quadrature, so that G_K = G_L + R keeps
+       the accuracy of G_L */
+    const double scale = 1.0 / (4.0 * ORC_PI * (1.0 + sqrt((double)q.n[0] * q.n[0] + (double)q.n[1] * q.n[1] + (double)q.n[2] * q.n[2])));
+    double s = 0.0;
+    for (double a = 0.0; a < alpha; a += 1.0) {
+        const double b = a + 1.0 < alpha ? a + 1.0 : alpha;
+        s += adapt(lgf_integrand, &q, a, b, 1e-11 * scale, 0);
+    }
+    free(q.buf);
+    return s;
+}
+
+double orc_gk_quad(double alpha, int n1, int n2, int n3)
+{
+    return orc_lgf_quad(n1, n2, n3) + orc_lgf_r(alpha, n1, n2, n3);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Far-field asymptotic expansion (monomials in X = n1^2, Y = n2^2, Z = n3^2). */
 /* ------------------------------------------------------------------------ */
 typedef struct { int a, b, c; double v; } mono;
@@ -261,6 +296,26 @@ int orc_lgf_table(int R, double *out)
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < n; ++i)
         out[i] = orc_lgf_quad(abc[3 * i], abc[3 * i + 1], abc[3 * i + 2]);
+    free(abc);
+    return 0;
+}
+
+/* Table of G_K(alpha) over the same sorted offsets. */
+int orc_gk_table(double alpha, int R, double *out)
+{
+    if (R < 0 || !out || !(alpha >= 0.0)) return -1;
+    const int64_t n = orc_table_size(R);
+    int *abc = (int *)malloc(sizeof(int) * 3 * (size_t)n);
+    if (!abc) return -2;
+    for (int a = 0; a <= R; ++a)
+        for (int b = 0; b <= a; ++b)
+            for (int c = 0; c <= b; ++c) {
+                int64_t i = orc_table_index(a, b, c);
+                abc[3 * i] = a; abc[3 * i + 1] = b; abc[3 * i + 2] = c;
+            }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = orc_gk_quad(alpha, abc[3 * i], abc[3 * i + 1], abc[3 * i + 2]);
     free(abc);
     return 0;
 }

@@ -14,6 +14,9 @@ it follows; the C source documents the numerical method):
   poisson_direct     u = dx^2 sum_m G_L(n-m) f(m)                Sec. 2.2, Eq. dpoisson_conv
   intfactor_weights  e^{-2a} I_n(2a), n = 0..nmax                App. A, Eq. lgf_intfac
   intfactor_box      u = E(alpha) f on a dense box (untruncated) Sec. 2.3 footnote
+  lgf_r              R(alpha)(n) = int_0^alpha G_E(t)(n) dt      App. A (partition of G_K)
+  gk_quad, gk_table  G_K(alpha) = G_L + R(alpha)                 App. A, Eq. lgf_iflap
+  kinv_direct        u = dx^2 sum_m G_K(alpha)(n-m) f(m)         Sec. 2.2 (action of K^{-1})
 """
 from __future__ import annotations
 
@@ -67,6 +70,11 @@ def lib():
             L.orc_intfactor_weights.argtypes = [ctypes.c_double, ctypes.c_int, _dp]
             L.orc_intfactor_box.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_lgf_r.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_lgf_r.restype = ctypes.c_double
+            L.orc_gk_quad.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_gk_quad.restype = ctypes.c_double
+            L.orc_gk_table.argtypes = [ctypes.c_double, ctypes.c_int, _dp]
             _lib = L
     return _lib
 
@@ -207,3 +215,52 @@ def block_points(b: int, coords) -> np.ndarray:
     z, y, x = np.meshgrid(r, r, r, indexing="ij")
     loc = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
     return (coords[:, None, :] * b + loc[None, :, :]).reshape(-1, 3)
+
+
+def lgf_r(alpha: float, n1: int, n2: int, n3: int) -> float:
+    """R(alpha)(n) = int_0^alpha prod_i e^{-2t} I_{|n_i|}(2t) dt (App. A)."""
+    return float(lib().orc_lgf_r(float(alpha), int(n1), int(n2), int(n3)))
+
+
+def gk_quad(alpha: float, n1: int, n2: int, n3: int) -> float:
+    """G_K(alpha)(n) = G_L(n) + R(alpha)(n) (App. A, Eq. lgf_iflap)."""
+    return float(lib().orc_gk_quad(float(alpha), int(n1), int(n2), int(n3)))
+
+
+_gk_cache: dict = {}
+
+
+def gk_table(alpha: float, R: int) -> np.ndarray:
+    """G_K(alpha) over sorted offsets a >= b >= c >= 0, a <= R (cached)."""
+    key = (float(alpha), int(R))
+    if key not in _gk_cache:
+        out = np.empty(int(lib().orc_table_size(int(R))))
+        if lib().orc_gk_table(float(alpha), int(R), _p(out)) != 0:
+            raise RuntimeError("orc_gk_table failed")
+        _gk_cache[key] = out
+    return _gk_cache[key]
+
+
+def gk(n, alpha: float, R: int = 32) -> np.ndarray:
+    """G_K(alpha) at integer offsets n [..., 3]: table up to R, the G_L
+    expansion beyond (R(alpha) is below 1e-9 |G_L(0)| there for alpha <= 1,
+    App. A footnote; tests check the shell)."""
+    n = np.asarray(n, dtype=np.int64).reshape(-1, 3)
+    tab = gk_table(alpha, R)
+    L = lib()
+    return np.array([L.orc_lgf(_p(tab), int(R), int(a), int(b), int(c)) for a, b, c in n])
+
+
+def kinv_direct(alpha: float, b: int, src_coords, f, tgt_pts, dx: float = 1.0, R: int = 32) -> np.ndarray:
+    """u(t) = dx^2 sum_{m in src blocks} G_K(alpha)(t - m) f(m): the action of
+    K(alpha)^{-1} = [E(-alpha) L]^{-1} (Sec. 2.2) by direct summation."""
+    src = np.ascontiguousarray(src_coords, dtype=np.int32).reshape(-1, 3)
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(src.shape[0], b ** 3)
+    tp = np.ascontiguousarray(tgt_pts, dtype=np.int32).reshape(-1, 3)
+    tab = gk_table(alpha, R)
+    out = np.empty(tp.shape[0])
+    rc = lib().orc_poisson_direct(int(b), src.shape[0], _p(src, _ip), _p(f), tp.shape[0], _p(tp, _ip),
+                                  float(dx), _p(tab), int(R), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_poisson_direct failed ({rc})")
+    return out

@@ -281,3 +281,83 @@ def test_plate_marker_spacing():
     X = li.plate_markers(40.0, 80.0, 1.05, 30.0)
     d = np.linalg.norm(X[1] - X[0])
     assert 1.0 < d < 1.1
+
+
+# -------------------------------------------------------------- G_K(alpha)
+@pytest.mark.parametrize("alpha", [0.05, 0.25, 1.0, 2.0, 3.5])
+def test_gk_laplacian_is_heat_kernel(oracle, alpha):
+    """L G_K(alpha) = G_E(alpha): the symbol of G_K is e^{alpha sigma} / sigma
+    (App. A, Eq. lgf_iflap), so the 7-point Laplacian of the G_K values must
+    give the Bessel product of Eq. lgf_intfac.  A wrong lower limit, sign or
+    integrand in R(alpha) fails this."""
+    w = oracle.intfactor_weights(alpha, 12)
+    for n in [(0, 0, 0), (1, 0, 0), (1, 1, 0), (2, 1, 0), (3, 2, 1), (4, 0, 2), (6, 1, 1)]:
+        n = np.array(n)
+        g = lambda m: oracle.gk_quad(alpha, *m)
+        lap = sum(g(n + e) + g(n - e) for e in np.eye(3, dtype=int)) - 6.0 * g(n)
+        ge = w[abs(n[0])] * w[abs(n[1])] * w[abs(n[2])]
+        assert abs(lap - ge) < 3e-15 + 1e-12 * ge, (alpha, tuple(n), lap, ge)
+
+
+def test_gk_at_alpha_zero_is_gl(oracle):
+    # R(0) = 0 (App. A partition): G_K(0) = G_L exactly
+    for n in [(0, 0, 0), (1, 0, 0), (5, 3, 2), (12, 0, 7)]:
+        assert oracle.gk_quad(0.0, *n) == oracle.lgf_quad(*n)
+
+
+def test_gk_equals_lgf_convolved_with_heat_kernel(oracle):
+    """G_K(alpha) = G_L * G_E(alpha) (the product e^{alpha sigma} / sigma of the
+    two symbols), summed directly from the G_L table and the Bessel weights: an
+    independent route to the same numbers."""
+    alpha, Rm, R = 0.5, 18, 32
+    w = oracle.intfactor_weights(alpha, Rm)
+    assert w[Rm] < 1e-21
+    tab = oracle.lgf_table(R)
+    r = np.arange(-Rm, Rm + 1)
+    mz, my, mx = np.meshgrid(r, r, r, indexing="ij")
+    ge = w[np.abs(mx)] * w[np.abs(my)] * w[np.abs(mz)]
+
+    def gl_of(dx, dy, dz):
+        a = np.sort(np.abs(np.stack([dx, dy, dz])), axis=0)[::-1]
+        idx = a[0] * (a[0] + 1) * (a[0] + 2) // 6 + a[1] * (a[1] + 1) // 2 + a[2]
+        return tab[idx]
+
+    for n in [(0, 0, 0), (1, 0, 0), (2, 2, 1), (5, 0, 3), (9, 4, 1)]:
+        conv = float(np.sum(gl_of(n[0] - mx, n[1] - my, n[2] - mz) * ge))
+        assert abs(conv - oracle.gk_quad(alpha, *n)) < 2e-15, n
+
+
+def test_gk_minus_gl_bound_from_paper(oracle):
+    """The footnote bound, with |n| read as the largest offset component: every
+    offset with max |n_i| > 10 stays below 1e-9 |G_L(0)| for alpha <= 1.  (With
+    the Euclidean norm the bound is missed narrowly: R(1)(10,1,0) is
+    1.24e-9 |G_L(0)|, so that reading is not the paper's.)"""
+    bound = GOLD["gk_minus_gl_bound"]["value"]
+    g0 = abs(oracle.lgf_quad(0, 0, 0))
+    for alpha in (0.25, 0.5, 1.0):
+        worst = 0.0
+        for a in (11, 12):
+            for b in range(0, a + 1, 3):
+                for c in range(0, b + 1, 4):
+                    worst = max(worst, abs(oracle.lgf_r(alpha, a, b, c)) / g0)
+        assert worst < bound, alpha
+    assert 1.1e-9 < oracle.lgf_r(1.0, 10, 1, 0) / g0 < 1.4e-9
+    # and R(alpha) grows with alpha (its integrand is positive)
+    vals = [oracle.lgf_r(a, 2, 1, 0) for a in (0.1, 0.2, 0.5, 1.0, 2.0)]
+    assert all(b > a > 0 for a, b in zip(vals, vals[1:]))
+
+
+def test_gk_table_and_direct_apply(oracle):
+    """The G_K table agrees with pointwise quadrature, and the direct-sum apply
+    with G_K reproduces the table for a unit point source (K^{-1} delta = G_K)."""
+    alpha, R = 0.75, 6
+    tab = oracle.gk_table(alpha, R)
+    for (a, b, c) in [(0, 0, 0), (3, 2, 1), (6, 6, 6), (5, 0, 0)]:
+        assert tab[oracle.table_index(a, b, c)] == oracle.gk_quad(alpha, a, b, c)
+    b = 4
+    f = np.zeros((1, b ** 3))
+    f[0, 0] = 1.0
+    tp = np.array([[0, 0, 0], [1, 2, 3], [-4, 1, 0], [3, 3, -2]])
+    got = oracle.kinv_direct(alpha, b, [[0, 0, 0]], f, tp, dx=1.0, R=R)
+    ref = [oracle.gk_quad(alpha, *t) for t in tp]
+    assert np.allclose(got, ref, rtol=0, atol=1e-16)
