@@ -491,6 +491,9 @@ EXTRA = {
                "RK right-hand sides (12 fields), FP32; one G_L apply of all fields per step",
     "plates64": "64 flat-plate problems, 16^3 blocks, N_b log-uniform in [8, 1200], 3 components, FP32; "
                 "one lgf_batch_apply of G_L then E(0.25) for every problem per step",
+    "kinv_sphere": "K(0.25)^{-1} on the surface blocks of the icosphere (5120 markers, radius 20 cells, 16^3 "
+                   "blocks, source = target = the blocks the 3-point delta touches), 3 components, FP32; one "
+                   "G_K(0.25) apply per step",
 }
 
 
@@ -508,6 +511,10 @@ def run_extra(args, rank, world, dist):
         probs = [(li.wake_domain(), lgf.LGF_OP_POISSON, 0.0)]
     elif args.workload == "plates64":
         probs = [(q, lgf.LGF_OP_POISSON_THEN_INTFACTOR, 0.25) for q in li.plate_batch()]
+    elif args.workload == "kinv_sphere":
+        q = li.sphere_ib()
+        q = li.Problem("sphere_surface", q.b, q.src, q.src.copy(), q.f, alphas=(0.25,))
+        probs = [(q, lgf.LGF_OP_KINV, 0.25)]
     else:
         raise ValueError(f"unknown workload {args.workload}")
     ctx = lgf.Context("f32", device=dev.index)
@@ -520,7 +527,8 @@ def run_extra(args, rank, world, dist):
         u = torch.empty(nf * p.tgt.shape[0] * p.b ** 3, dtype=torch.float32, device=dev)
         batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, nrhs=p.nrhs, op=op, alpha=a))
         points += float(u.numel())
-        for k, v in algorithmic_bytes_per_step(p, nf, 1 if op != lgf.LGF_OP_POISSON else 0).items():
+        n_intf = 1 if op in (lgf.LGF_OP_INTFACTOR, lgf.LGF_OP_POISSON_THEN_INTFACTOR) else 0
+        for k, v in algorithmic_bytes_per_step(p, nf, n_intf).items():
             alg_step[k] = alg_step.get(k, 0) + v
     s = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(s):

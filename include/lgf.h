@@ -132,6 +132,31 @@ LGF_API lgf_status lgf_poisson_apply(lgf_ctx *ctx, const lgf_blockset *src, cons
                              const void *f_dev, void *u_dev, int32_t ncomp, int32_t nrhs, double dx,
                              void *stream);
 
+/* G_K(alpha) at `n` integer offsets (App. A, Eq. lgf_iflap):
+     G_K(alpha)(n) = -int_alpha^inf prod_i e^{-2t} I_{|n_i|}(2t) dt
+                   = G_L(n) + R(alpha)(n),  R(alpha)(n) = int_0^alpha (same) dt,
+   the kernel of K(alpha)^{-1} = [E(-alpha) L]^{-1} (Sec. 2.2).  The context
+   builds one FP64 table per alpha on first use: R(alpha) by Gauss-Legendre
+   quadrature on the GPU over the offsets of the G_L table, added to it;
+   beyond the table radius the G_L expansion is used, and the build fails with
+   LGF_EUNSUPPORTED when R(alpha) on the table's outer shell exceeds
+   2.5e-16 (alpha too large for the radius: build a larger table).  alpha = 0
+   gives G_L.  offsets_dev [n][3] int32 and out_dev [n] double are device
+   pointers.  Errors: LGF_ENOTABLE, LGF_EINVAL (alpha < 0 or not finite),
+   LGF_EUNSUPPORTED (alpha > 64 or the shell check), LGF_ENOMEM, LGF_ECUDA. */
+LGF_API lgf_status lgf_kinv_lookup(lgf_ctx *ctx, double alpha, const int32_t *offsets_dev, int64_t n,
+                                   double *out_dev, void *stream);
+
+/* K(alpha)^{-1} apply (Sec. 2.2, the action of [E(-alpha) L]^{-1} through the
+   LGF G_K(alpha) of App. A):
+     u[r][c][t] = dx^2 * sum_{s in src} G_K(alpha)(n_t - m_s) f[r][c][s]
+   with the layouts, engine and errors of lgf_poisson_apply (only the kernel
+   spectrum differs; it is cached per transform shape and alpha).  alpha = 0
+   equals lgf_poisson_apply. */
+LGF_API lgf_status lgf_kinv_apply(lgf_ctx *ctx, double alpha, const lgf_blockset *src, const lgf_blockset *tgt,
+                                  const void *f_dev, void *u_dev, int32_t ncomp, int32_t nrhs, double dx,
+                                  void *stream);
+
 /* Integrating-factor apply (Sec. 2.3 footnote; App. A, Eq. lgf_intfac):
      u[r][c][t] = sum_{s in src} E_alpha(n_t - m_s) f[r][c][s],  alpha >= 0,
    with E_alpha truncated at the radius R where the 1-D factor falls below
@@ -149,7 +174,7 @@ LGF_API lgf_status lgf_intfactor_weights(lgf_ctx *ctx, double alpha, double *w_d
                                  void *stream);
 
 /* Batched applies.  Operations: */
-enum { LGF_OP_POISSON = 0, LGF_OP_INTFACTOR = 1, LGF_OP_POISSON_THEN_INTFACTOR = 2 };
+enum { LGF_OP_POISSON = 0, LGF_OP_INTFACTOR = 1, LGF_OP_POISSON_THEN_INTFACTOR = 2, LGF_OP_KINV = 3 };
 
 typedef struct {
     lgf_blockset src, tgt;   /* as in lgf_poisson_apply; for POISSON_THEN_INTFACTOR
@@ -181,7 +206,8 @@ typedef struct {
    recently used batches (so, e.g., double-buffered batches alternate
    without recapture).  u buffers must not alias one another or any f
    buffer of the same batch.  POISSON_THEN_INTFACTOR writes
-   E_alpha(G_L * f) into u_dev.  Results equal those of the single applies
+   E_alpha(G_L * f) into u_dev; KINV writes dx^2 G_K(alpha) * f (alpha is
+   the kernel's, no integrating factor follows).  Results equal those of the single applies
    bit for bit.  Errors: as the single applies. */
 LGF_API lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob, void *stream);
 

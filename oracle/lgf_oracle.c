@@ -300,8 +300,8 @@ int orc_lgf_table(int R, double *out)
     return 0;
 }
 
-/* Table of G_K(alpha) over the same sorted offsets. */
-int orc_gk_table(double alpha, int R, double *out)
+/* Table of R(alpha) over the same sorted offsets (G_K = G_L table + this). */
+int orc_r_table(double alpha, int R, double *out)
 {
     if (R < 0 || !out || !(alpha >= 0.0)) return -1;
     const int64_t n = orc_table_size(R);
@@ -315,7 +315,7 @@ int orc_gk_table(double alpha, int R, double *out)
             }
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < n; ++i)
-        out[i] = orc_gk_quad(alpha, abc[3 * i], abc[3 * i + 1], abc[3 * i + 2]);
+        out[i] = orc_lgf_r(alpha, abc[3 * i], abc[3 * i + 1], abc[3 * i + 2]);
     free(abc);
     return 0;
 }

@@ -74,7 +74,7 @@ def lib():
             L.orc_lgf_r.restype = ctypes.c_double
             L.orc_gk_quad.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.orc_gk_quad.restype = ctypes.c_double
-            L.orc_gk_table.argtypes = [ctypes.c_double, ctypes.c_int, _dp]
+            L.orc_r_table.argtypes = [ctypes.c_double, ctypes.c_int, _dp]
             _lib = L
     return _lib
 
@@ -234,10 +234,10 @@ def gk_table(alpha: float, R: int) -> np.ndarray:
     """G_K(alpha) over sorted offsets a >= b >= c >= 0, a <= R (cached)."""
     key = (float(alpha), int(R))
     if key not in _gk_cache:
-        out = np.empty(int(lib().orc_table_size(int(R))))
-        if lib().orc_gk_table(float(alpha), int(R), _p(out)) != 0:
-            raise RuntimeError("orc_gk_table failed")
-        _gk_cache[key] = out
+        r = np.empty(int(lib().orc_table_size(int(R))))
+        if lib().orc_r_table(float(alpha), int(R), _p(r)) != 0:
+            raise RuntimeError("orc_r_table failed")
+        _gk_cache[key] = lgf_table(R) + r
     return _gk_cache[key]
 
 

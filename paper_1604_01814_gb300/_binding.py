@@ -18,11 +18,11 @@ LIB_PATH = os.path.join(_PKG, "liblgf.so")
 
 LGF_OK, LGF_EINVAL, LGF_ENOMEM, LGF_ECUDA, LGF_ETIMEOUT, LGF_EUNSUPPORTED, LGF_ENOTABLE = range(7)
 LGF_F32, LGF_F64 = 0, 1
-LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR = 0, 1, 2
+LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR, LGF_OP_KINV = 0, 1, 2, 3
 
 # Every symbol include/lgf.h declares (checked by the symbol test).
 EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
-           "lgf_poisson_apply", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
+           "lgf_kinv_lookup", "lgf_poisson_apply", "lgf_kinv_apply", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
            "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_intfactor_apply_noalloc",
            "lgf_status_string", "lgf_last_error", "lgf_version")
 
@@ -73,6 +73,8 @@ def load(path: str = LIB_PATH):
         "lgf_table_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)],
         "lgf_table_lookup": [vp, vp, i64, vp, vp],
         "lgf_poisson_apply": [vp, bsp, bsp, vp, vp, i32, i32, dbl, vp],
+        "lgf_kinv_lookup": [vp, dbl, vp, i64, vp, vp],
+        "lgf_kinv_apply": [vp, dbl, bsp, bsp, vp, vp, i32, i32, dbl, vp],
         "lgf_intfactor_apply": [vp, dbl, bsp, bsp, vp, vp, i32, i32, vp],
         "lgf_intfactor_weights": [vp, dbl, vp, i32, ctypes.POINTER(i32), vp],
         "lgf_batch_apply": [vp, ctypes.POINTER(lgf_problem), i32, vp],
@@ -178,6 +180,27 @@ class Context:
                                              _stream_ptr(stream)), "lgf_table_lookup")
         return out
 
+    def kinv_lookup(self, alpha: float, offsets, stream=None):
+        import torch
+        off = offsets.to(device=f"cuda:{self.device}", dtype=torch.int32).contiguous()
+        out = torch.empty(off.shape[0], dtype=torch.float64, device=off.device)
+        self._check(self._L.lgf_kinv_lookup(self._h, float(alpha), off.data_ptr(), off.shape[0], out.data_ptr(),
+                                            _stream_ptr(stream)), "lgf_kinv_lookup")
+        return out
+
+    def kinv_apply(self, alpha: float, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1, dx: float = 1.0,
+                   stream=None):
+        s, sa = _blockset(b, src)
+        t, ta = _blockset(b, tgt)
+        nf = ncomp * nrhs
+        if s.nblocks and t.nblocks:
+            self._field(f, s.nblocks, b, nf, "f")
+        if t.nblocks:
+            self._field(u, t.nblocks, b, nf, "u")
+        self._check(self._L.lgf_kinv_apply(self._h, float(alpha), ctypes.byref(s), ctypes.byref(t), _ptr(f),
+                                           _ptr(u), ncomp, nrhs, float(dx), _stream_ptr(stream)), "lgf_kinv_apply")
+        return u
+
     def poisson_apply(self, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1, dx: float = 1.0, stream=None):
         s, sa = _blockset(b, src)
         t, ta = _blockset(b, tgt)
@@ -276,8 +299,16 @@ def lgf_table_lookup(ctx: Context, offsets, stream=None):
     return ctx.table_lookup(offsets, stream)
 
 
+def lgf_kinv_lookup(ctx: Context, alpha: float, offsets, stream=None):
+    return ctx.kinv_lookup(alpha, offsets, stream)
+
+
 def lgf_poisson_apply(ctx: Context, *a, **kw):
     return ctx.poisson_apply(*a, **kw)
+
+
+def lgf_kinv_apply(ctx: Context, *a, **kw):
+    return ctx.kinv_apply(*a, **kw)
 
 
 def lgf_intfactor_apply(ctx: Context, *a, **kw):

@@ -123,13 +123,14 @@ struct PreparedPoisson {
     Spectrum *spec = nullptr;
 };
 
+// kalpha = 0: the kernel G_L; kalpha > 0: G_K(kalpha).
 lgf_status prepare_poisson(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, int nfields,
-                           cudaStream_t s, PreparedPoisson *pp)
+                           double kalpha, cudaStream_t s, PreparedPoisson *pp)
 {
     if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "lgf_table_build has not been called");
     lgf_status st = poisson_plan(ctx, src, tgt, &pp->plan);
     if (st != LGF_OK) return st;
-    st = poisson_spectrum(ctx, pp->plan->g.M, &pp->spec, s);
+    st = poisson_spectrum(ctx, pp->plan->g.M, kalpha, &pp->spec, s);
     if (st != LGF_OK) return st;
     st = poisson_prepare_scratch(ctx, pp->plan, nfields);
     if (st != LGF_OK) return st;
@@ -220,6 +221,7 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
     ctx->pplans.clear();
     ctx->iplans.clear();
     for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
+    for (auto &kv : ctx->gk_tables) cudaFree(kv.second);
     for (auto &kv : ctx->tw32) cudaFree(kv.second);
     for (auto &kv : ctx->tw64) cudaFree(kv.second);
     for (auto &w : ctx->weights) {
@@ -257,9 +259,11 @@ lgf_status lgf_table_build(lgf_ctx *ctx, int32_t max_offset, void *stream)
     if (ctx->table_dev && ctx->table_radius >= R) return LGF_OK;
     st = table_build(ctx, R, (cudaStream_t)stream);
     if (st != LGF_OK) return st;
-    // spectra built from an older table are stale
+    // spectra and G_K tables built from an older table are stale
     for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
     ctx->spectra.clear();
+    for (auto &kv : ctx->gk_tables) cudaFree(kv.second);
+    ctx->gk_tables.clear();
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
     return LGF_OK;
@@ -280,14 +284,31 @@ lgf_status lgf_table_lookup(lgf_ctx *ctx, const int32_t *offsets_dev, int64_t n,
     if (st != LGF_OK) return st;
     if (!ctx->table_dev) return fail(ctx, LGF_ENOTABLE, "table not built");
     if (n < 0 || (n > 0 && (!offsets_dev || !out_dev))) return fail(ctx, LGF_EINVAL, "table_lookup: bad arguments");
-    return table_lookup(ctx, offsets_dev, n, out_dev, (cudaStream_t)stream);
+    return table_lookup(ctx, ctx->table_dev, offsets_dev, n, out_dev, (cudaStream_t)stream);
 }
 
-lgf_status lgf_poisson_apply(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, const void *f_dev,
-                             void *u_dev, int32_t ncomp, int32_t nrhs, double dx, void *stream)
+lgf_status lgf_kinv_lookup(lgf_ctx *ctx, double alpha, const int32_t *offsets_dev, int64_t n, double *out_dev,
+                           void *stream)
 {
     lgf_status st = enter(ctx);
     if (st != LGF_OK) return st;
+    if (!ctx->table_dev) return fail(ctx, LGF_ENOTABLE, "table not built");
+    if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(ctx, LGF_EINVAL, "alpha must be >= 0 and finite");
+    if (n < 0 || (n > 0 && (!offsets_dev || !out_dev))) return fail(ctx, LGF_EINVAL, "kinv_lookup: bad arguments");
+    const double *table = nullptr;
+    if ((st = gk_table(ctx, alpha, &table, (cudaStream_t)stream)) != LGF_OK) return st;
+    return table_lookup(ctx, table, offsets_dev, n, out_dev, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+lgf_status kernel_apply(lgf_ctx *ctx, double kalpha, const lgf_blockset *src, const lgf_blockset *tgt,
+                        const void *f_dev, void *u_dev, int32_t ncomp, int32_t nrhs, double dx, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (!(kalpha >= 0.0) || !std::isfinite(kalpha)) return fail(ctx, LGF_EINVAL, "alpha must be >= 0 and finite");
     if ((st = check_blockset(ctx, src, "source")) != LGF_OK) return st;
     if ((st = check_blockset(ctx, tgt, "target")) != LGF_OK) return st;
     if (src->b != tgt->b) return fail(ctx, LGF_EINVAL, "source and target block edges differ");
@@ -302,8 +323,23 @@ lgf_status lgf_poisson_apply(lgf_ctx *ctx, const lgf_blockset *src, const lgf_bl
         return LGF_OK;
     }
     PreparedPoisson pp;
-    if ((st = prepare_poisson(ctx, src, tgt, nf, s, &pp)) != LGF_OK) return st;
+    if ((st = prepare_poisson(ctx, src, tgt, nf, kalpha, s, &pp)) != LGF_OK) return st;
     return poisson_run(ctx, pp.plan, pp.spec, f_dev, u_dev, nf, dx, s);
+}
+}  // namespace
+
+extern "C" {
+
+lgf_status lgf_poisson_apply(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, const void *f_dev,
+                             void *u_dev, int32_t ncomp, int32_t nrhs, double dx, void *stream)
+{
+    return kernel_apply(ctx, 0.0, src, tgt, f_dev, u_dev, ncomp, nrhs, dx, stream);
+}
+
+lgf_status lgf_kinv_apply(lgf_ctx *ctx, double alpha, const lgf_blockset *src, const lgf_blockset *tgt,
+                          const void *f_dev, void *u_dev, int32_t ncomp, int32_t nrhs, double dx, void *stream)
+{
+    return kernel_apply(ctx, alpha, src, tgt, f_dev, u_dev, ncomp, nrhs, dx, stream);
 }
 
 lgf_status lgf_intfactor_weights(lgf_ctx *ctx, double alpha, double *w_dev, int32_t cap, int32_t *radius,
@@ -421,7 +457,7 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         if ((st = check_blockset(ctx, &p.src, "batch source")) != LGF_OK) return st;
         if ((st = check_blockset(ctx, &p.tgt, "batch target")) != LGF_OK) return st;
         if (p.src.b != p.tgt.b) return fail(ctx, LGF_EINVAL, "batch: block edges differ");
-        if (p.op < LGF_OP_POISSON || p.op > LGF_OP_POISSON_THEN_INTFACTOR || p.reserved != 0)
+        if (p.op < LGF_OP_POISSON || p.op > LGF_OP_KINV || p.reserved != 0)
             return fail(ctx, LGF_EINVAL, "batch: unknown operation");
         if (p.op != LGF_OP_POISSON && (!(p.alpha >= 0.0) || !std::isfinite(p.alpha)))
             return fail(ctx, LGF_EINVAL, "batch: alpha must be >= 0 and finite");
@@ -456,9 +492,11 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         const lgf_problem &p = probs[i];
         const int nf = p.ncomp * p.nrhs;
         if (p.tgt.nblocks == 0 || p.src.nblocks == 0) continue;
-        if (p.op != LGF_OP_INTFACTOR)
-            if ((st = prepare_poisson(ctx, &p.src, &p.tgt, nf, s, &pois[i])) != LGF_OK) return st;
-        if (p.op == LGF_OP_POISSON) continue;
+        if (p.op != LGF_OP_INTFACTOR) {
+            const double kalpha = p.op == LGF_OP_KINV ? p.alpha : 0.0;
+            if ((st = prepare_poisson(ctx, &p.src, &p.tgt, nf, kalpha, s, &pois[i])) != LGF_OK) return st;
+        }
+        if (p.op == LGF_OP_POISSON || p.op == LGF_OP_KINV) continue;
         PreparedIntf pi;
         const lgf_blockset *isrc = p.op == LGF_OP_INTFACTOR ? &p.src : &p.tgt;
         if ((st = prepare_intf(ctx, p.alpha, isrc, &p.tgt, nf, s, &pi)) != LGF_OK) return st;

@@ -109,7 +109,12 @@ struct lgf_ctx {
     // twiddles per log2 length: exp(-2 pi i m / M), m < M
     std::map<int, void *> tw32, tw64;
 
-    std::map<std::array<int, 3>, lgf::Spectrum> spectra;
+    // G_K(alpha) tables (alpha > 0) over the same offsets as the G_L table
+    std::map<double, double *> gk_tables;
+
+    // kernel spectra per transform-box shape and kernel (alpha = 0: G_L,
+    // alpha > 0: G_K(alpha))
+    std::map<std::pair<std::array<int, 3>, double>, lgf::Spectrum> spectra;
     std::vector<std::unique_ptr<lgf::PoissonPlan>> pplans;
     std::vector<std::unique_ptr<lgf::IntfPlan>> iplans;
     std::vector<std::unique_ptr<lgf::IntfWeights>> weights;
@@ -177,13 +182,15 @@ void prof_end(lgf_ctx *ctx, cudaStream_t s, int handle);
 
 // Table (lgf_table.cu)
 lgf_status table_build(lgf_ctx *ctx, int radius, cudaStream_t s);
-lgf_status table_lookup(lgf_ctx *ctx, const int32_t *off, int64_t n, double *out, cudaStream_t s);
-lgf_status kernel_window(lgf_ctx *ctx, const int M[3], double *box, cudaStream_t s);
+lgf_status gk_table(lgf_ctx *ctx, double alpha, const double **out, cudaStream_t s);
+lgf_status table_lookup(lgf_ctx *ctx, const double *table, const int32_t *off, int64_t n, double *out,
+                        cudaStream_t s);
+lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], double *box, cudaStream_t s);
 lgf_status bessel_weights(lgf_ctx *ctx, double z, int nmax, double *out_dev, cudaStream_t s);
 
 // Poisson (lgf_poisson.cu)
 lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, PoissonPlan **out);
-lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], Spectrum **out, cudaStream_t s);
+lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum **out, cudaStream_t s);
 lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const void *f, void *u, int nfields,
                        double dx, cudaStream_t s);
 lgf_status poisson_prepare_scratch(lgf_ctx *ctx, const PoissonPlan *pl, int nfields);

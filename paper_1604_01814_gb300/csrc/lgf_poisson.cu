@@ -231,15 +231,19 @@ lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockse
     return LGF_OK;
 }
 
-lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], Spectrum **out, cudaStream_t s)
+lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum **out, cudaStream_t s)
 {
-    const std::array<int, 3> key{M[0], M[1], M[2]};
+    const std::array<int, 3> shape{M[0], M[1], M[2]};
+    const auto key = std::make_pair(shape, alpha);
     auto it = ctx->spectra.find(key);
     if (it != ctx->spectra.end()) {
         *out = &it->second;
         return LGF_OK;
     }
     if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "poisson: lgf_table_build has not been called");
+    const double *table = nullptr;
+    lgf_status tst = gk_table(ctx, alpha, &table, s);
+    if (tst != LGF_OK) return tst;
     PoissonGeom g{};
     for (int d = 0; d < 3; ++d) {
         g.M[d] = M[d];
@@ -274,7 +278,7 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], Spectrum **out, cudaSt
         cudaFree(spec);
         return fail(ctx, LGF_ENOMEM, "poisson: kernel spectrum scratch allocation failed");
     }
-    lgf_status st = kernel_window(ctx, M, box, s);
+    lgf_status st = kernel_window(ctx, table, M, box, s);
     if (st == LGF_OK)
         st = run_passes<double>(ctx, g, box, nullptr, A, B, nullptr, 1, M[0], true, s);
     if (st == LGF_OK) {
@@ -292,7 +296,7 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], Spectrum **out, cudaSt
         return st;
     }
     Spectrum sp;
-    sp.M = key;
+    sp.M = shape;
     sp.dev = spec;
     auto ins = ctx->spectra.emplace(key, sp);
     *out = &ins.first->second;

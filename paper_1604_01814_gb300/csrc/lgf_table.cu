@@ -10,6 +10,14 @@
 // large-argument series; with t = T / s^2 the tail becomes a smooth integral
 // over s in (0, 1] that the same Gauss-Legendre rule evaluates.
 //
+// G_K(alpha) (App. A, Eq. lgf_iflap) is built on top of the G_L table as
+// G_L + R(alpha), R(alpha)(n) = int_0^alpha prod_i e^{-2t} I_{|n_i|}(2t) dt,
+// with the same Gauss-Legendre rule on panels of width <= 1/2 of [0, alpha]
+// (the integrand is smooth and bounded by 1 there).  Beyond the table radius
+// G_K takes the G_L expansion; the builder requires R(alpha) on the outer
+// shell to be negligible (the footnote of Sec. 2.2: R decays faster than any
+// exponential), else the table must grow.
+//
 // Beyond the table radius G_L is taken from its far-field expansion
 // -1/(4 pi r) + T3 + T5 + T7 (terms of order r^-3, r^-5, r^-7; Sec. 2.2 and
 // the App. A footnote give the leading term), whose terms follow from
@@ -184,6 +192,24 @@ __global__ void k_table(const int *abc, int64_t n, const double *B, const double
     }
 }
 
+// G_K(alpha) = G_L + R(alpha) per sorted offset; the largest |R| on the
+// outer shell a = R goes to *shell.
+__global__ void k_rtable(const int *abc, int64_t n, const double *B, const double *wt, int nnodes, int R,
+                         const double *gl, double *gk, unsigned long long *shell)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = abc[3 * i], b = abc[3 * i + 1], c = abc[3 * i + 2];
+    const int ld = R + 1;
+    double r = 0.0;
+    for (int j = 0; j < nnodes; ++j) {
+        const double *bj = B + (size_t)j * ld;
+        r += wt[j] * (bj[a] * bj[b] * bj[c]);
+    }
+    gk[i] = gl[i] + r;
+    if (a == R) atomicMax(shell, (unsigned long long)__double_as_longlong(fabs(r)));
+}
+
 __global__ void k_lookup(const double *table, int R, const int32_t *off, int64_t n, double *out)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -208,13 +234,10 @@ __global__ void k_bessel_one(double z, int nmax, double *out) { ive_ratio(z, nma
 
 }  // namespace
 
-lgf_status table_build(lgf_ctx *ctx, int R, cudaStream_t s)
+namespace {
+// Sorted offsets a >= b >= c >= 0, a <= R, in table order.
+std::vector<int> sorted_offsets(int R)
 {
-    const double T = 24.0 * R * (double)R + 200.0;
-    std::vector<double> edge{0.0, 0.25};
-    while (edge.back() < T) edge.push_back(std::min(T, edge.back() * 1.5));
-    const int npanel = (int)edge.size() - 1;
-    const int nnodes = npanel * kGL;
     const int64_t n = (int64_t)(R + 1) * (R + 2) * (R + 3) / 6;
     std::vector<int> abc(3 * n);
     for (int a = 0; a <= R; ++a)
@@ -225,6 +248,19 @@ lgf_status table_build(lgf_ctx *ctx, int R, cudaStream_t s)
                 abc[3 * i + 1] = b;
                 abc[3 * i + 2] = c;
             }
+    return abc;
+}
+}  // namespace
+
+lgf_status table_build(lgf_ctx *ctx, int R, cudaStream_t s)
+{
+    const double T = 24.0 * R * (double)R + 200.0;
+    std::vector<double> edge{0.0, 0.25};
+    while (edge.back() < T) edge.push_back(std::min(T, edge.back() * 1.5));
+    const int npanel = (int)edge.size() - 1;
+    const int nnodes = npanel * kGL;
+    const int64_t n = (int64_t)(R + 1) * (R + 2) * (R + 3) / 6;
+    const std::vector<int> abc = sorted_offsets(R);
 
     double *glx = nullptr, *glw = nullptr, *dedge = nullptr, *t = nullptr, *wt = nullptr, *B = nullptr;
     double *table = nullptr;
@@ -275,17 +311,92 @@ lgf_status table_build(lgf_ctx *ctx, int R, cudaStream_t s)
     return LGF_OK;
 }
 
-lgf_status table_lookup(lgf_ctx *ctx, const int32_t *off, int64_t n, double *out, cudaStream_t s)
+lgf_status gk_table(lgf_ctx *ctx, double alpha, const double **out, cudaStream_t s)
+{
+    if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "lgf_table_build has not been called");
+    if (alpha == 0.0) {
+        *out = ctx->table_dev;
+        return LGF_OK;
+    }
+    if (!(alpha > 0.0) || !(alpha <= 64.0))
+        return fail(ctx, LGF_EUNSUPPORTED, "G_K: alpha must lie in [0, 64]");
+    auto it = ctx->gk_tables.find(alpha);
+    if (it != ctx->gk_tables.end()) {
+        *out = it->second;
+        return LGF_OK;
+    }
+    const int R = ctx->table_radius;
+    const int npanel = std::max(1, (int)std::ceil(alpha / 0.5));
+    std::vector<double> edge(npanel + 1);
+    for (int p = 0; p <= npanel; ++p) edge[p] = alpha * p / npanel;
+    const int nnodes = npanel * kGL;
+    const int64_t n = (int64_t)(R + 1) * (R + 2) * (R + 3) / 6;
+    const std::vector<int> abc = sorted_offsets(R);
+    double *glx = nullptr, *glw = nullptr, *dedge = nullptr, *t = nullptr, *wt = nullptr, *B = nullptr;
+    double *table = nullptr;
+    int *dabc = nullptr;
+    unsigned long long *shell = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(glx); cudaFree(glw); cudaFree(dedge); cudaFree(t); cudaFree(wt); cudaFree(B);
+        cudaFree(dabc); cudaFree(shell);
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&glx, kGL * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&glw, kGL * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&dedge, edge.size() * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&t, nnodes * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&wt, nnodes * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&B, (size_t)nnodes * (R + 1) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&dabc, abc.size() * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&shell, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&table, n * sizeof(double))) != cudaSuccess) {
+        cleanup();
+        cudaFree(table);
+        return fail(ctx, LGF_ENOMEM, std::string("G_K table: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    cudaMemcpyAsync(dedge, edge.data(), edge.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dabc, abc.data(), abc.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(shell, 0, sizeof(unsigned long long), s);
+    k_gauss_legendre<<<1, kGL, 0, s>>>(kGL, glx, glw);
+    k_nodes<<<(nnodes + 127) / 128, 128, 0, s>>>(dedge, npanel, glx, glw, t, wt);
+    k_bessel_nodes<<<(nnodes + 63) / 64, 64, 0, s>>>(t, nnodes, R, B);
+    k_rtable<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(dabc, n, B, wt, nnodes, R, ctx->table_dev, table, shell);
+    unsigned long long sh = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sh, shell, sizeof(sh), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) {
+        cudaFree(table);
+        return cuda_fail(ctx, e, "G_K table");
+    }
+    double shell_r;
+    memcpy(&shell_r, &sh, sizeof(shell_r));
+    // |G_L(0)| = 0.2527...: R(alpha) past the table must be negligible
+    if (!(shell_r <= 1e-15 * 0.25)) {
+        cudaFree(table);
+        char msg[160];
+        snprintf(msg, sizeof msg, "G_K: R(alpha=%g) is %.3g on the table's outer shell; build a larger table", alpha,
+                 shell_r);
+        return fail(ctx, LGF_EUNSUPPORTED, msg);
+    }
+    ctx->gk_tables[alpha] = table;
+    *out = table;
+    return LGF_OK;
+}
+
+lgf_status table_lookup(lgf_ctx *ctx, const double *table, const int32_t *off, int64_t n, double *out,
+                        cudaStream_t s)
 {
     if (n == 0) return LGF_OK;
-    k_lookup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->table_dev, ctx->table_radius, off, n, out);
+    k_lookup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(table, ctx->table_radius, off, n, out);
     LGF_CHECK_LAUNCH(ctx, "lookup kernel");
     return LGF_OK;
 }
 
-lgf_status kernel_window(lgf_ctx *ctx, const int M[3], double *box, cudaStream_t s)
+lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], double *box, cudaStream_t s)
 {
-    k_window<<<152 * 8, 256, 0, s>>>(ctx->table_dev, ctx->table_radius, M[0], M[1], M[2], box);
+    k_window<<<152 * 8, 256, 0, s>>>(table, ctx->table_radius, M[0], M[1], M[2], box);
     LGF_CHECK_LAUNCH(ctx, "window kernel");
     return LGF_OK;
 }
