@@ -17,6 +17,10 @@ it follows; the C source documents the numerical method):
   lgf_r              R(alpha)(n) = int_0^alpha G_E(t)(n) dt      App. A (partition of G_K)
   gk_quad, gk_table  G_K(alpha) = G_L + R(alpha)                 App. A, Eq. lgf_iflap
   kinv_direct        u = dx^2 sum_m G_K(alpha)(n-m) f(m)         Sec. 2.2 (action of K^{-1})
+  curl_box           C: faces -> edges (staggered curl)          Sec. 2.1 (operator list)
+  curl_adj_box       C^dagger: edges -> faces (adjoint of C)     Sec. 2.1
+  grad_box, div_box  G: cells -> faces, Dbar = -G^dagger          Sec. 2.1 (pins only)
+  velocity_refresh   w = C u, s = L^{-1} w, u = -C^dagger s      Sec. 4.1, Eq. vel_refresh
 """
 from __future__ import annotations
 
@@ -264,3 +268,110 @@ def kinv_direct(alpha: float, b: int, src_coords, f, tgt_pts, dx: float = 1.0, R
     if rc != 0:
         raise RuntimeError(f"orc_poisson_direct failed ({rc})")
     return out
+
+
+# ----------------------------------------------------------------------------
+# Staggered-grid operators (Sec. 2.1) on dense boxes [3][z][y][x], zero outside.
+# Cell n of the lattice holds face k at (n + (1 - e_k)/2) dx and edge k at
+# (n + e_k/2) dx; a vector field stores component k of cell n at [k][z][y][x].
+# The paper lists C: faces -> edges and its adjoint C^dagger but prints no
+# stencil; these are the standard second-order finite-volume (MAC) ones, and
+# the tests pin them to the paper's mimetic identity L_F = -G G^dagger - C^dagger C.
+# ----------------------------------------------------------------------------
+_AX = {0: 2, 1: 1, 2: 0}   # lattice axis k -> array axis of [z][y][x]
+
+
+def _shift(a: np.ndarray, k: int, d: int) -> np.ndarray:
+    """b(n) = a(n + d e_k) on the same box (the last three array axes are z, y, x),
+    zero where n + d e_k leaves it."""
+    out = np.zeros_like(a)
+    ax = a.ndim - 3 + _AX[k]
+    n = a.shape[ax]
+    src = [slice(None)] * a.ndim
+    dst = [slice(None)] * a.ndim
+    if d > 0:
+        src[ax], dst[ax] = slice(d, n), slice(0, n - d)
+    else:
+        src[ax], dst[ax] = slice(0, n + d), slice(-d, n)
+    out[tuple(dst)] = a[tuple(src)]
+    return out
+
+
+_EPS = ((0, 1, 2), (1, 2, 0), (2, 0, 1))   # (k, i, j) with eps_kij = +1
+
+
+def curl_box(u: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """(C u)_k(n) = [u_j(n) - u_j(n - e_i)] - [u_i(n) - u_i(n - e_j)] / dx, (k,i,j) cyclic:
+    the circulation of the face velocities around edge k (backward differences)."""
+    w = np.empty_like(u)
+    for k, i, j in _EPS:
+        w[k] = ((u[j] - _shift(u[j], i, -1)) - (u[i] - _shift(u[i], j, -1))) / dx
+    return w
+
+
+def curl_adj_box(w: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """(C^dagger w)_k(m) = [w_i(m) - w_i(m + e_j)] - [w_j(m) - w_j(m + e_i)] / dx: the adjoint
+    of curl_box under sum_n a(n) b(n) (forward differences)."""
+    u = np.empty_like(w)
+    for k, i, j in _EPS:
+        u[k] = ((w[i] - _shift(w[i], j, +1)) - (w[j] - _shift(w[j], i, +1))) / dx
+    return u
+
+
+def grad_box(q: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """(G q)_k(n) = [q(n) - q(n - e_k)] / dx: cells -> faces."""
+    return np.stack([(q - _shift(q, k, -1)) / dx for k in range(3)])
+
+
+def div_box(u: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """(Dbar u)(n) = sum_k [u_k(n + e_k) - u_k(n)] / dx = -(G^dagger u)(n): faces -> cells."""
+    return sum((_shift(u[k], k, +1) - u[k]) / dx for k in range(3))
+
+
+def lap_box(a: np.ndarray, dx: float = 1.0) -> np.ndarray:
+    """7-point Laplacian of each component (the scalar L of Sec. 2.2 applied componentwise)."""
+    out = -6.0 * a
+    for k in range(3):
+        out = out + _shift(a, k, 1) + _shift(a, k, -1)
+    return out / dx ** 2
+
+
+def _vec_to_box(b: int, coords, v, lo, shape):
+    v = np.asarray(v, dtype=np.float64).reshape(3, -1)
+    return np.stack([blocks_to_box(b, coords, v[k], lo, shape)[0] for k in range(3)])
+
+
+def _vec_from_box(b: int, coords, box, lo):
+    return np.stack([box_to_blocks(b, coords, box[k], lo) for k in range(3)])
+
+
+def grown_forward(coords) -> np.ndarray:
+    """The block set with every block's +x, +y and +z neighbours added (sorted)."""
+    c = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
+    out = {tuple(r) for r in c}
+    for e in np.eye(3, dtype=np.int64):
+        out |= {tuple(r) for r in c + e}
+    return np.array(sorted(out), dtype=np.int32)
+
+
+def velocity_refresh(b: int, src_coords, u, tgt_coords, dx: float = 1.0, R: int = 64) -> np.ndarray:
+    """Velocity refresh of Eq. vel_refresh on block sets: w = C u on the source blocks
+    (u zero outside them), s = L^{-1} w = dx^2 G_L * w (each edge component a scalar
+    convolution) on the target blocks and their forward neighbours, u_new = -C^dagger s
+    on the target blocks.  The minus sign is the reading of the printed composition that
+    returns a divergence-free u unchanged (with L_F = -G G^dagger - C^dagger C, Sec. 2.1).
+    u: [3][nsrc][b^3]; returns [3][ntgt][b^3]."""
+    src = np.asarray(src_coords, dtype=np.int64).reshape(-1, 3)
+    tgt = np.asarray(tgt_coords, dtype=np.int64).reshape(-1, 3)
+    tg = grown_forward(tgt).astype(np.int64)
+    allc = np.concatenate([src, tg])
+    lo = allc.min(axis=0)
+    hi = allc.max(axis=0) + 1
+    shape = tuple(int(v) for v in ((hi - lo) * b)[::-1])
+    ubox = _vec_to_box(b, src, u, lo, shape)
+    w = _vec_from_box(b, src, curl_box(ubox, dx), lo)           # C u, kept on the source blocks
+    pts = block_points(b, tg)
+    s = np.stack([poisson_direct(b, src, w[k], pts, dx=dx, R=R).reshape(tg.shape[0], b ** 3)
+                  for k in range(3)])
+    sbox = _vec_to_box(b, tg, s, lo, shape)
+    return -_vec_from_box(b, tgt, curl_adj_box(sbox, dx), lo)

@@ -361,3 +361,67 @@ def test_gk_table_and_direct_apply(oracle):
     got = oracle.kinv_direct(alpha, b, [[0, 0, 0]], f, tp, dx=1.0, R=R)
     ref = [oracle.gk_quad(alpha, *t) for t in tp]
     assert np.allclose(got, ref, rtol=0, atol=1e-16)
+
+
+# ------------------------------------------------- staggered curl and refresh
+def _rand_field(rng, shape, margin, integer=True):
+    a = rng.integers(-5, 6, size=shape).astype(np.float64) if integer else rng.uniform(-1, 1, size=shape)
+    m = margin
+    mask = np.zeros(shape[-3:], dtype=bool)
+    mask[m:-m, m:-m, m:-m] = True
+    return a * mask
+
+
+def test_curl_adjoint_pair(oracle):
+    """<C u, w> = <u, C^dagger w> for fields vanishing near the box boundary."""
+    rng = np.random.default_rng(1)
+    u = _rand_field(rng, (3, 9, 10, 11), 2, integer=False)
+    w = _rand_field(rng, (3, 9, 10, 11), 2, integer=False)
+    lhs = float(np.sum(oracle.curl_box(u, 0.7) * w))
+    rhs = float(np.sum(u * oracle.curl_adj_box(w, 0.7)))
+    assert abs(lhs - rhs) < 1e-12 * (abs(lhs) + 1.0)
+
+
+def test_mimetic_identity_of_section_2_1(oracle):
+    """L_F = -G G^dagger - C^dagger C with G^dagger = -Dbar (Sec. 2.1): on integer
+    fields the identity C^dagger C u - G Dbar u = -L u holds exactly, which fixes
+    the stencils of C and C^dagger against the 7-point Laplacian."""
+    rng = np.random.default_rng(2)
+    u = _rand_field(rng, (3, 8, 9, 10), 2)
+    lhs = oracle.curl_adj_box(oracle.curl_box(u)) - oracle.grad_box(oracle.div_box(u))
+    assert np.array_equal(lhs, -oracle.lap_box(u))
+
+
+def test_curl_orthogonality(oracle):
+    """Im(G) = Null(C) and Dbar C^dagger = 0 (Sec. 2.1), exactly on integers."""
+    rng = np.random.default_rng(3)
+    q = _rand_field(rng, (8, 8, 8), 2)
+    assert np.array_equal(oracle.curl_box(oracle.grad_box(q)), np.zeros((3, 8, 8, 8)))
+    w = _rand_field(rng, (3, 8, 8, 8), 2)
+    assert np.array_equal(oracle.div_box(oracle.curl_adj_box(w)), np.zeros((8, 8, 8)))
+
+
+def test_velocity_refresh_returns_divergence_free_field(oracle):
+    """For u = C^dagger psi (divergence free) whose vorticity stays inside the
+    source blocks, the refresh returns u on any target set: this fixes the sign
+    of the composition of Eq. vel_refresh (u <- -C^dagger L^{-1} C u)."""
+    b = 8
+    src = np.array([[0, 0, 0], [1, 0, 0]], dtype=np.int32)
+    rng = np.random.default_rng(4)
+    psi = np.zeros((3, b, b, 2 * b))
+    psi[:, 3:5, 3:5, 3:13] = rng.uniform(-1, 1, size=(3, 2, 2, 10))
+    ubox = oracle.curl_adj_box(psi)
+    assert np.max(np.abs(oracle.div_box(ubox))) < 1e-14
+    u = np.stack([oracle.box_to_blocks(b, src, ubox[k], np.zeros(3, dtype=np.int64)) for k in range(3)])
+    tgt = np.array([[1, 0, 0], [0, 1, 0], [-1, 0, 0]], dtype=np.int32)
+    got = oracle.velocity_refresh(b, src, u, tgt, dx=1.0, R=32)
+    lo = np.array([-1, 0, 0])
+    big, _ = None, None
+    ref = np.zeros_like(got)
+    for k in range(3):
+        box, _ = oracle.blocks_to_box(b, src, u[k], lo, (b, 2 * b, 3 * b))
+        ref[k] = oracle.box_to_blocks(b, tgt, box, lo)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(u))
+    # the refresh does not depend on dx (C, L^{-1} and C^dagger scale as 1/dx, dx^2, 1/dx)
+    got2 = oracle.velocity_refresh(b, src, u, tgt, dx=0.5, R=32)
+    assert np.allclose(got2, got, rtol=0, atol=1e-13)
