@@ -211,6 +211,39 @@ typedef struct {
    bit for bit.  Errors: as the single applies. */
 LGF_API lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob, void *stream);
 
+/* Staggered-grid curl C: faces -> edges (Sec. 2.1, operator list).  Cell n
+   holds face k at (n + (1 - e_k)/2) dx and edge k at (n + e_k/2) dx; with
+   (k, i, j) cyclic,
+     w_k(n) = ([u_j(n) - u_j(n - e_i)] - [u_i(n) - u_i(n - e_j)]) / dx
+   at every cell of `tgt`, u read on `src` and zero elsewhere.  u_dev:
+   [nrhs][3][src.nblocks][b^3], w_dev: [nrhs][3][tgt.nblocks][b^3], context
+   precision, component k of cell n in the cell's slot.  The paper lists C but
+   prints no stencil: this is the second-order finite-volume one, which
+   satisfies the mimetic identity L_F = -G G^dagger - C^dagger C of Sec. 2.1.
+   Errors: LGF_EINVAL (b mismatch, null pointers, dx <= 0), LGF_ENOMEM,
+   LGF_ECUDA. */
+LGF_API lgf_status lgf_curl(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, const void *u_dev,
+                            void *w_dev, int32_t nrhs, double dx, void *stream);
+
+/* Adjoint curl C^dagger: edges -> faces, the transpose of lgf_curl under the
+   sum over cells:
+     u_k(n) = -([w_j(n) - w_j(n + e_i)] - [w_i(n) - w_i(n + e_j)]) / dx.
+   Same layouts and errors as lgf_curl (w on `src`, u on `tgt`). */
+LGF_API lgf_status lgf_curl_adjoint(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt,
+                                    const void *w_dev, void *u_dev, int32_t nrhs, double dx, void *stream);
+
+/* Velocity refresh (Sec. 4.1, Eq. vel_refresh): w = C u on the source blocks,
+   s = L^{-1} w = dx^2 G_L * w (each edge component a scalar convolution, the
+   exact box convolution of lgf_poisson_apply) on the target blocks and their
+   +x, +y, +z neighbours, and u_out = -C^dagger s on the target blocks.  The
+   printed composition C^dagger L^{-1} C returns -u for a divergence-free u
+   under the paper's L_F = -G G^dagger - C^dagger C; the minus sign is the
+   reading that refreshes u.  u_dev: [nrhs][3][src.nblocks][b^3] (zero
+   outside the source blocks); u_out_dev: [nrhs][3][tgt.nblocks][b^3].  The
+   result does not depend on dx.  Errors: as lgf_poisson_apply and lgf_curl. */
+LGF_API lgf_status lgf_velocity_refresh(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt,
+                                        const void *u_dev, void *u_out_dev, int32_t nrhs, double dx, void *stream);
+
 /* FP64 residual check of the discrete Poisson problem (Sec. 2.2, Eq. dpoisson):
      r = (L_h u)(n) - f(n),  L_h u = (sum_{+-e_i} u(n +- e) - 6 u(n)) / dx^2,
    at every point of `set` whose six neighbours are in `set`; r = 0 elsewhere.

@@ -22,7 +22,8 @@ LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR, LGF_OP_KINV = 0
 
 # Every symbol include/lgf.h declares (checked by the symbol test).
 EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
-           "lgf_kinv_lookup", "lgf_poisson_apply", "lgf_kinv_apply", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
+           "lgf_kinv_lookup", "lgf_poisson_apply", "lgf_kinv_apply", "lgf_curl", "lgf_curl_adjoint",
+           "lgf_velocity_refresh", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
            "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_intfactor_apply_noalloc",
            "lgf_status_string", "lgf_last_error", "lgf_version")
 
@@ -75,6 +76,9 @@ def load(path: str = LIB_PATH):
         "lgf_poisson_apply": [vp, bsp, bsp, vp, vp, i32, i32, dbl, vp],
         "lgf_kinv_lookup": [vp, dbl, vp, i64, vp, vp],
         "lgf_kinv_apply": [vp, dbl, bsp, bsp, vp, vp, i32, i32, dbl, vp],
+        "lgf_curl": [vp, bsp, bsp, vp, vp, i32, dbl, vp],
+        "lgf_curl_adjoint": [vp, bsp, bsp, vp, vp, i32, dbl, vp],
+        "lgf_velocity_refresh": [vp, bsp, bsp, vp, vp, i32, dbl, vp],
         "lgf_intfactor_apply": [vp, dbl, bsp, bsp, vp, vp, i32, i32, vp],
         "lgf_intfactor_weights": [vp, dbl, vp, i32, ctypes.POINTER(i32), vp],
         "lgf_batch_apply": [vp, ctypes.POINTER(lgf_problem), i32, vp],
@@ -201,6 +205,29 @@ class Context:
                                            _ptr(u), ncomp, nrhs, float(dx), _stream_ptr(stream)), "lgf_kinv_apply")
         return u
 
+    def _vector_op(self, name: str, b: int, src, tgt, a, out, nrhs: int, dx: float, stream):
+        s, sa = _blockset(b, src)
+        t, ta = _blockset(b, tgt)
+        if s.nblocks and t.nblocks:
+            self._field(a, s.nblocks, b, 3 * nrhs, "input")
+        if t.nblocks:
+            self._field(out, t.nblocks, b, 3 * nrhs, "output")
+        self._check(getattr(self._L, name)(self._h, ctypes.byref(s), ctypes.byref(t), _ptr(a), _ptr(out), int(nrhs),
+                                           float(dx), _stream_ptr(stream)), name)
+        return out
+
+    def curl(self, b: int, src, tgt, u, w, nrhs: int = 1, dx: float = 1.0, stream=None):
+        """w = C u (faces -> edges), [nrhs][3][nblocks][b^3] fields."""
+        return self._vector_op("lgf_curl", b, src, tgt, u, w, nrhs, dx, stream)
+
+    def curl_adjoint(self, b: int, src, tgt, w, u, nrhs: int = 1, dx: float = 1.0, stream=None):
+        """u = C^dagger w (edges -> faces)."""
+        return self._vector_op("lgf_curl_adjoint", b, src, tgt, w, u, nrhs, dx, stream)
+
+    def velocity_refresh(self, b: int, src, tgt, u, u_out, nrhs: int = 1, dx: float = 1.0, stream=None):
+        """u_out = -C^dagger L^{-1} C u (Eq. vel_refresh)."""
+        return self._vector_op("lgf_velocity_refresh", b, src, tgt, u, u_out, nrhs, dx, stream)
+
     def poisson_apply(self, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1, dx: float = 1.0, stream=None):
         s, sa = _blockset(b, src)
         t, ta = _blockset(b, tgt)
@@ -309,6 +336,18 @@ def lgf_poisson_apply(ctx: Context, *a, **kw):
 
 def lgf_kinv_apply(ctx: Context, *a, **kw):
     return ctx.kinv_apply(*a, **kw)
+
+
+def lgf_curl(ctx: Context, *a, **kw):
+    return ctx.curl(*a, **kw)
+
+
+def lgf_curl_adjoint(ctx: Context, *a, **kw):
+    return ctx.curl_adjoint(*a, **kw)
+
+
+def lgf_velocity_refresh(ctx: Context, *a, **kw):
+    return ctx.velocity_refresh(*a, **kw)
 
 
 def lgf_intfactor_apply(ctx: Context, *a, **kw):

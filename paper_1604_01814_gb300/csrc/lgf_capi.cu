@@ -220,6 +220,7 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
     ctx->graphs.clear();
     ctx->pplans.clear();
     ctx->iplans.clear();
+    ctx->cplans.clear();
     for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
     for (auto &kv : ctx->gk_tables) cudaFree(kv.second);
     for (auto &kv : ctx->tw32) cudaFree(kv.second);
@@ -234,6 +235,8 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
         cudaFree(sc.B);
         cudaFree(sc.C);
         cudaFree(sc.D);
+        cudaFree(sc.E);
+        cudaFree(sc.F);
     }
     for (int b = 0; b < kBranches; ++b) {
         if (ctx->br[b]) cudaStreamDestroy(ctx->br[b]);
@@ -340,6 +343,77 @@ lgf_status lgf_kinv_apply(lgf_ctx *ctx, double alpha, const lgf_blockset *src, c
                           const void *f_dev, void *u_dev, int32_t ncomp, int32_t nrhs, double dx, void *stream)
 {
     return kernel_apply(ctx, alpha, src, tgt, f_dev, u_dev, ncomp, nrhs, dx, stream);
+}
+
+}  // extern "C"
+
+namespace {
+lgf_status curl_apply(lgf_ctx *ctx, int dir, const lgf_blockset *src, const lgf_blockset *tgt, const void *in_dev,
+                      void *out_dev, int32_t nrhs, double dx, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if ((st = check_blockset(ctx, src, "source")) != LGF_OK) return st;
+    if ((st = check_blockset(ctx, tgt, "target")) != LGF_OK) return st;
+    if (src->b != tgt->b) return fail(ctx, LGF_EINVAL, "source and target block edges differ");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(ctx, LGF_EINVAL, "dx must be positive and finite");
+    if ((st = check_fields(ctx, in_dev, out_dev, 3, nrhs, src->nblocks, tgt->nblocks)) != LGF_OK) return st;
+    if (tgt->nblocks == 0) return LGF_OK;
+    CurlPlan *pl = nullptr;
+    if ((st = curl_plan(ctx, src, tgt, dir, &pl)) != LGF_OK) return st;
+    return curl_run(ctx, pl, in_dev, out_dev, nrhs, dir < 0 ? 1.0 / dx : -1.0 / dx, (cudaStream_t)stream);
+}
+}  // namespace
+
+extern "C" {
+
+lgf_status lgf_curl(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, const void *u_dev, void *w_dev,
+                    int32_t nrhs, double dx, void *stream)
+{
+    return curl_apply(ctx, -1, src, tgt, u_dev, w_dev, nrhs, dx, stream);
+}
+
+lgf_status lgf_curl_adjoint(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, const void *w_dev,
+                            void *u_dev, int32_t nrhs, double dx, void *stream)
+{
+    return curl_apply(ctx, 1, src, tgt, w_dev, u_dev, nrhs, dx, stream);
+}
+
+lgf_status lgf_velocity_refresh(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, const void *u_dev,
+                                void *u_out_dev, int32_t nrhs, double dx, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if ((st = check_blockset(ctx, src, "source")) != LGF_OK) return st;
+    if ((st = check_blockset(ctx, tgt, "target")) != LGF_OK) return st;
+    if (src->b != tgt->b) return fail(ctx, LGF_EINVAL, "source and target block edges differ");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(ctx, LGF_EINVAL, "dx must be positive and finite");
+    if ((st = check_fields(ctx, u_dev, u_out_dev, 3, nrhs, src->nblocks, tgt->nblocks)) != LGF_OK) return st;
+    if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "lgf_table_build has not been called");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int b = src->b;
+    const size_t b3 = (size_t)b * b * b;
+    if (tgt->nblocks == 0) return LGF_OK;
+    if (src->nblocks == 0) {
+        LGF_CUDA(ctx, cudaMemsetAsync(u_out_dev, 0, (size_t)tgt->nblocks * b3 * 3 * nrhs * elem_size(ctx), s));
+        return LGF_OK;
+    }
+    const std::vector<int32_t> grown = grown_forward(tgt);
+    const lgf_blockset tp{b, (int32_t)(grown.size() / 3), grown.data()};
+    CurlPlan *pc = nullptr, *pa = nullptr;
+    if ((st = curl_plan(ctx, src, src, -1, &pc)) != LGF_OK) return st;
+    if ((st = curl_plan(ctx, &tp, tgt, 1, &pa)) != LGF_OK) return st;
+    PreparedPoisson pp;
+    if ((st = prepare_poisson(ctx, src, &tp, 3 * nrhs, 0.0, s, &pp)) != LGF_OK) return st;
+    Scratch &sc = ctx->scr[0];
+    const size_t esz = elem_size(ctx);
+    if ((st = ensure_scratch(ctx, &sc.E, &sc.e, (size_t)nrhs * 3 * src->nblocks * b3 * esz)) != LGF_OK) return st;
+    if ((st = ensure_scratch(ctx, &sc.F, &sc.f, (size_t)nrhs * 3 * tp.nblocks * b3 * esz)) != LGF_OK) return st;
+    // w = C u on the source blocks; s = dx^2 G_L * w on the grown targets;
+    // u = -C^dagger s on the targets
+    if ((st = curl_run(ctx, pc, u_dev, sc.E, nrhs, 1.0 / dx, s)) != LGF_OK) return st;
+    if ((st = poisson_run(ctx, pp.plan, pp.spec, sc.E, sc.F, 3 * nrhs, dx, s)) != LGF_OK) return st;
+    return curl_run(ctx, pa, sc.F, u_out_dev, nrhs, 1.0 / dx, s);
 }
 
 lgf_status lgf_intfactor_weights(lgf_ctx *ctx, double alpha, double *w_dev, int32_t cap, int32_t *radius,

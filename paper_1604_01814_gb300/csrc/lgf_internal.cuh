@@ -89,6 +89,17 @@ struct Spectrum {
 struct Scratch {
     void *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr;
     size_t a = 0, b = 0, c = 0, d = 0;
+    void *E = nullptr, *F = nullptr;   // velocity refresh: vorticity and its potential
+    size_t e = 0, f = 0;
+};
+
+// Curl stencil plan: for every target block, the source blocks at the block
+// itself and at +dir along x, y, z (-1 where absent).
+struct CurlPlan {
+    int b = 0, dir = 0;
+    std::vector<int32_t> src, tgt;
+    int *nbr_dev = nullptr;   // [ntgt][4]
+    ~CurlPlan();
 };
 constexpr int kBranches = 4;   // concurrent branches of a batch
 
@@ -118,6 +129,7 @@ struct lgf_ctx {
     std::vector<std::unique_ptr<lgf::PoissonPlan>> pplans;
     std::vector<std::unique_ptr<lgf::IntfPlan>> iplans;
     std::vector<std::unique_ptr<lgf::IntfWeights>> weights;
+    std::vector<std::unique_ptr<lgf::CurlPlan>> cplans;
 
     // grow-only scratch, one set per concurrent branch of lgf_batch_apply
     // (branch 0 also serves the single applies); `cur` is the set the next
@@ -207,6 +219,12 @@ struct IntfJob {
 lgf_status intf_run_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, int njobs, int nfields, cudaStream_t s);
 lgf_status intf_run(lgf_ctx *ctx, IntfPlan *pl, const IntfWeights *w, const void *f, void *u, int nfields,
                     cudaStream_t s);
+
+// Curl and velocity refresh (lgf_curl.cu)
+lgf_status curl_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, int dir, CurlPlan **out);
+lgf_status curl_run(lgf_ctx *ctx, const CurlPlan *pl, const void *in, void *out, int nrhs, double scale,
+                    cudaStream_t s);
+std::vector<int32_t> grown_forward(const lgf_blockset *tgt);
 
 // Residual (lgf_residual.cu)
 lgf_status residual_run(lgf_ctx *ctx, const lgf_blockset *set, const void *u, const void *f, double dx,
