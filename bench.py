@@ -491,6 +491,9 @@ EXTRA = {
                "RK right-hand sides (12 fields), FP32; one G_L apply of all fields per step",
     "plates64": "64 flat-plate problems, 16^3 blocks, N_b log-uniform in [8, 1200], 3 components, FP32; "
                 "one lgf_batch_apply of G_L then E(0.25) for every problem per step",
+    "refresh_sphere": "velocity refresh u <- -C^dagger L^{-1} C u (Eq. vel_refresh) on the sphere-plus-wake "
+                      "active set (16^3 blocks), u = curl of a Gaussian-blob vector potential, FP32; one refresh "
+                      "per step",
     "kinv_sphere": "K(0.25)^{-1} on the surface blocks of the icosphere (5120 markers, radius 20 cells, 16^3 "
                    "blocks, source = target = the blocks the 3-point delta touches), 3 components, FP32; one "
                    "G_K(0.25) apply per step",
@@ -498,15 +501,17 @@ EXTRA = {
 
 
 def run_extra(args, rank, world, dist):
-    """The larger paper-shaped workloads (working sets far above L2): their own
-    JSON line with throughput and per-kernel algorithmic GB/s.  Not the bench
-    line: the bench workload is the dense 128^3 box."""
+    """The larger paper-shaped workloads (working sets far above L2) and the
+    rows beyond the Poisson/integrating-factor path: their own JSON line with
+    throughput and per-kernel algorithmic GB/s.  Not the bench line: the bench
+    workload is the dense 128^3 box."""
     import torch
     import lgf_inputs as li
     import paper_1604_01814_gb300 as lgf
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    probs = []
     if args.workload == "wake512":
         probs = [(li.wake_domain(), lgf.LGF_OP_POISSON, 0.0)]
     elif args.workload == "plates64":
@@ -515,25 +520,50 @@ def run_extra(args, rank, world, dist):
         q = li.sphere_ib()
         q = li.Problem("sphere_surface", q.b, q.src, q.src.copy(), q.f, alphas=(0.25,))
         probs = [(q, lgf.LGF_OP_KINV, 0.25)]
-    else:
+    elif args.workload != "refresh_sphere":
         raise ValueError(f"unknown workload {args.workload}")
     ctx = lgf.Context("f32", device=dev.index)
     ctx.table_build(48)
     batch, points = [], 0.0
     alg_step = {}
-    for p, op, a in probs:
-        nf = p.nrhs * p.ncomp
-        f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device=dev)
-        u = torch.empty(nf * p.tgt.shape[0] * p.b ** 3, dtype=torch.float32, device=dev)
-        batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, nrhs=p.nrhs, op=op, alpha=a))
-        points += float(u.numel())
-        n_intf = 1 if op in (lgf.LGF_OP_INTFACTOR, lgf.LGF_OP_POISSON_THEN_INTFACTOR) else 0
-        for k, v in algorithmic_bytes_per_step(p, nf, n_intf).items():
-            alg_step[k] = alg_step.get(k, 0) + v
     s = torch.cuda.Stream(device=dev)
+    if args.workload == "refresh_sphere":
+        q = li.sphere_ib()
+        cells = q.tgt
+        u = li.curl_blob_field(q.b, cells, centres=np.array([[-30.0, 0.0, 0.0], [40.0, 10.0, -5.0]]),
+                               amps=np.array([[0.0, 0.0, 1.0], [0.5, -1.0, 0.0]]), sigma=8.0)
+        ut = torch.tensor(u.reshape(-1), dtype=torch.float32, device=dev)
+        uo = torch.empty_like(ut)
+        ncell = cells.shape[0] * q.b ** 3
+        points = float(3 * ncell)
+        # the Poisson part maps the cells to the cells and their +x, +y, +z neighbour blocks
+        grown = set(map(tuple, cells.tolist()))
+        for e in np.eye(3, dtype=np.int64):
+            grown |= set(map(tuple, (cells + e).tolist()))
+        grown = np.array(sorted(grown), dtype=np.int32)
+        pg = li.Problem("refresh", q.b, cells, grown, np.zeros((1, 3, cells.shape[0], 1)))
+        alg_step = algorithmic_bytes_per_step(pg, 3, 0)
+        alg_step["curl"] = 2 * 3 * 4 * ncell
+        alg_step["curl_adjoint"] = 2 * 3 * 4 * ncell
+
+        def step():
+            ctx.velocity_refresh(q.b, cells, cells, ut, uo, stream=s)
+    else:
+        for p, op, a in probs:
+            nf = p.nrhs * p.ncomp
+            f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device=dev)
+            u = torch.empty(nf * p.tgt.shape[0] * p.b ** 3, dtype=torch.float32, device=dev)
+            batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, nrhs=p.nrhs, op=op, alpha=a))
+            points += float(u.numel())
+            n_intf = 1 if op in (lgf.LGF_OP_INTFACTOR, lgf.LGF_OP_POISSON_THEN_INTFACTOR) else 0
+            for k, v in algorithmic_bytes_per_step(p, nf, n_intf).items():
+                alg_step[k] = alg_step.get(k, 0) + v
+
+        def step():
+            ctx.batch_apply(batch, stream=s)
     with torch.cuda.stream(s):
         for _ in range(max(3, args.warmup)):
-            ctx.batch_apply(batch, stream=s)
+            step()
     s.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
@@ -544,7 +574,7 @@ def run_extra(args, rank, world, dist):
     with torch.cuda.stream(s):
         for a, b in evs:
             a.record(s)
-            ctx.batch_apply(batch, stream=s)
+            step()
             b.record(s)
     s.synchronize()
     clocks = clk.stop()
@@ -552,7 +582,7 @@ def run_extra(args, rank, world, dist):
     ctx.profile_enable(True)
     with torch.cuda.stream(s):
         for _ in range(args.steps):
-            ctx.batch_apply(batch, stream=s)
+            step()
     stats = ctx.profile_read()
     ctx.profile_enable(False)
     tot = sum(t for _, t in stats.values())
