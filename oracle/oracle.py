@@ -21,10 +21,14 @@ it follows; the C source documents the numerical method):
   curl_adj_box       C^dagger: edges -> faces (adjoint of C)     Sec. 2.1
   grad_box, div_box  G: cells -> faces, Dbar = -G^dagger          Sec. 2.1 (pins only)
   velocity_refresh   w = C u, s = L^{-1} w, u = -C^dagger s      Sec. 4.1, Eq. vel_refresh
+  phi3               three-point kernel phi(r) (reading: Roma-Peskin-Berger)  Sec. 2.1
+  ib_spread          (R g)^k(n) = sum_i g^k(i) delta_dx(x_F^k(n) - X_i)       Sec. 2.1 (operator R)
+  ib_interp          (I v)^k(i) = dx^3 sum_n v^k(n) delta_dx(x_F^k(n) - X_i)  Sec. 2.1 (operator I)
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -375,3 +379,77 @@ def velocity_refresh(b: int, src_coords, u, tgt_coords, dx: float = 1.0, R: int 
                   for k in range(3)])
     sbox = _vec_to_box(b, tg, s, lo, shape)
     return -_vec_from_box(b, tgt, curl_adj_box(sbox, dx), lo)
+
+
+# ----------------------------------------------------------------------------
+# Immersed-boundary regularisation R and interpolation I (Sec. 2.1): face k of
+# cell n sits at x_F^k(n) = (n + (1 - e_k)/2) dx; delta_h(x) = h^-3 prod_d
+# phi(x_d / h).  Marker positions X are given in units of dx.  Plain loops over
+# markers and the 4 x 4 x 4 lattice points around each (phi vanishes beyond
+# |r| = 3/2, so the extra ring only adds zeros).
+# ----------------------------------------------------------------------------
+def phi3(r):
+    """phi(r) = (1 + sqrt(1 - 3 r^2)) / 3 for |r| <= 1/2,
+    (5 - 3|r| - sqrt(1 - 3 (1 - |r|)^2)) / 6 for 1/2 <= |r| <= 3/2, 0 beyond."""
+    a = abs(float(r))
+    if a <= 0.5:
+        return (1.0 + math.sqrt(1.0 - 3.0 * a * a)) / 3.0
+    if a <= 1.5:
+        return (5.0 - 3.0 * a - math.sqrt(max(0.0, 1.0 - 3.0 * (1.0 - a) ** 2))) / 6.0
+    return 0.0
+
+
+def _block_lookup(b: int, coords):
+    c = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
+    return {tuple(v): i for i, v in enumerate(c.tolist())}
+
+
+def _ib_points(X, k):
+    """Lattice cells n whose face k may lie within 3/2 of X (per axis), with weights."""
+    o = [0.5, 0.5, 0.5]
+    o[k] = 0.0
+    base = [int(math.floor(X[d] - o[d])) - 1 for d in range(3)]
+    for dz in range(4):
+        for dy in range(4):
+            for dx_ in range(4):
+                n = (base[0] + dx_, base[1] + dy, base[2] + dz)
+                w = phi3(n[0] + o[0] - X[0]) * phi3(n[1] + o[1] - X[1]) * phi3(n[2] + o[2] - X[2])
+                if w != 0.0:
+                    yield n, w
+
+
+def ib_spread(b: int, coords, X, g, dx: float = 1.0) -> np.ndarray:
+    """f = R g on the face lattices of the blocks: g [nrhs][3][nm] -> [nrhs][3][nblk][b^3].
+    Points outside the block set are dropped."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
+    g = np.asarray(g, dtype=np.float64).reshape(-1, 3, X.shape[0])
+    lut = _block_lookup(b, coords)
+    out = np.zeros((g.shape[0], 3, len(lut), b ** 3))
+    for i in range(X.shape[0]):
+        for k in range(3):
+            for n, w in _ib_points(X[i], k):
+                blk = lut.get((n[0] // b, n[1] // b, n[2] // b))
+                if blk is None:
+                    continue
+                loc = ((n[2] % b) * b + n[1] % b) * b + n[0] % b
+                out[:, k, blk, loc] += w * g[:, k, i] / dx ** 3
+    return out
+
+
+def ib_interp(b: int, coords, X, v) -> np.ndarray:
+    """U = I v at the markers: v [nrhs][3][nblk][b^3] -> [nrhs][3][nm]
+    (dx^3 delta_dx = prod phi, so dx drops out).  Absent blocks read as zero."""
+    X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
+    lut = _block_lookup(b, coords)
+    v = np.asarray(v, dtype=np.float64).reshape(-1, 3, len(lut), b ** 3)
+    out = np.zeros((v.shape[0], 3, X.shape[0]))
+    for i in range(X.shape[0]):
+        for k in range(3):
+            for n, w in _ib_points(X[i], k):
+                blk = lut.get((n[0] // b, n[1] // b, n[2] // b))
+                if blk is None:
+                    continue
+                loc = ((n[2] % b) * b + n[1] % b) * b + n[0] % b
+                out[:, k, i] += w * v[:, k, blk, loc]
+    return out
+

@@ -425,3 +425,68 @@ def test_velocity_refresh_returns_divergence_free_field(oracle):
     # the refresh does not depend on dx (C, L^{-1} and C^dagger scale as 1/dx, dx^2, 1/dx)
     got2 = oracle.velocity_refresh(b, src, u, tgt, dx=0.5, R=32)
     assert np.allclose(got2, got, rtol=0, atol=1e-13)
+
+
+# ------------------------------------------- IB regularisation / interpolation
+@pytest.mark.parametrize("t", [0.0, 0.25, 0.5, 0.77, 1.0, -1.3, 2.49])
+def test_phi3_moment_conditions(oracle, t):
+    """The three-point kernel is defined by sum_j phi(t - j) = 1, sum_j (t - j)
+    phi(t - j) = 0 and sum_j phi(t - j)^2 = 1/2 for every shift t, with support
+    |r| < 3/2; a wrong branch or constant breaks one of them."""
+    js = np.arange(-6, 7)
+    w = np.array([oracle.phi3(t - j) for j in js])
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert abs(np.sum((t - js) * w)) < 1e-15
+    assert abs(np.sum(w * w) - 0.5) < 1e-15
+    assert oracle.phi3(1.5) == 0.0 and oracle.phi3(-1.6) == 0.0 and np.count_nonzero(w) <= 3
+
+
+def _ib_case(rng, nm=7):
+    b = 4
+    coords = np.array([[x, y, z] for x in range(-1, 2) for y in range(-1, 2) for z in range(0, 2)], dtype=np.int32)
+    X = rng.uniform([-1.5, -1.5, 2.5], [1.5, 1.5, 5.5], size=(nm, 3))   # support well inside the blocks
+    return b, coords, X
+
+
+def test_ib_interp_is_scaled_adjoint_of_spread(oracle):
+    """I = dx^3 R^dagger (Sec. 2.1): <R g, v> dx^3 = <g, I v>."""
+    rng = np.random.default_rng(21)
+    b, coords, X = _ib_case(rng)
+    dx = 0.3
+    g = rng.normal(size=(2, 3, X.shape[0]))
+    v = rng.normal(size=(2, 3, coords.shape[0], b ** 3))
+    lhs = np.sum(oracle.ib_spread(b, coords, X, g, dx) * v) * dx ** 3
+    rhs = np.sum(g * oracle.ib_interp(b, coords, X, v))
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+
+
+def test_ib_spread_conserves_force_and_moment(oracle):
+    """sum_n dx^3 (R g)(n) = sum_i g(i) and the first moment about the face
+    positions equals sum_i X_i g(i) (partition of unity and zero first moment)."""
+    rng = np.random.default_rng(22)
+    b, coords, X = _ib_case(rng)
+    g = rng.normal(size=(1, 3, X.shape[0]))
+    f = oracle.ib_spread(b, coords, X, g, dx=1.0)
+    pts = oracle.block_points(b, coords).astype(np.float64)
+    for k in range(3):
+        off = np.full(3, 0.5)
+        off[k] = 0.0
+        xf = pts + off
+        fk = f[0, k].reshape(-1)
+        assert abs(fk.sum() - g[0, k].sum()) < 1e-13
+        assert np.allclose(xf.T @ fk, X.T @ g[0, k], rtol=0, atol=1e-12)
+
+
+def test_ib_interp_exact_for_linear_fields(oracle):
+    rng = np.random.default_rng(23)
+    b, coords, X = _ib_case(rng)
+    pts = oracle.block_points(b, coords).astype(np.float64)
+    a, c = 0.7, np.array([0.3, -1.1, 2.0])
+    v = np.empty((1, 3, coords.shape[0], b ** 3))
+    for k in range(3):
+        off = np.full(3, 0.5)
+        off[k] = 0.0
+        v[0, k] = (a + (pts + off) @ c).reshape(coords.shape[0], b ** 3)
+    U = oracle.ib_interp(b, coords, X, v)
+    for k in range(3):
+        assert np.allclose(U[0, k], a + X @ c, rtol=0, atol=1e-13)
