@@ -494,6 +494,9 @@ EXTRA = {
     "refresh_sphere": "velocity refresh u <- -C^dagger L^{-1} C u (Eq. vel_refresh) on the sphere-plus-wake "
                       "active set (16^3 blocks), u = curl of a Gaussian-blob vector potential, FP32; one refresh "
                       "per step",
+    "ib_sphere": "immersed-boundary regularisation R then interpolation I (Sec. 2.1) of 5120 icosphere markers "
+                 "(radius 20 cells) on the 32 blocks of 16^3 their three-point support touches, 3 components, "
+                 "FP32; throughput in marker-components per second",
     "kinv_sphere": "K(0.25)^{-1} on the surface blocks of the icosphere (5120 markers, radius 20 cells, 16^3 "
                    "blocks, source = target = the blocks the 3-point delta touches), 3 components, FP32; one "
                    "G_K(0.25) apply per step",
@@ -520,7 +523,7 @@ def run_extra(args, rank, world, dist):
         q = li.sphere_ib()
         q = li.Problem("sphere_surface", q.b, q.src, q.src.copy(), q.f, alphas=(0.25,))
         probs = [(q, lgf.LGF_OP_KINV, 0.25)]
-    elif args.workload != "refresh_sphere":
+    elif args.workload not in ("refresh_sphere", "ib_sphere"):
         raise ValueError(f"unknown workload {args.workload}")
     ctx = lgf.Context("f32", device=dev.index)
     ctx.table_build(48)
@@ -548,6 +551,20 @@ def run_extra(args, rank, world, dist):
 
         def step():
             ctx.velocity_refresh(q.b, cells, cells, ut, uo, stream=s)
+    elif args.workload == "ib_sphere":
+        q = li.sphere_ib()
+        Xm = torch.tensor(li.icosphere_markers(5) * 20.0, dtype=torch.float64, device=dev)   # as in sphere_ib
+        nm = Xm.shape[0]
+        gm = torch.tensor(np.random.default_rng(2).normal(size=3 * nm), dtype=torch.float32, device=dev)
+        fm = torch.empty(3 * q.src.shape[0] * q.b ** 3, dtype=torch.float32, device=dev)
+        Um = torch.empty_like(gm)
+        points = float(3 * nm)
+        # marker values and positions read, the field written (spread) or the 27 support values read (interp)
+        alg_step = {"ib_spread": 4 * 3 * nm + 24 * nm + 4 * fm.numel(), "ib_interp": 4 * 3 * nm * 28 + 24 * nm}
+
+        def step():
+            ctx.ib_spread(q.b, q.src, Xm, gm, fm, stream=s)
+            ctx.ib_interp(q.b, q.src, Xm, fm, Um, stream=s)
     else:
         for p, op, a in probs:
             nf = p.nrhs * p.ncomp

@@ -244,6 +244,30 @@ LGF_API lgf_status lgf_curl_adjoint(lgf_ctx *ctx, const lgf_blockset *src, const
 LGF_API lgf_status lgf_velocity_refresh(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt,
                                         const void *u_dev, void *u_out_dev, int32_t nrhs, double dx, void *stream);
 
+/* Immersed-boundary regularisation R (Sec. 2.1):
+     f^k(n) = dx^-3 sum_i g^k(i) prod_d phi(x_F^k(n)_d - X_i,d)
+   on the face lattices of `set` (face k of cell n at n + (1 - e_k)/2, in
+   units of dx), with the three-point kernel phi(r) = (1 + sqrt(1 - 3 r^2)) / 3
+   for |r| <= 1/2, (5 - 3|r| - sqrt(1 - 3 (1 - |r|)^2)) / 6 for
+   1/2 <= |r| <= 3/2, 0 beyond (the paper cites a smoothed three-point kernel
+   without printing it; this is the Roma-Peskin-Berger one).  X_dev:
+   [nmarkers][3] double, marker positions in units of dx; g_dev:
+   [nrhs][3][nmarkers]; f_dev: [nrhs][3][set.nblocks][b^3] (overwritten;
+   points outside the set are dropped).  Context precision for g and f.  The
+   additions are atomic, so the last bits vary between runs.  Errors:
+   LGF_EINVAL, LGF_EUNSUPPORTED (bounding box of the set above 2^26 blocks),
+   LGF_ENOMEM, LGF_ECUDA. */
+LGF_API lgf_status lgf_ib_spread(lgf_ctx *ctx, const lgf_blockset *set, int64_t nmarkers, const double *X_dev,
+                                 const void *g_dev, void *f_dev, int32_t nrhs, double dx, void *stream);
+
+/* Immersed-boundary interpolation I = dx^3 R^dagger (Sec. 2.1):
+     U^k(i) = sum_n v^k(n) prod_d phi(x_F^k(n)_d - X_i,d)
+   (dx^3 delta_dx is the bare product of phi, so dx does not enter).  v_dev:
+   [nrhs][3][set.nblocks][b^3] (absent blocks read as zero); U_dev:
+   [nrhs][3][nmarkers].  Deterministic.  Errors: as lgf_ib_spread. */
+LGF_API lgf_status lgf_ib_interp(lgf_ctx *ctx, const lgf_blockset *set, int64_t nmarkers, const double *X_dev,
+                                 const void *v_dev, void *U_dev, int32_t nrhs, void *stream);
+
 /* FP64 residual check of the discrete Poisson problem (Sec. 2.2, Eq. dpoisson):
      r = (L_h u)(n) - f(n),  L_h u = (sum_{+-e_i} u(n +- e) - 6 u(n)) / dx^2,
    at every point of `set` whose six neighbours are in `set`; r = 0 elsewhere.

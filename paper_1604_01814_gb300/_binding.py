@@ -23,7 +23,7 @@ LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR, LGF_OP_KINV = 0
 # Every symbol include/lgf.h declares (checked by the symbol test).
 EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
            "lgf_kinv_lookup", "lgf_poisson_apply", "lgf_kinv_apply", "lgf_curl", "lgf_curl_adjoint",
-           "lgf_velocity_refresh", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
+           "lgf_velocity_refresh", "lgf_ib_spread", "lgf_ib_interp", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
            "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_intfactor_apply_noalloc",
            "lgf_status_string", "lgf_last_error", "lgf_version")
 
@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH):
         "lgf_curl": [vp, bsp, bsp, vp, vp, i32, dbl, vp],
         "lgf_curl_adjoint": [vp, bsp, bsp, vp, vp, i32, dbl, vp],
         "lgf_velocity_refresh": [vp, bsp, bsp, vp, vp, i32, dbl, vp],
+        "lgf_ib_spread": [vp, bsp, i64, vp, vp, vp, i32, dbl, vp],
+        "lgf_ib_interp": [vp, bsp, i64, vp, vp, vp, i32, vp],
         "lgf_intfactor_apply": [vp, dbl, bsp, bsp, vp, vp, i32, i32, vp],
         "lgf_intfactor_weights": [vp, dbl, vp, i32, ctypes.POINTER(i32), vp],
         "lgf_batch_apply": [vp, ctypes.POINTER(lgf_problem), i32, vp],
@@ -228,6 +230,39 @@ class Context:
         """u_out = -C^dagger L^{-1} C u (Eq. vel_refresh)."""
         return self._vector_op("lgf_velocity_refresh", b, src, tgt, u, u_out, nrhs, dx, stream)
 
+    def _markers(self, X):
+        import torch
+        if not X.is_cuda or X.dtype != torch.float64 or not X.is_contiguous() or X.dim() != 2 or X.shape[1] != 3:
+            raise ValueError("X must be a contiguous CUDA float64 tensor of shape [nmarkers, 3]")
+        return X
+
+    def _marker_values(self, t, n, name):
+        if t.numel() != n or t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of {n} context-precision values")
+        return t
+
+    def ib_spread(self, b: int, blocks, X, g, f, nrhs: int = 1, dx: float = 1.0, stream=None):
+        """f = R g: marker values g [nrhs][3][nm] onto the face lattices of the blocks."""
+        bs, ba = _blockset(b, blocks)
+        X = self._markers(X)
+        self._marker_values(g, nrhs * 3 * X.shape[0], "g")
+        if bs.nblocks:
+            self._field(f, bs.nblocks, b, 3 * nrhs, "f")
+        self._check(self._L.lgf_ib_spread(self._h, ctypes.byref(bs), X.shape[0], X.data_ptr(), _ptr(g), _ptr(f),
+                                          int(nrhs), float(dx), _stream_ptr(stream)), "lgf_ib_spread")
+        return f
+
+    def ib_interp(self, b: int, blocks, X, v, U, nrhs: int = 1, stream=None):
+        """U = I v at the markers: [nrhs][3][nm]."""
+        bs, ba = _blockset(b, blocks)
+        X = self._markers(X)
+        if bs.nblocks:
+            self._field(v, bs.nblocks, b, 3 * nrhs, "v")
+        self._marker_values(U, nrhs * 3 * X.shape[0], "U")
+        self._check(self._L.lgf_ib_interp(self._h, ctypes.byref(bs), X.shape[0], X.data_ptr(), _ptr(v), _ptr(U),
+                                          int(nrhs), _stream_ptr(stream)), "lgf_ib_interp")
+        return U
+
     def poisson_apply(self, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1, dx: float = 1.0, stream=None):
         s, sa = _blockset(b, src)
         t, ta = _blockset(b, tgt)
@@ -348,6 +383,14 @@ def lgf_curl_adjoint(ctx: Context, *a, **kw):
 
 def lgf_velocity_refresh(ctx: Context, *a, **kw):
     return ctx.velocity_refresh(*a, **kw)
+
+
+def lgf_ib_spread(ctx: Context, *a, **kw):
+    return ctx.ib_spread(*a, **kw)
+
+
+def lgf_ib_interp(ctx: Context, *a, **kw):
+    return ctx.ib_interp(*a, **kw)
 
 
 def lgf_intfactor_apply(ctx: Context, *a, **kw):

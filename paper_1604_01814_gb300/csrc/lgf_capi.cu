@@ -221,6 +221,7 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
     ctx->pplans.clear();
     ctx->iplans.clear();
     ctx->cplans.clear();
+    ctx->ibplans.clear();
     for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
     for (auto &kv : ctx->gk_tables) cudaFree(kv.second);
     for (auto &kv : ctx->tw32) cudaFree(kv.second);
@@ -414,6 +415,48 @@ lgf_status lgf_velocity_refresh(lgf_ctx *ctx, const lgf_blockset *src, const lgf
     if ((st = curl_run(ctx, pc, u_dev, sc.E, nrhs, 1.0 / dx, s)) != LGF_OK) return st;
     if ((st = poisson_run(ctx, pp.plan, pp.spec, sc.E, sc.F, 3 * nrhs, dx, s)) != LGF_OK) return st;
     return curl_run(ctx, pa, sc.F, u_out_dev, nrhs, 1.0 / dx, s);
+}
+
+}  // extern "C"
+
+namespace {
+lgf_status ib_apply(lgf_ctx *ctx, bool spread, const lgf_blockset *set, int64_t nmarkers, const double *X_dev,
+                    const void *in_dev, void *out_dev, int32_t nrhs, double dx, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if ((st = check_blockset(ctx, set, "block set")) != LGF_OK) return st;
+    if (nrhs < 1) return fail(ctx, LGF_EINVAL, "nrhs must be >= 1");
+    if (nmarkers < 0 || (nmarkers > 0 && !X_dev)) return fail(ctx, LGF_EINVAL, "IB: bad marker arrays");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(ctx, LGF_EINVAL, "dx must be positive and finite");
+    const bool has_out = spread ? set->nblocks > 0 : nmarkers > 0;
+    if (has_out && !out_dev) return fail(ctx, LGF_EINVAL, "null output pointer");
+    const bool reads_in = spread ? nmarkers > 0 : (set->nblocks > 0 && nmarkers > 0);
+    if (reads_in && !in_dev) return fail(ctx, LGF_EINVAL, "null input pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (set->nblocks == 0) {
+        if (!spread && nmarkers > 0)
+            LGF_CUDA(ctx, cudaMemsetAsync(out_dev, 0, (size_t)nrhs * 3 * nmarkers * elem_size(ctx), s));
+        return LGF_OK;
+    }
+    IBPlan *pl = nullptr;
+    if ((st = ib_plan(ctx, set, &pl)) != LGF_OK) return st;
+    return ib_run(ctx, pl, spread, nmarkers, X_dev, in_dev, out_dev, nrhs, dx, s);
+}
+}  // namespace
+
+extern "C" {
+
+lgf_status lgf_ib_spread(lgf_ctx *ctx, const lgf_blockset *set, int64_t nmarkers, const double *X_dev,
+                         const void *g_dev, void *f_dev, int32_t nrhs, double dx, void *stream)
+{
+    return ib_apply(ctx, true, set, nmarkers, X_dev, g_dev, f_dev, nrhs, dx, stream);
+}
+
+lgf_status lgf_ib_interp(lgf_ctx *ctx, const lgf_blockset *set, int64_t nmarkers, const double *X_dev,
+                         const void *v_dev, void *U_dev, int32_t nrhs, void *stream)
+{
+    return ib_apply(ctx, false, set, nmarkers, X_dev, v_dev, U_dev, nrhs, 1.0, stream);
 }
 
 lgf_status lgf_intfactor_weights(lgf_ctx *ctx, double alpha, double *w_dev, int32_t cap, int32_t *radius,

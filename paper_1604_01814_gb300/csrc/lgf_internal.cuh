@@ -93,6 +93,15 @@ struct Scratch {
     size_t e = 0, f = 0;
 };
 
+// Block look-up for the immersed-boundary operators: dense table over the
+// bounding box of the block set.
+struct IBPlan {
+    int b = 0, lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+    std::vector<int32_t> coords;
+    int *lut_dev = nullptr;
+    ~IBPlan();
+};
+
 // Curl stencil plan: for every target block, the source blocks at the block
 // itself and at +dir along x, y, z (-1 where absent).
 struct CurlPlan {
@@ -130,6 +139,7 @@ struct lgf_ctx {
     std::vector<std::unique_ptr<lgf::IntfPlan>> iplans;
     std::vector<std::unique_ptr<lgf::IntfWeights>> weights;
     std::vector<std::unique_ptr<lgf::CurlPlan>> cplans;
+    std::vector<std::unique_ptr<lgf::IBPlan>> ibplans;
 
     // grow-only scratch, one set per concurrent branch of lgf_batch_apply
     // (branch 0 also serves the single applies); `cur` is the set the next
@@ -225,6 +235,11 @@ lgf_status curl_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *
 lgf_status curl_run(lgf_ctx *ctx, const CurlPlan *pl, const void *in, void *out, int nrhs, double scale,
                     cudaStream_t s);
 std::vector<int32_t> grown_forward(const lgf_blockset *tgt);
+
+// Immersed-boundary operators (lgf_ib.cu)
+lgf_status ib_plan(lgf_ctx *ctx, const lgf_blockset *set, IBPlan **out);
+lgf_status ib_run(lgf_ctx *ctx, const IBPlan *pl, bool spread, int64_t nm, const double *X, const void *in, void *out,
+                  int nrhs, double dx, cudaStream_t s);
 
 // Residual (lgf_residual.cu)
 lgf_status residual_run(lgf_ctx *ctx, const lgf_blockset *set, const void *u, const void *f, double dx,
