@@ -151,13 +151,17 @@ def make_workload(name: str):
     raise ValueError(f"unknown workload {name}")
 
 
+# transform lengths of the library's plans: 2^k and 3 * 2^k from 32 to 4096
+FFT_SIZES = (32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096)
+
+
 def geometry(p):
     """Transform-box geometry of the Poisson plan (mirrors the library's plan)."""
     b = p.b
     allc = np.concatenate([p.src, p.tgt])
     lo, hi = allc.min(0), allc.max(0)
     L = (hi - lo + 1) * b
-    M = [32 * 2 ** max(0, math.ceil(math.log2(max(1, 2 * l - 1) / 32))) for l in L]
+    M = [next(m for m in FFT_SIZES if m >= 2 * l - 1) for l in L]
     Ls = [int(v) for v in (p.src.max(0) - p.src.min(0) + 1) * b]
     Lt = [int(v) for v in (p.tgt.max(0) - p.tgt.min(0) + 1) * b]
     return [int(m) for m in M], Ls, Lt

@@ -1,14 +1,14 @@
-// Shared-memory FFTs of power-of-two length M (32..4096) for many lines at once.
+// In-register DFT building blocks of the pass kernels (lgf_poisson_kernels.cuh).
 //
-// A line is factored into radix-16/8/4/2 stages.  The forward transform is a
-// decimation-in-frequency sweep: each stage reads R elements at stride N/R of
-// a sub-problem of size N, does the R-point DFT in registers, multiplies by
-// the twiddles w_N^{j q} and writes the results back to the same R slots, so
-// sub-problem q occupies a contiguous range afterwards.  The spectrum ends in
-// mixed-radix digit-reversed order; pos_of_freq/freq_of_pos convert.  The
-// inverse is the exact adjoint sweep (conjugate twiddles, stages reversed),
-// which takes digit-reversed input to natural-order output.  A z-pass can
-// therefore run forward -> pointwise multiply -> inverse with no permutation.
+// A line of length M (2^k, or 3 * 2^k) is transformed by decimation in
+// frequency: each stage reads R elements at stride N/R of a sub-problem of
+// size N, does the R-point DFT in registers, multiplies by the twiddles
+// w_N^{j q} and writes the results back to the same R slots, so sub-problem q
+// occupies a contiguous range afterwards.  The spectrum ends in mixed-radix
+// digit-reversed order.  The inverse is the exact adjoint sweep (conjugate
+// twiddles, stages reversed), which takes digit-reversed input to
+// natural-order output, so a z pass can run forward -> pointwise multiply ->
+// inverse with no permutation.
 //
 // Sign convention: forward X[k] = sum_n x[n] e^{-2 pi i n k / M};
 // inverse x[n] = sum_k X[k] e^{+2 pi i n k / M} (unnormalised).
@@ -35,40 +35,41 @@ __device__ __forceinline__ Cx<R> cmulc(Cx<R> a, Cx<R> b) { return {a.x * b.x + a
 template <typename R>
 __device__ __forceinline__ Cx<R> cconj(Cx<R> a) { return {a.x, -a.y}; }
 
-// Radix factorisation of a power-of-two length, passed to kernels by value.
-struct FftShape {
-    int M;       // length
-    int logM;    // log2(M)
-    int nst;     // number of stages
-    int lg[4];   // log2 of each stage's radix, first stage first
-};
-
-// cos(pi k / 8) and sin(pi k / 8), k = 0..8 (the 16th roots of unity).
-__host__ __device__ constexpr double c16(int k)
+// cos(pi m / 24) for m = 0..12 (every twiddle angle of the register DFTs,
+// radices 2..16 and 3 * 2^j up to 48, is a multiple of pi / 24).
+__host__ __device__ constexpr double c24q(int m)
 {
-    return k == 0 ? 1.0 : k == 1 ? 0.92387953251128675613 : k == 2 ? 0.70710678118654752440
-         : k == 3 ? 0.38268343236508977173 : k == 4 ? 0.0 : k == 5 ? -0.38268343236508977173
-         : k == 6 ? -0.70710678118654752440 : k == 7 ? -0.92387953251128675613 : -1.0;
+    return m == 0 ? 1.0 : m == 1 ? 0.99144486137381041114 : m == 2 ? 0.96592582628906828675
+         : m == 3 ? 0.92387953251128675613 : m == 4 ? 0.86602540378443864676 : m == 5 ? 0.79335334029123516458
+         : m == 6 ? 0.70710678118654752440 : m == 7 ? 0.60876142900872063942 : m == 8 ? 0.5
+         : m == 9 ? 0.38268343236508977173 : m == 10 ? 0.25881904510252076235 : m == 11 ? 0.13052619222005159155
+         : 0.0;
 }
-__host__ __device__ constexpr double s16(int k) { return c16(k < 4 ? 4 - k : k - 4) * (k <= 8 ? 1.0 : -1.0); }
+// cos(pi m / 24) and sin(pi m / 24) for any integer m.
+__host__ __device__ constexpr double c24(int m)
+{
+    return (m = ((m % 48) + 48) % 48, m > 24 ? c24(48 - m) : m > 12 ? -c24q(24 - m) : c24q(m));
+}
+__host__ __device__ constexpr double s24(int m) { return c24(m - 12); }
 
-// v * exp(DIR * 2 pi i k / R) for compile-time R, k.
+// v * exp(DIR * 2 pi i k / R) for compile-time R (a divisor of 48 times k), k.
 template <int R, int K, int DIR, typename T>
 __device__ __forceinline__ Cx<T> rot(Cx<T> v)
 {
-    constexpr int q = (16 / R) * K;   // angle = pi q / 8
-    if constexpr (q == 0) {
+    static_assert((48 * K) % R == 0, "twiddle angle must be a multiple of pi/24");
+    constexpr int m = 48 * K / R;   // angle = pi m / 24
+    if constexpr (m % 48 == 0) {
         return v;
-    } else if constexpr (q == 4) {    // multiply by DIR * i
+    } else if constexpr (m % 48 == 12) {   // multiply by DIR * i
         return {T(-DIR) * v.y, T(DIR) * v.x};
     } else {
-        const T c = T(c16(q)), s = T(DIR) * T(s16(q));
+        const T c = T(c24(m)), s = T(DIR) * T(s24(m));
         return {v.x * c - v.y * s, v.x * s + v.y * c};
     }
 }
 
 // In-register DFT of R points (natural order in, natural order out), by
-// recursive even/odd splitting unrolled at compile time.
+// recursive even/odd splitting unrolled at compile time (R = 2^j or 3 * 2^j).
 template <int R, int DIR, typename T>
 struct Dft {
     template <int K>
@@ -97,6 +98,20 @@ struct Dft {
 template <int DIR, typename T>
 struct Dft<1, DIR, T> {
     static __device__ __forceinline__ void run(Cx<T> *) {}
+};
+// Three points: X0 = a0 + t, X1,2 = a0 - t/2 +- DIR i (sqrt(3)/2)(a1 - a2), t = a1 + a2.
+template <int DIR, typename T>
+struct Dft<3, DIR, T> {
+    static __device__ __forceinline__ void run(Cx<T> *a)
+    {
+        const T h = T(0.86602540378443864676);
+        const Cx<T> t = cadd(a[1], a[2]), d = csub(a[1], a[2]);
+        const Cx<T> m = {a[0].x - T(0.5) * t.x, a[0].y - T(0.5) * t.y};
+        const Cx<T> sd = {T(-DIR) * h * d.y, T(DIR) * h * d.x};
+        a[0] = cadd(a[0], t);
+        a[1] = cadd(m, sd);
+        a[2] = csub(m, sd);
+    }
 };
 
 // DFT of R points whose upper half a[R/2..R) is zero (only a[0..R/2) is
@@ -148,135 +163,6 @@ __device__ __forceinline__ void dft_half_out(Cx<T> *a)
     Dft<R / 2, DIR, T>::run(e);
     Dft<R / 2, DIR, T>::run(o);
     combine_low<R, DIR, T>(a, e, o);
-}
-
-// Shared-memory addressing of lines.
-// Rows: line-major, each line contiguous, one padding slot per 16 elements
-// (keeps stride-R accesses of late stages off a single bank).
-struct RowAddr {
-    int ld;  // = M + M / 16
-    __device__ __forceinline__ int operator()(int line, int m) const { return line * ld + m + (m >> 4); }
-};
-// Columns: element m of line w at m * W + w (consecutive threads -> consecutive w).
-struct ColAddr {
-    int W;
-    __device__ __forceinline__ int operator()(int line, int m) const { return m * W + line; }
-};
-
-// One stage.  Forward (DIR = -1): butterfly then twiddle.  Adjoint (DIR = +1):
-// conjugate twiddle then butterfly, data movement reversed.
-// tw[m] = exp(-2 pi i m / M), m < M.  LINE_FAST selects the thread -> (line,
-// group) mapping so that consecutive threads touch consecutive addresses.
-template <int LOGR, int DIR, bool LINE_FAST, typename T, class Addr>
-__device__ __forceinline__ void fft_stage(Cx<T> *s, const Addr &ad, int nlines, int logM, int logN,
-                                          const Cx<T> *tw)
-{
-    constexpr int R = 1 << LOGR;
-    const int logNp = logN - LOGR;                 // sub-problem size after this stage
-    const int Np = 1 << logNp;
-    const int logG = logM - LOGR;                  // groups per line
-    const int items = nlines << logG;
-    const int twshift = logM - logN;               // twiddle index = (M/N) * j * q
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        int line, g;
-        if (LINE_FAST) {
-            line = it % nlines;
-            g = it / nlines;
-        } else {
-            g = it & ((1 << logG) - 1);
-            line = it >> logG;
-        }
-        const int sub = g >> logNp, j = g & (Np - 1);
-        const int o = sub << logN;
-        Cx<T> a[R];
-        if (DIR < 0) {
-#pragma unroll
-            for (int p = 0; p < R; ++p) a[p] = s[ad(line, o + j + (p << logNp))];
-            Dft<R, -1, T>::run(a);
-#pragma unroll
-            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], tw[(j * q) << twshift]);
-#pragma unroll
-            for (int q = 0; q < R; ++q) s[ad(line, o + (q << logNp) + j)] = a[q];
-        } else {
-#pragma unroll
-            for (int q = 0; q < R; ++q) a[q] = s[ad(line, o + (q << logNp) + j)];
-#pragma unroll
-            for (int q = 1; q < R; ++q) a[q] = cmulc(a[q], tw[(j * q) << twshift]);
-            Dft<R, 1, T>::run(a);
-#pragma unroll
-            for (int p = 0; p < R; ++p) s[ad(line, o + j + (p << logNp))] = a[p];
-        }
-    }
-}
-
-template <int DIR, bool LINE_FAST, typename T, class Addr>
-__device__ __forceinline__ void fft_stage_any(int lgR, Cx<T> *s, const Addr &ad, int nlines, int logM, int logN,
-                                              const Cx<T> *tw)
-{
-    switch (lgR) {
-    case 4: fft_stage<4, DIR, LINE_FAST>(s, ad, nlines, logM, logN, tw); break;
-    case 3: fft_stage<3, DIR, LINE_FAST>(s, ad, nlines, logM, logN, tw); break;
-    case 2: fft_stage<2, DIR, LINE_FAST>(s, ad, nlines, logM, logN, tw); break;
-    default: fft_stage<1, DIR, LINE_FAST>(s, ad, nlines, logM, logN, tw); break;
-    }
-}
-
-// Forward transform of `nlines` lines: natural order in, digit-reversed out.
-// Every thread of the block must call it (it synchronises between stages).
-template <bool LINE_FAST, typename T, class Addr>
-__device__ void fft_forward(Cx<T> *s, const Addr &ad, int nlines, const FftShape &sh, const Cx<T> *tw)
-{
-    int logN = sh.logM;
-    for (int st = 0; st < sh.nst; ++st) {
-        fft_stage_any<-1, LINE_FAST>(sh.lg[st], s, ad, nlines, sh.logM, logN, tw);
-        __syncthreads();
-        logN -= sh.lg[st];
-    }
-}
-
-// Inverse (adjoint) transform: digit-reversed in, natural order out.
-template <bool LINE_FAST, typename T, class Addr>
-__device__ void fft_inverse(Cx<T> *s, const Addr &ad, int nlines, const FftShape &sh, const Cx<T> *tw)
-{
-    int logN[4];
-    int l = sh.logM;
-    for (int st = 0; st < sh.nst; ++st) {
-        logN[st] = l;
-        l -= sh.lg[st];
-    }
-    for (int st = sh.nst - 1; st >= 0; --st) {
-        fft_stage_any<1, LINE_FAST>(sh.lg[st], s, ad, nlines, sh.logM, logN[st], tw);
-        __syncthreads();
-    }
-}
-
-// Position in the forward output of frequency k.
-__device__ __forceinline__ int pos_of_freq(int k, const FftShape &sh)
-{
-    int P = 0, logN = sh.logM;
-    for (int st = 0; st < sh.nst; ++st) {
-        const int lgR = sh.lg[st];
-        const int q = k & ((1 << lgR) - 1);
-        k >>= lgR;
-        logN -= lgR;
-        P += q << logN;
-    }
-    return P;
-}
-
-// Frequency held at position P of the forward output.
-__device__ __forceinline__ int freq_of_pos(int P, const FftShape &sh)
-{
-    int k = 0, shift = 0, logN = sh.logM;
-    for (int st = 0; st < sh.nst; ++st) {
-        const int lgR = sh.lg[st];
-        logN -= lgR;
-        const int q = P >> logN;
-        P &= (1 << logN) - 1;
-        k += q << shift;
-        shift += lgR;
-    }
-    return k;
 }
 
 }  // namespace lgf

@@ -18,11 +18,9 @@ constexpr int kMaxFft = 4096;        // largest transform length per axis
 constexpr int kMinTableRadius = 24;  // expansion error at |n| > 24 is below 1e-9 relative
 
 // --------------------------------------------------------------------------
-// Host-side factorisation of a power-of-two FFT length.
+// Transform lengths: 2^k and 3 * 2^k from 32 to 4096.
 // --------------------------------------------------------------------------
-FftShape make_fft_shape(int M);
-int next_fft_size(int n);   // smallest supported length >= n (power of two >= 32)
-
+int next_fft_size(int n);   // smallest supported length >= n
 // --------------------------------------------------------------------------
 // Poisson plan: one problem's padded transform box.
 // Box coordinates are lattice coordinates minus `lo` (the union bounding box

@@ -29,28 +29,13 @@
 
 namespace lgf {
 
-FftShape make_fft_shape(int M)
-{
-    FftShape sh{};
-    sh.M = M;
-    int l = 0;
-    while ((1 << l) < M) ++l;
-    sh.logM = l;
-    sh.nst = 0;
-    int rem = l;
-    while (rem > 0) {
-        const int r = rem >= 4 ? 4 : rem;
-        sh.lg[sh.nst++] = r;
-        rem -= r;
-    }
-    return sh;
-}
-
 int next_fft_size(int n)
 {
-    int m = 32;
-    while (m < n) m *= 2;
-    return m;
+    // 2^k and 3 * 2^k: the box pays at most 1.5x its extent per axis
+    static const int sizes[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
+    for (int m : sizes)
+        if (m >= n) return m;
+    return 2 * kMaxFft;   // beyond the largest supported length: the plan rejects it
 }
 
 PoissonPlan::~PoissonPlan()

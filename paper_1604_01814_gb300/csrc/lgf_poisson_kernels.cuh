@@ -1,7 +1,7 @@
 // Pass kernels of the Poisson apply, specialised on the transform length.
 //
-// Every length M = 2^LOGM (32..4096) has a fixed plan of two or three DIF
-// stages (radix <= 16), see Plan below.  A line (a column of W adjacent kx
+// Every length M = 2^k or 3 * 2^k (32..4096) has a fixed plan of two or three
+// DIF stages (radix <= 16), see Plan below.  A line (a column of W adjacent kx
 // values, or one packed pair of x rows) is handled by TPC threads:
 //   - the first forward stage loads its operands straight from global memory
 //     into registers (all loads of a thread in flight together), does the
@@ -19,72 +19,72 @@
 namespace lgf {
 namespace pk {
 
-template <int LOGM>
+constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+
+// Stage plan of a length M (2^k or 3 * 2^k, 32..4096): a first stage of radix
+// R0, for M >= 384 a middle stage of radix R1 (R0, R1 powers of two), and a
+// last stage of radix RL (16, 8 or 4; 12 when M = 3 * 2^k).  Every stage
+// before the last splits off a power of two, so its twiddle index stays
+// j q M/N with M/N a power of two.  TPC threads share a line: the greatest
+// common divisor of the stages' group counts, so that every thread owns a
+// whole number of groups in every stage.
+template <int ML>
 struct Plan {
-    static constexpr int M = 1 << LOGM;
-    static constexpr int NST = LOGM <= 8 ? 2 : 3;
-    static constexpr int LG0 = (LOGM == 5 || LOGM == 6 || LOGM == 9) ? 3 : 4;
-    static constexpr int LG1 = LOGM == 5 ? 2 : (LOGM == 6 || LOGM == 7 || LOGM == 9 || LOGM == 10) ? 3 : 4;
-    static constexpr int LG2 = NST == 3 ? LOGM - LG0 - LG1 : 0;
-    static constexpr int LGL = NST == 3 ? LG2 : LG1;             // last stage
-    static constexpr int LOGN1 = LOGM - LG0;                      // sub-problem size entering stage 1
-    static constexpr int G0 = M >> LG0, G1 = M >> LG1, G2 = NST == 3 ? (M >> LG2) : (1 << 30);
-    static constexpr int TPC = G0 < G1 ? (G0 < G2 ? G0 : G2) : (G1 < G2 ? G1 : G2);
-    static constexpr int GL = M >> LGL;                           // groups of the last stage
-    static_assert(LG0 + LG1 + LG2 == LOGM, "plan must cover the length");
+    static constexpr int M = ML;
+    static constexpr int R0 = M == 32 || M == 64 || M == 96 || M == 384 || M == 512 || M == 768 ? 8 : 16;
+    static constexpr int R1 = M == 384 ? 4 : M == 512 || M == 768 || M == 1024 || M == 1536 ? 8
+                            : M == 2048 || M == 3072 || M == 4096 ? 16 : 1;
+    static constexpr int RL = M / (R0 * R1);
+    static constexpr int NST = R1 > 1 ? 3 : 2;
+    static constexpr int N1 = M / R0;                             // sub-problem size entering stage 1
+    static constexpr int G0 = M / R0, G1 = M / R1, GL = M / RL;   // groups per stage
+    static constexpr int TPC = cgcd(cgcd(G0, NST == 3 ? G1 : G0), GL);
+    static_assert(R0 * R1 * RL == M && RL <= 16 && RL >= 4, "plan must cover the length");
+    static_assert(G0 % TPC == 0 && G1 % TPC == 0 && GL % TPC == 0, "whole groups per thread");
 };
 
-// Position of frequency k after the forward sweep, and back.
-template <int LOGM>
+// Position of frequency k after the forward sweep, and back: position
+// q0 M/R0 + q1 RL + qL holds frequency q0 + R0 q1 + R0 R1 qL.
+template <int ML>
 __device__ __forceinline__ int pos_of(int k)
 {
-    using P = Plan<LOGM>;
-    const int q0 = k & ((1 << P::LG0) - 1);
-    k >>= P::LG0;
-    const int q1 = k & ((1 << P::LG1) - 1);
-    k >>= P::LG1;
-    int pos = (q0 << (LOGM - P::LG0)) + (q1 << (LOGM - P::LG0 - P::LG1));
-    if (P::NST == 3) pos += k;   // k now holds q2
-    return pos;
+    using P = Plan<ML>;
+    const int q0 = k % P::R0;
+    k /= P::R0;
+    const int q1 = k % P::R1;
+    const int qL = k / P::R1;
+    return q0 * (ML / P::R0) + q1 * P::RL + qL;
 }
 
-template <int LOGM>
+template <int ML>
 __device__ __forceinline__ int freq_of(int pos)
 {
-    using P = Plan<LOGM>;
-    const int q0 = pos >> (LOGM - P::LG0);
-    const int r0 = pos & ((1 << (LOGM - P::LG0)) - 1);
-    const int q1 = r0 >> (LOGM - P::LG0 - P::LG1);
-    const int q2 = r0 & ((1 << (LOGM - P::LG0 - P::LG1)) - 1);
-    return q0 + (q1 << P::LG0) + (q2 << (P::LG0 + P::LG1));
+    using P = Plan<ML>;
+    const int q0 = pos / (ML / P::R0);
+    const int r0 = pos % (ML / P::R0);
+    return q0 + P::R0 * (r0 / P::RL) + P::R0 * P::R1 * (r0 % P::RL);
 }
 
-// Forward butterfly of one group: DFT then twiddles w_N^{j q} (none when the
-// stage is the last one, N = R).
-// HALF: the inputs a[R/2..R) are zero (not read).
-template <int LOGM, int LOGN, int LOGR, bool HALF = false, typename T>
+// Forward butterfly of one group of a stage that is not the last: DFT then
+// twiddles w_N^{j q} = tw[j q TWS] (TWS = M/N).  HALF: the inputs
+// a[R/2..R) are zero (not read).
+template <int R, int TWS, bool HALF = false, typename T>
 __device__ __forceinline__ void dif_group(Cx<T> *a, int j, const Cx<T> *tw)
 {
-    constexpr int R = 1 << LOGR;
     if constexpr (HALF)
         dft_half_in<R, -1, T>(a);
     else
         Dft<R, -1, T>::run(a);
-    if constexpr (LOGN > LOGR) {
 #pragma unroll
-        for (int q = 1; q < R; ++q) a[q] = cmul(a[q], tw[(j * q) << (LOGM - LOGN)]);
-    }
+    for (int q = 1; q < R; ++q) a[q] = cmul(a[q], tw[j * q * TWS]);
 }
 
-// HALF: only the outputs a[0..R/2) are formed.
-template <int LOGM, int LOGN, int LOGR, bool HALF = false, typename T>
+// Its adjoint.  HALF: only the outputs a[0..R/2) are formed.
+template <int R, int TWS, bool HALF = false, typename T>
 __device__ __forceinline__ void dit_group(Cx<T> *a, int j, const Cx<T> *tw)
 {
-    constexpr int R = 1 << LOGR;
-    if constexpr (LOGN > LOGR) {
 #pragma unroll
-        for (int q = 1; q < R; ++q) a[q] = cmulc(a[q], tw[(j * q) << (LOGM - LOGN)]);
-    }
+    for (int q = 1; q < R; ++q) a[q] = cmulc(a[q], tw[j * q * TWS]);
     if constexpr (HALF)
         dft_half_out<R, 1, T>(a);
     else
@@ -92,29 +92,28 @@ __device__ __forceinline__ void dit_group(Cx<T> *a, int j, const Cx<T> *tw)
 }
 
 // Middle stage (three-stage plans): shared memory to shared memory.
-template <int LOGM, int DIR, typename T, class Addr>
+template <int ML, int DIR, typename T, class Addr>
 __device__ __forceinline__ void middle_stage(Cx<T> *s, const Addr &ad, int line, int t, const Cx<T> *tw)
 {
-    using P = Plan<LOGM>;
+    using P = Plan<ML>;
     if constexpr (P::NST == 3) {
-        constexpr int LOGN = P::LOGN1, LOGR = P::LG1, R = 1 << LOGR;
-        constexpr int LOGNP = LOGN - LOGR;
+        constexpr int N = P::N1, R = P::R1, NP = N / R;
 #pragma unroll
         for (int g = t; g < P::G1; g += P::TPC) {
-            const int sub = g >> LOGNP, j = g & ((1 << LOGNP) - 1), o = sub << LOGN;
+            const int sub = g / NP, j = g % NP, o = sub * N;
             Cx<T> a[R];
             if (DIR < 0) {
 #pragma unroll
-                for (int p = 0; p < R; ++p) a[p] = s[ad(line, o + j + (p << LOGNP))];
-                dif_group<LOGM, LOGN, LOGR>(a, j, tw);
+                for (int p = 0; p < R; ++p) a[p] = s[ad(line, o + j + p * NP)];
+                dif_group<R, P::R0>(a, j, tw);
 #pragma unroll
-                for (int q = 0; q < R; ++q) s[ad(line, o + (q << LOGNP) + j)] = a[q];
+                for (int q = 0; q < R; ++q) s[ad(line, o + q * NP + j)] = a[q];
             } else {
 #pragma unroll
-                for (int q = 0; q < R; ++q) a[q] = s[ad(line, o + (q << LOGNP) + j)];
-                dit_group<LOGM, LOGN, LOGR>(a, j, tw);
+                for (int q = 0; q < R; ++q) a[q] = s[ad(line, o + q * NP + j)];
+                dit_group<R, P::R0>(a, j, tw);
 #pragma unroll
-                for (int p = 0; p < R; ++p) s[ad(line, o + j + (p << LOGNP))] = a[p];
+                for (int p = 0; p < R; ++p) s[ad(line, o + j + p * NP)] = a[p];
             }
         }
     }
@@ -182,14 +181,14 @@ __device__ __forceinline__ bool column_of(int cta, int w, int K, int nplanes, in
 // stage's upper inputs are zero at compile time and its first butterfly
 // layer is skipped.  Row addresses advance by a fixed stride per radix digit
 // (the last stage's digit is the top digit of the frequency).
-template <typename T, int LOGM, int W, bool HALF>
-__global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
+template <typename T, int ML, int W, bool HALF>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_forward(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
                                                                      int K, int nplanes, int lo, int n, int64_t rs,
                                                                      int64_t os, int64_t in_plane, int64_t out_plane,
                                                                      int64_t in_field, int64_t out_field,
                                                                      const Cx<T> *__restrict__ twg)
 {
-    using P = Plan<LOGM>;
+    using P = Plan<ML>;
     constexpr int M = P::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
@@ -201,7 +200,7 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T>
     const Cx<T> *ib = in + blockIdx.y * in_field + pl * in_plane + kx;
     Cx<T> *ob = out + blockIdx.y * out_field + pl * out_plane + kx;
     const ColAddrW ad{W};
-    constexpr int R0 = 1 << P::LG0;
+    constexpr int R0 = P::R0;
     constexpr int NG0 = P::G0 / P::TPC;
     constexpr int NP = HALF ? R0 / 2 : R0;
     const int64_t istep = (int64_t)P::G0 * rs;
@@ -221,25 +220,25 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T>
 #pragma unroll
     for (int i = 0; i < NG0; ++i) {
         const int g = t + i * P::TPC;
-        dif_group<LOGM, LOGM, P::LG0, HALF>(a[i], g, tw);
+        dif_group<P::R0, 1, HALF>(a[i], g, tw);
 #pragma unroll
         for (int q = 0; q < R0; ++q) s[ad(w, q * P::G0 + g)] = a[i][q];
     }
     __syncthreads();
     if constexpr (P::NST == 3) {
-        middle_stage<LOGM, -1>(s, ad, w, t, tw);
+        middle_stage<ML, -1>(s, ad, w, t, tw);
         __syncthreads();
     }
-    constexpr int RL = 1 << P::LGL;
+    constexpr int RL = P::RL;
     const int64_t ostep = (int64_t)(M / RL) * os;
 #pragma unroll
     for (int g = t; g < P::GL; g += P::TPC) {
         Cx<T> c[RL];
 #pragma unroll
-        for (int q = 0; q < RL; ++q) c[q] = s[ad(w, (g << P::LGL) + q)];
+        for (int q = 0; q < RL; ++q) c[q] = s[ad(w, (g * P::RL) + q)];
         Dft<RL, -1, T>::run(c);
         if (live) {
-            int64_t off = (int64_t)freq_of<LOGM>(g << P::LGL) * os;
+            int64_t off = (int64_t)freq_of<ML>(g * P::RL) * os;
 #pragma unroll
             for (int q = 0; q < RL; ++q) {
                 ob[off] = c[q];
@@ -253,14 +252,14 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_forward(const Cx<T>
 // in + k * rs) in; rows [lo, lo + n) of the result written to
 // out + (m - lo) * os.  The written rows lie in [0, M/2), so the last stage
 // forms only the lower half of its outputs.
-template <typename T, int LOGM, int W>
-__global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
+template <typename T, int ML, int W>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
                                                                      int K, int nplanes, int lo, int n, int64_t rs,
                                                                      int64_t os, int64_t in_plane, int64_t out_plane,
                                                                      int64_t in_field, int64_t out_field,
                                                                      const Cx<T> *__restrict__ twg)
 {
-    using P = Plan<LOGM>;
+    using P = Plan<ML>;
     constexpr int M = P::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
@@ -272,14 +271,14 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T>
     const Cx<T> *ib = in + blockIdx.y * in_field + pl * in_plane + kx;
     Cx<T> *ob = out + blockIdx.y * out_field + pl * out_plane + kx;
     const ColAddrW ad{W};
-    constexpr int RL = 1 << P::LGL;
+    constexpr int RL = P::RL;
     constexpr int NGL = P::GL / P::TPC;
     const int64_t istep = (int64_t)(M / RL) * rs;
     Cx<T> c[NGL][RL];
 #pragma unroll
     for (int i = 0; i < NGL; ++i) {
         const int g = t + i * P::TPC;
-        int64_t off = (int64_t)freq_of<LOGM>(g << P::LGL) * rs;
+        int64_t off = (int64_t)freq_of<ML>(g * P::RL) * rs;
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
             c[i][q] = live ? ib[off] : Cx<T>{T(0), T(0)};
@@ -291,21 +290,21 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T>
         const int g = t + i * P::TPC;
         Dft<RL, 1, T>::run(c[i]);
 #pragma unroll
-        for (int q = 0; q < RL; ++q) s[ad(w, (g << P::LGL) + q)] = c[i][q];
+        for (int q = 0; q < RL; ++q) s[ad(w, (g * P::RL) + q)] = c[i][q];
     }
     __syncthreads();
     if constexpr (P::NST == 3) {
-        middle_stage<LOGM, 1>(s, ad, w, t, tw);
+        middle_stage<ML, 1>(s, ad, w, t, tw);
         __syncthreads();
     }
-    constexpr int R0 = 1 << P::LG0;
+    constexpr int R0 = P::R0;
     const int64_t ostep = (int64_t)P::G0 * os;
 #pragma unroll
     for (int g = t; g < P::G0; g += P::TPC) {
         Cx<T> a[R0];
 #pragma unroll
         for (int q = 0; q < R0; ++q) a[q] = s[ad(w, q * P::G0 + g)];
-        dit_group<LOGM, LOGM, P::LG0, true>(a, g, tw);
+        dit_group<P::R0, 1, true>(a, g, tw);
         if (live) {
             const int r = g - lo;
             int64_t off = (int64_t)r * os;
@@ -327,17 +326,17 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC) k_col_inverse(const Cx<T>
 // stage forms only its lower outputs.
 // Resident CTAs per SM that the register allocation must allow (FP32 at the
 // common lengths 256 and 512: 32 and 24 warps).
-template <typename T, int LOGM>
+template <typename T, int ML>
 struct ConvOcc {
-    static constexpr int value = sizeof(T) == 4 ? (LOGM == 8 ? 4 : LOGM == 9 ? 3 : 1) : 1;
+    static constexpr int value = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 512 ? 3 : 1) : 1;
 };
 
-template <typename T, int LOGM, int W>
-__global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) k_col_convolve(Cx<T> *__restrict__ B, const T *__restrict__ spec,
+template <typename T, int ML, int W>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML>::value) k_col_convolve(Cx<T> *__restrict__ B, const T *__restrict__ spec,
                                                                       int K, int My, int s0, int ns, int t0, int nt,
                                                                       int64_t field, const Cx<T> *__restrict__ twg)
 {
-    using P = Plan<LOGM>;
+    using P = Plan<ML>;
     constexpr int M = P::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
@@ -351,7 +350,7 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) 
     const int64_t plane = (int64_t)My * K;
     Cx<T> *bb = B + field_i * field + (int64_t)ky * K + kx;
     const ColAddrW ad{W};
-    constexpr int R0 = 1 << P::LG0;
+    constexpr int R0 = P::R0;
     constexpr int NG0 = P::G0 / P::TPC;
     const int64_t step0 = (int64_t)P::G0 * plane;
     {
@@ -371,17 +370,17 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) 
 #pragma unroll
         for (int i = 0; i < NG0; ++i) {
             const int g = t + i * P::TPC;
-            dif_group<LOGM, LOGM, P::LG0, true>(a[i], g, tw);
+            dif_group<P::R0, 1, true>(a[i], g, tw);
 #pragma unroll
             for (int q = 0; q < R0; ++q) s[ad(w, q * P::G0 + g)] = a[i][q];
         }
     }
     __syncthreads();
     if constexpr (P::NST == 3) {
-        middle_stage<LOGM, -1>(s, ad, w, t, tw);
+        middle_stage<ML, -1>(s, ad, w, t, tw);
         __syncthreads();
     }
-    constexpr int RL = 1 << P::LGL;
+    constexpr int RL = P::RL;
     constexpr int S = M / RL;   // frequency step of the last stage's digit
     const int Khy = My / 2 + 1;
     const int kyr = ky <= My - ky ? ky : My - ky;
@@ -390,7 +389,7 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) 
 #pragma unroll
     for (int g = t; g < P::GL; g += P::TPC) {
         // frequency of digit q: kb + q S; its mirror M - kb - q S once past M/2
-        const int kb = freq_of<LOGM>(g << P::LGL);
+        const int kb = freq_of<ML>(g * P::RL);
         const T *spl = sp + (int64_t)kb * sp_plane;
         const T *sph = sp + (int64_t)(M - kb) * sp_plane;
         Cx<T> c[RL];
@@ -398,7 +397,7 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) 
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
             gk[q] = q < RL / 2 ? spl[(int64_t)(q * S) * sp_plane] : sph[-(int64_t)(q * S) * sp_plane];
-            c[q] = s[ad(w, (g << P::LGL) + q)];
+            c[q] = s[ad(w, (g * P::RL) + q)];
         }
         Dft<RL, -1, T>::run(c);
 #pragma unroll
@@ -408,11 +407,11 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) 
         }
         Dft<RL, 1, T>::run(c);
 #pragma unroll
-        for (int q = 0; q < RL; ++q) s[ad(w, (g << P::LGL) + q)] = c[q];
+        for (int q = 0; q < RL; ++q) s[ad(w, (g * P::RL) + q)] = c[q];
     }
     __syncthreads();
     if constexpr (P::NST == 3) {
-        middle_stage<LOGM, 1>(s, ad, w, t, tw);
+        middle_stage<ML, 1>(s, ad, w, t, tw);
         __syncthreads();
     }
     const int64_t step1 = (int64_t)P::G0 * plane;
@@ -421,7 +420,7 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) 
         Cx<T> a[R0];
 #pragma unroll
         for (int q = 0; q < R0; ++q) a[q] = s[ad(w, q * P::G0 + g)];
-        dit_group<LOGM, LOGM, P::LG0, true>(a, g, tw);
+        dit_group<P::R0, 1, true>(a, g, tw);
         if (live) {
             const int r = g - t0;
             int64_t off = (int64_t)r * plane;
@@ -441,12 +440,12 @@ __global__ void __launch_bounds__(W * Plan<LOGM>::TPC, ConvOcc<T, LOGM>::value) 
 // block layout (HALF: the apply, where the row lies in [0, M/2) so the first
 // stage's upper inputs are zero at compile time) or from a dense box with row
 // length dense_ld (the spectrum build, full rows).
-template <typename T, int LOGM, int LPC, bool HALF>
-__global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_forward(const T *__restrict__ f, Cx<T> *__restrict__ A,
+template <typename T, int ML, int LPC, bool HALF>
+__global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward(const T *__restrict__ f, Cx<T> *__restrict__ A,
                                                                        PoissonGeom g, const Cx<T> *__restrict__ twg,
                                                                        int npairs, int lb, int dense_ld)
 {
-    using P = Plan<LOGM>;
+    using P = Plan<ML>;
     constexpr int M = P::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
@@ -459,7 +458,7 @@ __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_forward(const T *
     const int zi = live ? pr / hp : 0, yi = live ? 2 * (pr - zi * hp) : 0;
     const T *ff = f + blockIdx.y * g.fstride;
     const RowAddrP ad{M + M / 16};
-    constexpr int R0 = 1 << P::LG0;
+    constexpr int R0 = P::R0;
     constexpr int NG0 = P::G0 / P::TPC;
     Cx<T> a[NG0][R0];
     if constexpr (HALF) {
@@ -507,32 +506,32 @@ __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_forward(const T *
 #pragma unroll
     for (int i = 0; i < NG0; ++i) {
         const int gg = t + i * P::TPC;
-        dif_group<LOGM, LOGM, P::LG0, HALF>(a[i], gg, tw);
+        dif_group<P::R0, 1, HALF>(a[i], gg, tw);
 #pragma unroll
         for (int q = 0; q < R0; ++q) s[ad(l, q * P::G0 + gg)] = a[i][q];
     }
     __syncthreads();
     if constexpr (P::NST == 3) {
-        middle_stage<LOGM, -1>(s, ad, l, t, tw);
+        middle_stage<ML, -1>(s, ad, l, t, tw);
         __syncthreads();
     }
-    constexpr int RL = 1 << P::LGL;
+    constexpr int RL = P::RL;
 #pragma unroll
     for (int gg = t; gg < P::GL; gg += P::TPC) {
         Cx<T> c[RL];
 #pragma unroll
-        for (int q = 0; q < RL; ++q) c[q] = s[ad(l, (gg << P::LGL) + q)];
+        for (int q = 0; q < RL; ++q) c[q] = s[ad(l, (gg * P::RL) + q)];
         Dft<RL, -1, T>::run(c);
 #pragma unroll
-        for (int q = 0; q < RL; ++q) s[ad(l, (gg << P::LGL) + q)] = c[q];
+        for (int q = 0; q < RL; ++q) s[ad(l, (gg * P::RL) + q)] = c[q];
     }
     __syncthreads();
     if (!live) return;
     const int K = g.Kx;
     Cx<T> *row = A + blockIdx.y * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
     for (int k = t; k < K; k += P::TPC) {
-        const Cx<T> zk = s[ad(l, pos_of<LOGM>(k))];
-        const Cx<T> zm = s[ad(l, pos_of<LOGM>((M - k) & (M - 1)))];
+        const Cx<T> zk = s[ad(l, pos_of<ML>(k))];
+        const Cx<T> zm = s[ad(l, pos_of<ML>(k == 0 ? 0 : M - k))];
         row[k] = Cx<T>{T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
         row[K + k] = Cx<T>{T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
     }
@@ -540,12 +539,12 @@ __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_forward(const T *
 
 // Inverse: rows (y, y+1) of target plane z from their half spectra; x in
 // [t0x, t0x + Ltx) scaled by dx^2 and scattered to the target block layout.
-template <typename T, int LOGM, int LPC>
-__global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_inverse(const Cx<T> *__restrict__ A, T *__restrict__ u,
+template <typename T, int ML, int LPC>
+__global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T> *__restrict__ A, T *__restrict__ u,
                                                                        PoissonGeom g, const Cx<T> *__restrict__ twg,
                                                                        int npairs, int lb)
 {
-    using P = Plan<LOGM>;
+    using P = Plan<ML>;
     constexpr int M = P::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
@@ -583,22 +582,22 @@ __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_inverse(const Cx<
         } else {
             v = {g1[i].x + g2[i].y, g2[i].x - g1[i].y};
         }
-        s[ad(l, pos_of<LOGM>(k))] = v;
+        s[ad(l, pos_of<ML>(k))] = v;
     }
     __syncthreads();
-    constexpr int RL = 1 << P::LGL;
+    constexpr int RL = P::RL;
 #pragma unroll
     for (int gg = t; gg < P::GL; gg += P::TPC) {
         Cx<T> c[RL];
 #pragma unroll
-        for (int q = 0; q < RL; ++q) c[q] = s[ad(l, (gg << P::LGL) + q)];
+        for (int q = 0; q < RL; ++q) c[q] = s[ad(l, (gg * P::RL) + q)];
         Dft<RL, 1, T>::run(c);
 #pragma unroll
-        for (int q = 0; q < RL; ++q) s[ad(l, (gg << P::LGL) + q)] = c[q];
+        for (int q = 0; q < RL; ++q) s[ad(l, (gg * P::RL) + q)] = c[q];
     }
     __syncthreads();
     if constexpr (P::NST == 3) {
-        middle_stage<LOGM, 1>(s, ad, l, t, tw);
+        middle_stage<ML, 1>(s, ad, l, t, tw);
         __syncthreads();
     }
     if (!live) return;
@@ -607,14 +606,14 @@ __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_inverse(const Cx<
     const int bm = g.b - 1;
     const int *mrow = g.tgtmap + ((zi >> lb) * g.nbt[1] + (yi >> lb)) * g.nbt[0];
     const int inner = (((zi & bm) << lb) + (yi & bm)) << lb;
-    constexpr int R0 = 1 << P::LG0;
+    constexpr int R0 = P::R0;
     // target x lies in [0, M/2): only the lower half of the last outputs
 #pragma unroll
     for (int gg = t; gg < P::G0; gg += P::TPC) {
         Cx<T> a[R0];
 #pragma unroll
         for (int q = 0; q < R0; ++q) a[q] = s[ad(l, q * P::G0 + gg)];
-        dit_group<LOGM, LOGM, P::LG0, true>(a, gg, tw);
+        dit_group<P::R0, 1, true>(a, gg, tw);
         const int xr = gg - g.t0[0];
 #pragma unroll
         for (int p = 0; p < R0 / 2; ++p) {
@@ -632,23 +631,23 @@ __global__ void __launch_bounds__(LPC * Plan<LOGM>::TPC) k_row_inverse(const Cx<
 // ---------------------------------------------------------------------------
 // Host-side launch helpers.
 // ---------------------------------------------------------------------------
-template <typename T, int LOGM>
+template <typename T, int ML>
 struct ColCfg {
-    static constexpr int TPC = Plan<LOGM>::TPC;
+    static constexpr int TPC = Plan<ML>::TPC;
     static constexpr int W0 = 256 / TPC < 8 ? 8 : (256 / TPC > 32 ? 32 : 256 / TPC);
-    static constexpr int WMAX = int(98304 / (sizeof(Cx<T>) << LOGM)) < 1 ? 1 : int(98304 / (sizeof(Cx<T>) << LOGM));
+    static constexpr int WMAX = int(98304 / (sizeof(Cx<T>) * ML)) < 1 ? 1 : int(98304 / (sizeof(Cx<T>) * ML));
     static constexpr int W = W0 < WMAX ? W0 : WMAX;
-    static constexpr size_t SMEM = sizeof(Cx<T>) * (((size_t)1 << LOGM) * (W + 1));
+    static constexpr size_t SMEM = sizeof(Cx<T>) * (((size_t)ML) * (W + 1));
 };
 
-template <typename T, int LOGM>
+template <typename T, int ML>
 struct RowCfg {
-    static constexpr int TPC = Plan<LOGM>::TPC;
+    static constexpr int TPC = Plan<ML>::TPC;
     static constexpr int L0 = 256 / TPC < 1 ? 1 : (256 / TPC > 32 ? 32 : 256 / TPC);
-    static constexpr int LD = (1 << LOGM) + (1 << LOGM) / 16;
+    static constexpr int LD = ML + ML / 16;
     static constexpr int LMAX = int(98304 / (sizeof(Cx<T>) * LD)) < 1 ? 1 : int(98304 / (sizeof(Cx<T>) * LD));
     static constexpr int LPC = L0 < LMAX ? L0 : LMAX;
-    static constexpr size_t SMEM = sizeof(Cx<T>) * (((size_t)1 << LOGM) + (size_t)LPC * LD);
+    static constexpr size_t SMEM = sizeof(Cx<T>) * (((size_t)ML) + (size_t)LPC * LD);
 };
 
 }  // namespace pk
@@ -688,16 +687,16 @@ inline lgf_status set_smem(lgf_ctx *ctx, K kern, size_t smem)
     return LGF_OK;
 }
 
-template <typename T, int LOGM>
+template <typename T, int ML>
 lgf_status row_forward_m(lgf_ctx *ctx, const PoissonGeom &g, const T *f, Cx<T> *A, const Cx<T> *tw, int nfields,
                          int lb, int dense_ld, cudaStream_t s)
 {
-    using C = RowCfg<T, LOGM>;
-    auto kern = k_row_forward<T, LOGM, C::LPC, true>;
+    using C = RowCfg<T, ML>;
+    auto kern = k_row_forward<T, ML, C::LPC, true>;
     if (dense_ld) {
         // full dense rows: only the FP64 spectrum build
         if constexpr (sizeof(T) == 8)
-            kern = k_row_forward<T, LOGM, C::LPC, false>;
+            kern = k_row_forward<T, ML, C::LPC, false>;
         else
             return fail(ctx, LGF_EINVAL, "row forward: FP32 dense rows");
     } else if (g.s0[0] < 0 || 2 * (g.s0[0] + g.Ls[0]) > g.M[0]) {
@@ -714,12 +713,12 @@ lgf_status row_forward_m(lgf_ctx *ctx, const PoissonGeom &g, const T *f, Cx<T> *
     return LGF_OK;
 }
 
-template <typename T, int LOGM>
+template <typename T, int ML>
 lgf_status row_inverse_m(lgf_ctx *ctx, const PoissonGeom &g, const Cx<T> *A, T *u, const Cx<T> *tw, int nfields,
                          int lb, cudaStream_t s)
 {
-    using C = RowCfg<T, LOGM>;
-    auto kern = k_row_inverse<T, LOGM, C::LPC>;
+    using C = RowCfg<T, ML>;
+    auto kern = k_row_inverse<T, ML, C::LPC>;
     if (g.t0[0] < 0 || 2 * (g.t0[0] + g.Lt[0]) > g.M[0])
         return fail(ctx, LGF_EINVAL, "row inverse: target beyond half the transform length");
     lgf_status st = set_smem(ctx, kern, C::SMEM);
@@ -733,17 +732,17 @@ lgf_status row_inverse_m(lgf_ctx *ctx, const PoissonGeom &g, const Cx<T> *A, T *
     return LGF_OK;
 }
 
-template <typename T, int LOGM>
+template <typename T, int ML>
 lgf_status col_forward_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out, int lo, int n,
                          int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane, int64_t in_field,
                          int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
 {
-    using C = ColCfg<T, LOGM>;
-    auto kern = k_col_forward<T, LOGM, C::W, true>;
-    if (lo + n > (1 << LOGM) / 2) {
+    using C = ColCfg<T, ML>;
+    auto kern = k_col_forward<T, ML, C::W, true>;
+    if (lo + n > ML / 2) {
         // full-length input: only the FP64 spectrum build's z pass
         if constexpr (sizeof(T) == 8)
-            kern = k_col_forward<T, LOGM, C::W, false>;
+            kern = k_col_forward<T, ML, C::W, false>;
         else
             return fail(ctx, LGF_EINVAL, "column forward: FP32 input beyond half the transform length");
     }
@@ -758,14 +757,14 @@ lgf_status col_forward_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx
     return LGF_OK;
 }
 
-template <typename T, int LOGM>
+template <typename T, int ML>
 lgf_status col_inverse_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out, int lo, int n,
                          int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane, int64_t in_field,
                          int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
 {
-    using C = ColCfg<T, LOGM>;
-    auto kern = k_col_inverse<T, LOGM, C::W>;
-    if (lo < 0 || lo + n > (1 << LOGM) / 2) return fail(ctx, LGF_EINVAL, "column inverse: rows beyond half the length");
+    using C = ColCfg<T, ML>;
+    auto kern = k_col_inverse<T, ML, C::W>;
+    if (lo < 0 || lo + n > ML / 2) return fail(ctx, LGF_EINVAL, "column inverse: rows beyond half the length");
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
     dim3 grid(col_ctas<C::W>(K, nplanes), nfields);
@@ -777,12 +776,12 @@ lgf_status col_inverse_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx
     return LGF_OK;
 }
 
-template <typename T, int LOGM>
+template <typename T, int ML>
 lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw, int nfields,
                           cudaStream_t s)
 {
-    using C = ColCfg<T, LOGM>;
-    auto kern = k_col_convolve<T, LOGM, C::W>;
+    using C = ColCfg<T, ML>;
+    auto kern = k_col_convolve<T, ML, C::W>;
     if (g.s0[2] < 0 || g.t0[2] < 0 || 2 * (g.s0[2] + g.Ls[2]) > g.M[2] || 2 * (g.t0[2] + g.Lt[2]) > g.M[2])
         return fail(ctx, LGF_EINVAL, "z pass: planes beyond half the transform length");
     lgf_status st = set_smem(ctx, kern, C::SMEM);
@@ -796,24 +795,23 @@ lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T 
     return LGF_OK;
 }
 
-inline int ilog2(int v)
-{
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-}
-
-#define LGF_DISPATCH_LOGM(LOGM_RT, CALL)                                        \
-    switch (LOGM_RT) {                                                          \
-    case 5: { constexpr int LM = 5; return CALL; }                              \
-    case 6: { constexpr int LM = 6; return CALL; }                              \
-    case 7: { constexpr int LM = 7; return CALL; }                              \
-    case 8: { constexpr int LM = 8; return CALL; }                              \
-    case 9: { constexpr int LM = 9; return CALL; }                              \
-    case 10: { constexpr int LM = 10; return CALL; }                            \
-    case 11: { constexpr int LM = 11; return CALL; }                            \
-    case 12: { constexpr int LM = 12; return CALL; }                            \
-    default: return fail(ctx, LGF_EUNSUPPORTED, "transform length outside 32..4096"); \
+#define LGF_DISPATCH_ML(M_RT, CALL)                                             \
+    switch (M_RT) {                                                             \
+    case 32: { constexpr int LM = 32; return CALL; }                            \
+    case 64: { constexpr int LM = 64; return CALL; }                            \
+    case 96: { constexpr int LM = 96; return CALL; }                            \
+    case 128: { constexpr int LM = 128; return CALL; }                          \
+    case 192: { constexpr int LM = 192; return CALL; }                          \
+    case 256: { constexpr int LM = 256; return CALL; }                          \
+    case 384: { constexpr int LM = 384; return CALL; }                          \
+    case 512: { constexpr int LM = 512; return CALL; }                          \
+    case 768: { constexpr int LM = 768; return CALL; }                          \
+    case 1024: { constexpr int LM = 1024; return CALL; }                        \
+    case 1536: { constexpr int LM = 1536; return CALL; }                        \
+    case 2048: { constexpr int LM = 2048; return CALL; }                        \
+    case 3072: { constexpr int LM = 3072; return CALL; }                        \
+    case 4096: { constexpr int LM = 4096; return CALL; }                        \
+    default: return fail(ctx, LGF_EUNSUPPORTED, "transform length not 2^k or 3*2^k in 32..4096"); \
     }
 
 }  // namespace pk
@@ -822,14 +820,14 @@ template <typename T>
 lgf_status launch_row_forward(lgf_ctx *ctx, const PoissonGeom &g, const T *f, Cx<T> *A, const Cx<T> *tw, int nfields,
                               int lb, int dense_ld, cudaStream_t s)
 {
-    LGF_DISPATCH_LOGM(pk::ilog2(g.M[0]), (pk::row_forward_m<T, LM>(ctx, g, f, A, tw, nfields, lb, dense_ld, s)));
+    LGF_DISPATCH_ML(g.M[0], (pk::row_forward_m<T, LM>(ctx, g, f, A, tw, nfields, lb, dense_ld, s)));
 }
 
 template <typename T>
 lgf_status launch_row_inverse(lgf_ctx *ctx, const PoissonGeom &g, const Cx<T> *A, T *u, const Cx<T> *tw, int nfields,
                               int lb, cudaStream_t s)
 {
-    LGF_DISPATCH_LOGM(pk::ilog2(g.M[0]), (pk::row_inverse_m<T, LM>(ctx, g, A, u, tw, nfields, lb, s)));
+    LGF_DISPATCH_ML(g.M[0], (pk::row_inverse_m<T, LM>(ctx, g, A, u, tw, nfields, lb, s)));
 }
 
 template <typename T>
@@ -837,7 +835,7 @@ lgf_status launch_col_forward(lgf_ctx *ctx, int M, int K, int nplanes, int nfiel
                               int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
                               int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
 {
-    LGF_DISPATCH_LOGM(pk::ilog2(M), (pk::col_forward_m<T, LM>(ctx, K, nplanes, nfields, in, out, lo, n, rs, os,
+    LGF_DISPATCH_ML(M, (pk::col_forward_m<T, LM>(ctx, K, nplanes, nfields, in, out, lo, n, rs, os,
                                                                in_plane, out_plane, in_field, out_field, tw, s,
                                                                name)));
 }
@@ -847,7 +845,7 @@ lgf_status launch_col_inverse(lgf_ctx *ctx, int M, int K, int nplanes, int nfiel
                               int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
                               int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
 {
-    LGF_DISPATCH_LOGM(pk::ilog2(M), (pk::col_inverse_m<T, LM>(ctx, K, nplanes, nfields, in, out, lo, n, rs, os,
+    LGF_DISPATCH_ML(M, (pk::col_inverse_m<T, LM>(ctx, K, nplanes, nfields, in, out, lo, n, rs, os,
                                                                in_plane, out_plane, in_field, out_field, tw, s,
                                                                name)));
 }
@@ -856,7 +854,7 @@ template <typename T>
 lgf_status launch_col_convolve(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw,
                                int nfields, cudaStream_t s)
 {
-    LGF_DISPATCH_LOGM(pk::ilog2(g.M[2]), (pk::col_convolve_m<T, LM>(ctx, g, B, spec, tw, nfields, s)));
+    LGF_DISPATCH_ML(g.M[2], (pk::col_convolve_m<T, LM>(ctx, g, B, spec, tw, nfields, s)));
 }
 
 }  // namespace lgf
