@@ -138,3 +138,50 @@ def test_invalid_arguments(ctx32):
     assert e.value.status == 5
     with pytest.raises(ValueError):
         ctx32.poisson_apply(b, [[0, 0, 0]], [[0, 0, 0]], f.double(), u)
+
+
+def _box_lengths(p):
+    """Transform lengths the library's plan picks for this problem (smallest of
+    2^k, 3*2^k in 32..4096 at or above 2L - 1 per axis)."""
+    sizes = (32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096)
+    allc = np.concatenate([p.src, p.tgt])
+    L = (allc.max(0) - allc.min(0) + 1) * p.b
+    return [next(m for m in sizes if m >= 2 * l - 1) for l in L]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("b,ext,lengths", [(16, (3, 2, 5), (96, 64, 192)), (8, (5, 3, 1), (96, 64, 32)),
+                                           (16, (6, 3, 2), (192, 96, 64))])
+def test_mixed_radix_lengths_every_point(prec, b, ext, lengths, ctx64, ctx32, oracle):
+    """Sparse block sets spanning boxes whose transform lengths include
+    3 * 2^k (radix-12 last stage) on every axis position: every target point
+    against the oracle."""
+    ctx = ctx64 if prec == "f64" else ctx32
+    ex, ey, ez = ext
+    src = np.array([[0, 0, 0], [ex - 1, ey - 1, ez - 1], [ex // 2, 0, ez - 1]], dtype=np.int32)
+    tgt = np.array([[ex - 1, 0, 0], [0, ey - 1, ez - 1], [ex // 2, ey - 1, 0]], dtype=np.int32)
+    rng = np.random.default_rng(7)
+    p = li.Problem("mixed", b, src, tgt, rng.uniform(-1, 1, size=(1, 1, src.shape[0], b ** 3)))
+    assert tuple(_box_lengths(p)) == lengths
+    got = run_poisson(ctx, p)
+    ref = oracle_fields(oracle, p)
+    assert rel_linf(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mixed_radix_long_lengths_sampled(prec, ctx64, ctx32, oracle):
+    """Lengths 768 and 384 (three-stage plans with a radix-12 last stage) on a
+    sparse set; 400 sampled targets against the oracle."""
+    ctx = ctx64 if prec == "f64" else ctx32
+    b = 32
+    src = np.array([[0, 0, 0], [5, 0, 1], [2, 4, 0], [11, 1, 1]], dtype=np.int32)
+    tgt = np.array([[0, 0, 0], [6, 1, 1], [11, 0, 0], [3, 1, 1]], dtype=np.int32)
+    rng = np.random.default_rng(8)
+    f = rng.uniform(-1, 1, size=(1, 1, src.shape[0], b ** 3))
+    p = li.Problem("diag", b, src, tgt, f)
+    assert tuple(_box_lengths(p)) == (768, 384, 128)
+    got = run_poisson(ctx, p).reshape(-1)
+    pts = oracle.block_points(b, tgt)
+    idx = rng.choice(pts.shape[0], size=400, replace=False)
+    ref = oracle.poisson_direct(b, src, f[0, 0], pts[idx], R=64)
+    assert rel_linf(got[idx], ref) < TOL[prec]
