@@ -151,8 +151,8 @@ def make_workload(name: str):
     raise ValueError(f"unknown workload {name}")
 
 
-# transform lengths of the library's plans: 2^k and 3 * 2^k from 32 to 4096
-FFT_SIZES = (32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096)
+# transform lengths of the library's plans: 2^k, 3 * 2^k and 5 * 2^k from 32 to 4096
+FFT_SIZES = (32, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024, 1280, 1536, 2048, 2560, 3072, 4096)
 
 
 def geometry(p):

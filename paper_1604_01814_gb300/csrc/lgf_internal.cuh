@@ -18,7 +18,7 @@ constexpr int kMaxFft = 4096;        // largest transform length per axis
 constexpr int kMinTableRadius = 24;  // expansion error at |n| > 24 is below 1e-9 relative
 
 // --------------------------------------------------------------------------
-// Transform lengths: 2^k and 3 * 2^k from 32 to 4096.
+// Transform lengths: 2^k, 3 * 2^k and 5 * 2^k from 32 to 4096.
 // --------------------------------------------------------------------------
 int next_fft_size(int n);   // smallest supported length >= n
 // --------------------------------------------------------------------------

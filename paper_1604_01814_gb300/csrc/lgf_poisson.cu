@@ -31,8 +31,9 @@ namespace lgf {
 
 int next_fft_size(int n)
 {
-    // 2^k and 3 * 2^k: the box pays at most 1.5x its extent per axis
-    static const int sizes[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
+    // 2^k, 3 * 2^k and 5 * 2^k: the box pays at most 1.34x its extent per axis
+    static const int sizes[] = {32,  64,  80,  96,   128,  160,  192,  256,  320,  384,
+                                512, 640, 768, 1024, 1280, 1536, 2048, 2560, 3072, 4096};
     for (int m : sizes)
         if (m >= n) return m;
     return 2 * kMaxFft;   // beyond the largest supported length: the plan rejects it

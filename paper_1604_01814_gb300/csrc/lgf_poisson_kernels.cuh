@@ -1,7 +1,7 @@
 // Pass kernels of the Poisson apply, specialised on the transform length.
 //
-// Every length M = 2^k or 3 * 2^k (32..4096) has a fixed plan of two or three
-// DIF stages (radix <= 16), see Plan below.  A line (a column of W adjacent kx
+// Every length M = 2^k, 3 * 2^k or 5 * 2^k (32..4096) has a fixed plan of two
+// or three DIF stages (radix <= 20), see Plan below.  A line (a column of W adjacent kx
 // values, or one packed pair of x rows) is handled by TPC threads:
 //   - the first forward stage loads its operands straight from global memory
 //     into registers (all loads of a thread in flight together), does the
@@ -21,9 +21,10 @@ namespace pk {
 
 constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 
-// Stage plan of a length M (2^k or 3 * 2^k, 32..4096): a first stage of radix
-// R0, for M >= 384 a middle stage of radix R1 (R0, R1 powers of two), and a
-// last stage of radix RL (16, 8 or 4; 12 when M = 3 * 2^k).  Every stage
+// Stage plan of a length M (2^k, 3 * 2^k or 5 * 2^k, 32..4096): a first stage
+// of radix R0, for M >= 320 a middle stage of radix R1 (R0, R1 powers of two),
+// and a last stage of radix RL (16, 8 or 4; 12 when M = 3 * 2^k, 20 when
+// M = 5 * 2^k).  Every stage
 // before the last splits off a power of two, so its twiddle index stays
 // j q M/N with M/N a power of two.  TPC threads share a line: the greatest
 // common divisor of the stages' group counts, so that every thread owns a
@@ -31,15 +32,20 @@ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 template <int ML>
 struct Plan {
     static constexpr int M = ML;
-    static constexpr int R0 = M == 32 || M == 64 || M == 96 || M == 384 || M == 512 || M == 768 ? 8 : 16;
-    static constexpr int R1 = M == 384 ? 4 : M == 512 || M == 768 || M == 1024 || M == 1536 ? 8
+    static constexpr int R0 = M == 80 || M == 320 ? 4
+                            : M == 32 || M == 64 || M == 96 || M == 160 || M == 384 || M == 512 || M == 640 ||
+                                      M == 768 || M == 1280
+                                  ? 8
+                                  : 16;
+    static constexpr int R1 = M == 320 || M == 384 || M == 640 ? 4
+                            : M == 512 || M == 768 || M == 1024 || M == 1280 || M == 1536 || M == 2560 ? 8
                             : M == 2048 || M == 3072 || M == 4096 ? 16 : 1;
     static constexpr int RL = M / (R0 * R1);
     static constexpr int NST = R1 > 1 ? 3 : 2;
     static constexpr int N1 = M / R0;                             // sub-problem size entering stage 1
     static constexpr int G0 = M / R0, G1 = M / R1, GL = M / RL;   // groups per stage
     static constexpr int TPC = cgcd(cgcd(G0, NST == 3 ? G1 : G0), GL);
-    static_assert(R0 * R1 * RL == M && RL <= 16 && RL >= 4, "plan must cover the length");
+    static_assert(R0 * R1 * RL == M && RL <= 20 && RL >= 4, "plan must cover the length");
     static_assert(G0 % TPC == 0 && G1 % TPC == 0 && GL % TPC == 0, "whole groups per thread");
 };
 
@@ -799,6 +805,12 @@ lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T 
     switch (M_RT) {                                                             \
     case 32: { constexpr int LM = 32; return CALL; }                            \
     case 64: { constexpr int LM = 64; return CALL; }                            \
+    case 80: { constexpr int LM = 80; return CALL; }                            \
+    case 160: { constexpr int LM = 160; return CALL; }                          \
+    case 320: { constexpr int LM = 320; return CALL; }                          \
+    case 640: { constexpr int LM = 640; return CALL; }                          \
+    case 1280: { constexpr int LM = 1280; return CALL; }                        \
+    case 2560: { constexpr int LM = 2560; return CALL; }                        \
     case 96: { constexpr int LM = 96; return CALL; }                            \
     case 128: { constexpr int LM = 128; return CALL; }                          \
     case 192: { constexpr int LM = 192; return CALL; }                          \
@@ -811,7 +823,7 @@ lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T 
     case 2048: { constexpr int LM = 2048; return CALL; }                        \
     case 3072: { constexpr int LM = 3072; return CALL; }                        \
     case 4096: { constexpr int LM = 4096; return CALL; }                        \
-    default: return fail(ctx, LGF_EUNSUPPORTED, "transform length not 2^k or 3*2^k in 32..4096"); \
+    default: return fail(ctx, LGF_EUNSUPPORTED, "transform length not 2^k, 3*2^k or 5*2^k in 32..4096"); \
     }
 
 }  // namespace pk

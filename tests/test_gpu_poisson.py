@@ -142,20 +142,20 @@ def test_invalid_arguments(ctx32):
 
 def _box_lengths(p):
     """Transform lengths the library's plan picks for this problem (smallest of
-    2^k, 3*2^k in 32..4096 at or above 2L - 1 per axis)."""
-    sizes = (32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096)
+    2^k, 3*2^k, 5*2^k in 32..4096 at or above 2L - 1 per axis)."""
+    sizes = (32, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024, 1280, 1536, 2048, 2560, 3072, 4096)
     allc = np.concatenate([p.src, p.tgt])
     L = (allc.max(0) - allc.min(0) + 1) * p.b
     return [next(m for m in sizes if m >= 2 * l - 1) for l in L]
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("b,ext,lengths", [(16, (3, 2, 5), (96, 64, 192)), (8, (5, 3, 1), (96, 64, 32)),
-                                           (16, (6, 3, 2), (192, 96, 64))])
+@pytest.mark.parametrize("b,ext,lengths", [(16, (3, 2, 5), (96, 64, 160)), (8, (5, 3, 1), (80, 64, 32)),
+                                           (16, (6, 3, 2), (192, 96, 64)), (16, (2, 5, 3), (64, 160, 96))])
 def test_mixed_radix_lengths_every_point(prec, b, ext, lengths, ctx64, ctx32, oracle):
     """Sparse block sets spanning boxes whose transform lengths include
-    3 * 2^k (radix-12 last stage) on every axis position: every target point
-    against the oracle."""
+    3 * 2^k or 5 * 2^k (radix-12 or radix-20 last stage) on every axis
+    position: every target point against the oracle."""
     ctx = ctx64 if prec == "f64" else ctx32
     ex, ey, ez = ext
     src = np.array([[0, 0, 0], [ex - 1, ey - 1, ez - 1], [ex // 2, 0, ez - 1]], dtype=np.int32)
@@ -169,17 +169,20 @@ def test_mixed_radix_lengths_every_point(prec, b, ext, lengths, ctx64, ctx32, or
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_mixed_radix_long_lengths_sampled(prec, ctx64, ctx32, oracle):
-    """Lengths 768 and 384 (three-stage plans with a radix-12 last stage) on a
-    sparse set; 400 sampled targets against the oracle."""
+@pytest.mark.parametrize("src,tgt,lengths", [
+    ([[0, 0, 0], [5, 0, 1], [2, 4, 0], [11, 1, 1]], [[0, 0, 0], [6, 1, 1], [11, 0, 0], [3, 1, 1]], (768, 320, 128)),
+    ([[0, 0, 0], [9, 5, 1], [4, 2, 0]], [[9, 0, 0], [0, 5, 1], [5, 3, 1]], (640, 384, 128))])
+def test_mixed_radix_long_lengths_sampled(prec, src, tgt, lengths, ctx64, ctx32, oracle):
+    """Lengths 320 to 768 (three-stage plans with a radix-12 or radix-20 last
+    stage) on sparse sets; 400 sampled targets against the oracle."""
     ctx = ctx64 if prec == "f64" else ctx32
     b = 32
-    src = np.array([[0, 0, 0], [5, 0, 1], [2, 4, 0], [11, 1, 1]], dtype=np.int32)
-    tgt = np.array([[0, 0, 0], [6, 1, 1], [11, 0, 0], [3, 1, 1]], dtype=np.int32)
+    src = np.array(src, dtype=np.int32)
+    tgt = np.array(tgt, dtype=np.int32)
     rng = np.random.default_rng(8)
     f = rng.uniform(-1, 1, size=(1, 1, src.shape[0], b ** 3))
-    p = li.Problem("diag", b, src, tgt, f)
-    assert tuple(_box_lengths(p)) == (768, 384, 128)
+    p = li.Problem("sparse", b, src, tgt, f)
+    assert tuple(_box_lengths(p)) == lengths
     got = run_poisson(ctx, p).reshape(-1)
     pts = oracle.block_points(b, tgt)
     idx = rng.choice(pts.shape[0], size=400, replace=False)
