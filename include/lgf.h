@@ -196,9 +196,8 @@ typedef struct {
    other problem shares its group) and the groups that read only batch inputs
    are independent units: they are spread over up to 4 concurrent branches
    (context streams forked from and joined back to the caller's stream, each
-   with its own scratch), longest first onto the least loaded branch; the
-   branch with the longest unit runs at the greatest stream priority so that
-   the critical path is scheduled first.  Groups of several
+   with its own scratch), longest first onto the least loaded branch.
+   Groups of several
    POISSON_THEN_INTFACTOR problems run after the branches join.  On a
    non-default stream the whole batch is captured once into a CUDA graph,
    and later calls with an identical batch (same block lists, pointers,

@@ -699,15 +699,9 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         if ((st = intf_prepare_scratch(ctx, groups[k].plan, groups[k].nf, (int)groups[k].jobs.size())) != LGF_OK)
             return st;
     if (nb > 1) {
-        // branch 0 carries the longest unit (the critical path): its stream
-        // has the greatest priority, so its CTAs are scheduled first and the
-        // other branches fill the SMs it leaves idle
         if (!ctx->ev_fork) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-        int least = 0, greatest = 0;
-        LGF_CUDA(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest));
         for (int b = 0; b < nb; ++b) {
-            if (!ctx->br[b])
-                LGF_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->br[b], cudaStreamNonBlocking, b == 0 ? greatest : least));
+            if (!ctx->br[b]) LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->br[b], cudaStreamNonBlocking));
             if (!ctx->ev_join[b]) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming));
         }
     }

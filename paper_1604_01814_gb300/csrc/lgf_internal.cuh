@@ -145,8 +145,7 @@ struct lgf_ctx {
     lgf::Scratch scr[lgf::kBranches];
     lgf::Scratch *cur = &scr[0];
 
-    // branch streams (branch 0, the critical path, at the greatest priority)
-    // and the fork/join events on the caller's stream
+    // branch streams and the fork/join events on the caller's stream
     cudaStream_t br[lgf::kBranches] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[lgf::kBranches] = {};
