@@ -22,7 +22,8 @@ namespace pk {
 constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 
 // Stage plan of a length M (2^k, 3 * 2^k or 5 * 2^k, 32..4096): a first stage
-// of radix R0, for M >= 320 a middle stage of radix R1 (R0, R1 powers of two),
+// of radix R0, for M >= 512 and most 3 * 2^k, 5 * 2^k a middle stage of radix
+// R1 (R0, R1 powers of two; the middle stage keeps more threads per line),
 // and a last stage of radix RL (16, 8 or 4; 12 when M = 3 * 2^k, 20 when
 // M = 5 * 2^k).  Every stage
 // before the last splits off a power of two, so its twiddle index stays
@@ -32,12 +33,13 @@ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 template <int ML>
 struct Plan {
     static constexpr int M = ML;
-    static constexpr int R0 = M == 80 || M == 320 ? 4
-                            : M == 32 || M == 64 || M == 96 || M == 160 || M == 384 || M == 512 || M == 640 ||
-                                      M == 768 || M == 1280
+    static constexpr int R0 = M == 80 || M == 96 || M == 192 || M == 320 ? 4
+                            : M == 32 || M == 64 || M == 160 || M == 384 || M == 512 || M == 640 || M == 768 ||
+                                      M == 1280
                                   ? 8
                                   : 16;
-    static constexpr int R1 = M == 320 || M == 384 || M == 640 ? 4
+    static constexpr int R1 = M == 96 ? 2
+                            : M == 192 || M == 320 || M == 384 || M == 640 ? 4
                             : M == 512 || M == 768 || M == 1024 || M == 1280 || M == 1536 || M == 2560 ? 8
                             : M == 2048 || M == 3072 || M == 4096 ? 16 : 1;
     static constexpr int RL = M / (R0 * R1);
