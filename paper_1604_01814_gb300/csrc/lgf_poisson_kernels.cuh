@@ -333,10 +333,10 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
 // lie in [0, M/2): the first stage skips its zero upper inputs and the last
 // stage forms only its lower outputs.
 // Resident CTAs per SM that the register allocation must allow (FP32 at the
-// common lengths 256 and 512: 32 and 24 warps).
+// common lengths 256, 384 and 512: 32, 24 and 24 warps).
 template <typename T, int ML>
 struct ConvOcc {
-    static constexpr int value = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 512 ? 3 : 1) : 1;
+    static constexpr int value = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 384 || ML == 512 ? 3 : 1) : 1;
 };
 
 template <typename T, int ML, int W>
