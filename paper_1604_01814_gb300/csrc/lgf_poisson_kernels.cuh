@@ -333,10 +333,11 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
 // lie in [0, M/2): the first stage skips its zero upper inputs and the last
 // stage forms only its lower outputs.
 // Resident CTAs per SM that the register allocation must allow (FP32 at the
-// common lengths 256, 384 and 512: 32, 24 and 24 warps).
+// lengths 256 (32 warps), 320, 384 and 512 (24 warps) and the long mixed
+// lengths (2 CTAs); no spills).
 template <typename T, int ML>
 struct ConvOcc {
-    static constexpr int value = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 384 || ML == 512 ? 3 : 1) : 1;
+    static constexpr int value = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 320 || ML == 384 || ML == 512 ? 3 : ML == 640 || ML == 1536 || ML == 2560 || ML == 3072 ? 2 : 1) : 1;
 };
 
 template <typename T, int ML, int W>
