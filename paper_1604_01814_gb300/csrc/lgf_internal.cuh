@@ -35,6 +35,11 @@ struct PoissonGeom {
     int nbs[3], nbt[3]; // region extents in blocks
     const int *srcmap;  // [nbs_z][nbs_y][nbs_x] -> source block index or -1
     const int *tgtmap;  // [nbt_z][nbt_y][nbt_x] -> target block index or -1
+    // row-block occupancy per plane block: bit y of [nbs_z] (source) and
+    // [nbt_z] (target) set where some block lies along x in row block y;
+    // nullptr when every row block is occupied or a region has more than 64
+    // row blocks
+    const unsigned long long *srcrow, *tgtrow;
     int64_t fstride;    // elements per field in f (nsrc * b^3)
     int64_t ustride;    // elements per field in u (ntgt * b^3)
     int64_t Astride;    // complex elements per field in scratch A
@@ -49,6 +54,7 @@ struct PoissonPlan {
     std::vector<int32_t> src, tgt;   // block coordinates, for cache matching
     PoissonGeom g{};
     int *srcmap_dev = nullptr, *tgtmap_dev = nullptr;
+    unsigned long long *srcrow_dev = nullptr, *tgtrow_dev = nullptr;
     int64_t A_elems = 0, B_elems = 0; // complex elements per field
     ~PoissonPlan();
 };

@@ -43,6 +43,8 @@ PoissonPlan::~PoissonPlan()
 {
     cudaFree(srcmap_dev);
     cudaFree(tgtmap_dev);
+    cudaFree(srcrow_dev);
+    cudaFree(tgtrow_dev);
 }
 
 namespace {
@@ -101,16 +103,18 @@ lgf_status run_passes(lgf_ctx *ctx, const PoissonGeom &g, const T *f, T *u, Cx<T
     const int K = g.Kx, My = g.M[1], Mz = g.M[2];
     const int64_t planeA = (int64_t)g.ldA_y * K, planeB = (int64_t)My * K;
     if ((st = launch_row_forward<T>(ctx, g, f, A, twx, nf, lb, dense_ld, s)) != LGF_OK) return st;
+    const pk::RowFlags fsrc{spectrum_mode ? nullptr : g.srcrow, lb};
+    const pk::RowFlags ftgt{g.tgtrow, lb};
     if ((st = launch_col_forward<T>(ctx, My, K, g.Ls[2], nf, A, B, g.s0[1], g.Ls[1], K, K, planeA, planeB, g.Astride,
-                                    g.Bstride, twy, s, spectrum_mode ? "spectrum_y_forward" : "poisson_y_forward")) !=
-        LGF_OK)
+                                    g.Bstride, twy, fsrc, s,
+                                    spectrum_mode ? "spectrum_y_forward" : "poisson_y_forward")) != LGF_OK)
         return st;
     if (spectrum_mode)
         return launch_col_forward<T>(ctx, Mz, K, My, nf, B, B, 0, Mz, planeB, planeB, K, K, g.Bstride, g.Bstride, twz,
-                                     s, "spectrum_z_forward");
+                                     pk::RowFlags{}, s, "spectrum_z_forward");
     if ((st = launch_col_convolve<T>(ctx, g, B, spec, twz, nf, s)) != LGF_OK) return st;
     if ((st = launch_col_inverse<T>(ctx, My, K, g.Lt[2], nf, B, A, g.t0[1], g.Lt[1], K, K, planeB, planeA, g.Bstride,
-                                    g.Astride, twy, s, "poisson_y_inverse")) != LGF_OK)
+                                    g.Astride, twy, ftgt, s, "poisson_y_inverse")) != LGF_OK)
         return st;
     return launch_row_inverse<T>(ctx, g, A, u, twx, nf, lb, s);
 }
@@ -210,6 +214,33 @@ lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockse
     LGF_CUDA(ctx, cudaMemcpy(plan->tgtmap_dev, tmap.data(), tmap.size() * sizeof(int), cudaMemcpyHostToDevice));
     g.srcmap = plan->srcmap_dev;
     g.tgtmap = plan->tgtmap_dev;
+    // row blocks (y, z) with no block along x: the x passes skip them and the
+    // y passes neither read nor write their rows
+    auto row_flags = [&](const std::vector<int> &map, const int nb[3], unsigned long long **dev,
+                         const unsigned long long **out) -> lgf_status {
+        *out = nullptr;
+        if (nb[1] > 64) return LGF_OK;
+        std::vector<unsigned long long> f((size_t)nb[2], 0ull);
+        bool all = true;
+        for (int z = 0; z < nb[2]; ++z)
+            for (int y = 0; y < nb[1]; ++y) {
+                bool any = false;
+                for (int x = 0; x < nb[0]; ++x) any = any || map[((size_t)z * nb[1] + y) * nb[0] + x] >= 0;
+                if (any)
+                    f[z] |= 1ull << y;
+                else
+                    all = false;
+            }
+        if (all) return LGF_OK;
+        if (cudaMalloc(dev, f.size() * sizeof(unsigned long long)) != cudaSuccess)
+            return fail(ctx, LGF_ENOMEM, "poisson: row flag allocation failed");
+        LGF_CUDA(ctx, cudaMemcpy(*dev, f.data(), f.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+        *out = *dev;
+        return LGF_OK;
+    };
+    lgf_status rst = row_flags(smap, g.nbs, &plan->srcrow_dev, &g.srcrow);
+    if (rst == LGF_OK) rst = row_flags(tmap, g.nbt, &plan->tgtrow_dev, &g.tgtrow);
+    if (rst != LGF_OK) return rst;
     g.fstride = (int64_t)src->nblocks * b * b * b;
     g.ustride = (int64_t)tgt->nblocks * b * b * b;
         ctx->pplans.push_back(std::move(plan));
