@@ -36,7 +36,8 @@ struct PoissonGeom {
     const int *srcmap;  // [nbs_z][nbs_y][nbs_x] -> source block index or -1
     const int *tgtmap;  // [nbt_z][nbt_y][nbt_x] -> target block index or -1
     // row-block occupancy per plane block: bit y of [nbs_z] (source) and
-    // [nbt_z] (target) set where some block lies along x in row block y;
+    // [nbt_z] (target) set where some block lies along x in row block y (the
+    // x passes skip CTAs in empty row blocks, the y-forward pass their rows);
     // nullptr when every row block is occupied or a region has more than 64
     // row blocks
     const unsigned long long *srcrow, *tgtrow;

@@ -104,7 +104,6 @@ lgf_status run_passes(lgf_ctx *ctx, const PoissonGeom &g, const T *f, T *u, Cx<T
     const int64_t planeA = (int64_t)g.ldA_y * K, planeB = (int64_t)My * K;
     if ((st = launch_row_forward<T>(ctx, g, f, A, twx, nf, lb, dense_ld, s)) != LGF_OK) return st;
     const pk::RowFlags fsrc{spectrum_mode ? nullptr : g.srcrow, lb};
-    const pk::RowFlags ftgt{g.tgtrow, lb};
     if ((st = launch_col_forward<T>(ctx, My, K, g.Ls[2], nf, A, B, g.s0[1], g.Ls[1], K, K, planeA, planeB, g.Astride,
                                     g.Bstride, twy, fsrc, s,
                                     spectrum_mode ? "spectrum_y_forward" : "poisson_y_forward")) != LGF_OK)
@@ -114,7 +113,7 @@ lgf_status run_passes(lgf_ctx *ctx, const PoissonGeom &g, const T *f, T *u, Cx<T
                                      pk::RowFlags{}, s, "spectrum_z_forward");
     if ((st = launch_col_convolve<T>(ctx, g, B, spec, twz, nf, s)) != LGF_OK) return st;
     if ((st = launch_col_inverse<T>(ctx, My, K, g.Lt[2], nf, B, A, g.t0[1], g.Lt[1], K, K, planeB, planeA, g.Bstride,
-                                    g.Astride, twy, ftgt, s, "poisson_y_inverse")) != LGF_OK)
+                                    g.Astride, twy, s, "poisson_y_inverse")) != LGF_OK)
         return st;
     return launch_row_inverse<T>(ctx, g, A, u, twx, nf, lb, s);
 }
@@ -215,7 +214,7 @@ lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockse
     g.srcmap = plan->srcmap_dev;
     g.tgtmap = plan->tgtmap_dev;
     // row blocks (y, z) with no block along x: the x passes skip them and the
-    // y passes neither read nor write their rows
+    // y-forward pass does not read their rows
     auto row_flags = [&](const std::vector<int> &map, const int nb[3], unsigned long long **dev,
                          const unsigned long long **out) -> lgf_status {
         *out = nullptr;

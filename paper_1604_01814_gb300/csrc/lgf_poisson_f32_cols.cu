@@ -8,5 +8,5 @@ template lgf_status launch_col_forward<float>(lgf_ctx *, int, int, int, int, con
                                            pk::RowFlags, cudaStream_t, const char *);
 template lgf_status launch_col_inverse<float>(lgf_ctx *, int, int, int, int, const Cx<float> *, Cx<float> *, int, int,
                                            int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, const Cx<float> *,
-                                           pk::RowFlags, cudaStream_t, const char *);
+                                           cudaStream_t, const char *);
 }  // namespace lgf

@@ -8,5 +8,5 @@ template lgf_status launch_col_forward<double>(lgf_ctx *, int, int, int, int, co
                                            pk::RowFlags, cudaStream_t, const char *);
 template lgf_status launch_col_inverse<double>(lgf_ctx *, int, int, int, int, const Cx<double> *, Cx<double> *, int, int,
                                            int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, const Cx<double> *,
-                                           pk::RowFlags, cudaStream_t, const char *);
+                                           cudaStream_t, const char *);
 }  // namespace lgf

@@ -152,18 +152,17 @@ __device__ __forceinline__ void load_twiddles(Cx<T> *tw, const Cx<T> *__restrict
 // scattered accesses are slower, and they then overlap the rest instead of
 // trailing it.
 // ---------------------------------------------------------------------------
-// Row-block occupancy for the y passes: row y of plane pl (both relative to
-// the region) holds data unless its (z, y) row block has no block along x;
-// bit y >> lb of mask[pl >> lb].
+// Row-block occupancy for the y-forward pass: row y of plane pl (both
+// relative to the source region) holds data unless its (z, y) row block has
+// no block along x (the x-forward pass then skipped it); bit y >> lb of
+// mask[pl >> lb].
 struct RowFlags {
     const unsigned long long *mask = nullptr;   // nullptr: every row holds data
     int lb = 0;
     __device__ __forceinline__ unsigned long long plane(int pl) const { return mask ? mask[pl >> lb] : ~0ull; }
-    // (with a mask every region has at most 64 row blocks, so the shift stays below 64)
-    __device__ __forceinline__ bool row(unsigned long long pm, int y) const
-    {
-        return !mask || ((pm >> (y >> lb)) & 1ull);
-    }
+    // only with a mask: every region then has at most 64 row blocks, so the
+    // shift stays below 64
+    __device__ __forceinline__ bool row(unsigned long long pm, int y) const { return (pm >> (y >> lb)) & 1ull; }
 };
 
 template <int W>
@@ -226,18 +225,32 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_forward(const Cx<T> *
     constexpr int NG0 = P::G0 / P::TPC;
     constexpr int NP = HALF ? R0 / 2 : R0;
     const int64_t istep = (int64_t)P::G0 * rs;
-    const unsigned long long pm = rf.plane(pl);
     Cx<T> a[NG0][R0];
+    if (rf.mask == nullptr) {   // every row holds data (uniform branch)
 #pragma unroll
-    for (int i = 0; i < NG0; ++i) {
-        const int r = t + i * P::TPC - lo;   // data row of digit p = 0
-        int64_t off = (int64_t)r * rs;
+        for (int i = 0; i < NG0; ++i) {
+            const int r = t + i * P::TPC - lo;   // data row of digit p = 0
+            int64_t off = (int64_t)r * rs;
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const int y = r + p * P::G0;
-            const bool ok = live && (unsigned)y < (unsigned)n && rf.row(pm, y);
-            a[i][p] = ok ? ib[off] : Cx<T>{T(0), T(0)};
-            off += istep;
+            for (int p = 0; p < NP; ++p) {
+                const bool ok = live && (unsigned)(r + p * P::G0) < (unsigned)n;
+                a[i][p] = ok ? ib[off] : Cx<T>{T(0), T(0)};
+                off += istep;
+            }
+        }
+    } else {
+        const unsigned long long pm = rf.plane(pl);
+#pragma unroll
+        for (int i = 0; i < NG0; ++i) {
+            const int r = t + i * P::TPC - lo;
+            int64_t off = (int64_t)r * rs;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int y = r + p * P::G0;
+                const bool ok = live && (unsigned)y < (unsigned)n && rf.row(pm, y);
+                a[i][p] = ok ? ib[off] : Cx<T>{T(0), T(0)};
+                off += istep;
+            }
         }
     }
     __syncthreads();   // twiddles
@@ -281,7 +294,7 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
                                                                      int K, int nplanes, int lo, int n, int64_t rs,
                                                                      int64_t os, int64_t in_plane, int64_t out_plane,
                                                                      int64_t in_field, int64_t out_field,
-                                                                     const Cx<T> *__restrict__ twg, RowFlags rf)
+                                                                     const Cx<T> *__restrict__ twg)
 {
     using P = Plan<ML>;
     constexpr int M = P::M;
@@ -323,7 +336,6 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
     }
     constexpr int R0 = P::R0;
     const int64_t ostep = (int64_t)P::G0 * os;
-    const unsigned long long pm = rf.plane(pl);
 #pragma unroll
     for (int g = t; g < P::G0; g += P::TPC) {
         Cx<T> a[R0];
@@ -335,8 +347,7 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
             int64_t off = (int64_t)r * os;
 #pragma unroll
             for (int p = 0; p < R0 / 2; ++p) {
-                const int y = r + p * P::G0;
-                if ((unsigned)y < (unsigned)n && rf.row(pm, y)) ob[off] = a[p];
+                if ((unsigned)(r + p * P::G0) < (unsigned)n) ob[off] = a[p];
                 off += ostep;
             }
         }
@@ -586,7 +597,7 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T>
     const int hp = g.Lt[1] >> 1;
     const int zi = live ? pr / hp : 0, yi = live ? 2 * (pr - zi * hp) : 0;
     // a CTA whose lines all lie in row blocks without target blocks has
-    // nothing to write (the y pass did not write those rows)
+    // nothing to write
     if (g.tgtrow && !__syncthreads_or(live && ((g.tgtrow[zi >> lb] >> (yi >> lb)) & 1ull))) return;
     const int K = g.Kx;
     const Cx<T> *row = A + blockIdx.y * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
@@ -701,8 +712,7 @@ lgf_status launch_col_forward(lgf_ctx *ctx, int M, int K, int nplanes, int nfiel
 template <typename T>
 lgf_status launch_col_inverse(lgf_ctx *ctx, int M, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out,
                               int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
-                              int64_t in_field, int64_t out_field, const Cx<T> *tw, pk::RowFlags rf, cudaStream_t s,
-                              const char *name);
+                              int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name);
 template <typename T>
 lgf_status launch_col_convolve(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw,
                                int nfields, cudaStream_t s);
@@ -795,7 +805,7 @@ lgf_status col_forward_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx
 template <typename T, int ML>
 lgf_status col_inverse_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out, int lo, int n,
                          int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane, int64_t in_field,
-                         int64_t out_field, const Cx<T> *tw, RowFlags rf, cudaStream_t s, const char *name)
+                         int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
 {
     using C = ColCfg<T, ML>;
     auto kern = k_col_inverse<T, ML, C::W>;
@@ -805,7 +815,7 @@ lgf_status col_inverse_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx
     dim3 grid(col_ctas<C::W>(K, nplanes), nfields);
     const int ph = prof_begin(ctx, s, name);
     kern<<<grid, C::W * C::TPC, C::SMEM, s>>>(in, out, K, nplanes, lo, n, rs, os, in_plane, out_plane, in_field,
-                                              out_field, tw, rf);
+                                              out_field, tw);
     LGF_CHECK_LAUNCH(ctx, name);
     prof_end(ctx, s, ph);
     return LGF_OK;
@@ -885,11 +895,10 @@ lgf_status launch_col_forward(lgf_ctx *ctx, int M, int K, int nplanes, int nfiel
 template <typename T>
 lgf_status launch_col_inverse(lgf_ctx *ctx, int M, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out,
                               int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
-                              int64_t in_field, int64_t out_field, const Cx<T> *tw, pk::RowFlags rf, cudaStream_t s,
-                              const char *name)
+                              int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
 {
     LGF_DISPATCH_ML(M, (pk::col_inverse_m<T, LM>(ctx, K, nplanes, nfields, in, out, lo, n, rs, os,
-                                                               in_plane, out_plane, in_field, out_field, tw, rf,
+                                                               in_plane, out_plane, in_field, out_field, tw,
                                                                s, name)));
 }
 
