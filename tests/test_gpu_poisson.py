@@ -188,3 +188,24 @@ def test_mixed_radix_long_lengths_sampled(prec, src, tgt, lengths, ctx64, ctx32,
     idx = rng.choice(pts.shape[0], size=400, replace=False)
     ref = oracle.poisson_direct(b, src, f[0, 0], pts[idx], R=64)
     assert rel_linf(got[idx], ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("nbx,length", [(20, 1280), (24, 1536), (40, 2560), (48, 3072), (64, 4096)])
+def test_longest_lengths_sampled(prec, nbx, length, ctx64, ctx32, oracle):
+    """The long plans up to the largest supported length (4096, a union box of
+    2048 points along x): two source blocks at the ends of a thin box, 300
+    sampled targets against the oracle."""
+    ctx = ctx64 if prec == "f64" else ctx32
+    b = 32
+    src = np.array([[0, 0, 0], [nbx - 1, 0, 0]], dtype=np.int32)
+    tgt = np.array([[nbx // 2, 0, 0], [nbx - 1, 0, 0], [1, 0, 0]], dtype=np.int32)
+    rng = np.random.default_rng(nbx)
+    f = rng.uniform(-1, 1, size=(1, 1, src.shape[0], b ** 3))
+    p = li.Problem("thin", b, src, tgt, f)
+    assert tuple(_box_lengths(p)) == (length, 64, 64)
+    got = run_poisson(ctx, p).reshape(-1)
+    pts = oracle.block_points(b, tgt)
+    idx = rng.choice(pts.shape[0], size=300, replace=False)
+    ref = oracle.poisson_direct(b, src, f[0, 0], pts[idx], R=64)
+    assert rel_linf(got[idx], ref) < TOL[prec]
