@@ -74,6 +74,8 @@ struct IntfPlan {
     int n1 = 0, n2 = 0;       // sizes of the two intermediate block sets
     IntfPass pass[3];
     int *nbr_xy_dev = nullptr; // [n2][(2nr+1)^2] source block at xy offset of each Y2 block, or -1
+    int *xy_items_dev = nullptr; // [n_xy_items][2] Y2 blocks of each fused-pass CTA (second -1: single)
+    int n_xy_items = 0;
     ~IntfPlan();
 };
 

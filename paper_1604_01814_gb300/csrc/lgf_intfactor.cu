@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <tuple>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -30,14 +31,15 @@ extern template lgf_status launch_sep_window<float>(lgf_ctx *, int, int, int, co
 extern template lgf_status launch_sep_window<double>(lgf_ctx *, int, int, int, const SepJobs<double> &, cudaStream_t,
                                                      const int *, int, bool *);
 extern template lgf_status launch_sep_xy<float>(lgf_ctx *, int, int, const SepJobs<float> &, cudaStream_t, const int *,
-                                                int, bool *);
+                                                const int *, int, bool *);
 extern template lgf_status launch_sep_xy<double>(lgf_ctx *, int, int, const SepJobs<double> &, cudaStream_t,
-                                                 const int *, int, bool *);
+                                                 const int *, const int *, int, bool *);
 
 IntfPlan::~IntfPlan()
 {
     for (auto &p : pass) cudaFree(p.nbr_dev);
     cudaFree(nbr_xy_dev);
+    cudaFree(xy_items_dev);
 }
 
 namespace {
@@ -338,6 +340,34 @@ lgf_status intf_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *
                 return fail(ctx, LGF_ENOMEM, "intfactor: neighbour table allocation failed");
             LGF_CUDA(ctx, cudaMemcpy(plan->nbr_xy_dev, nxy.data(), nxy.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
+        // work items of the fused pass: Y2 blocks paired with their +y
+        // neighbour in Y2 where it exists (walking every (x, z) column upwards)
+        std::vector<int> order(y2.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::sort(order.begin(), order.end(), [&](int a, int c) {
+            return std::make_tuple(y2[a][2], y2[a][0], y2[a][1]) < std::make_tuple(y2[c][2], y2[c][0], y2[c][1]);
+        });
+        std::vector<char> used(y2.size(), 0);
+        std::vector<int> items;
+        for (int o : order) {
+            if (used[o]) continue;
+            used[o] = 1;
+            int o2 = -1;
+            auto it = Y2.find(pack(y2[o][0], y2[o][1] + 1, y2[o][2]));
+            if (it != Y2.end() && !used[it->second]) {
+                o2 = it->second;
+                used[o2] = 1;
+            }
+            items.push_back(o);
+            items.push_back(o2);
+        }
+        plan->n_xy_items = (int)(items.size() / 2);
+        if (!items.empty()) {
+            if (cudaMalloc(&plan->xy_items_dev, items.size() * sizeof(int)) != cudaSuccess)
+                return fail(ctx, LGF_ENOMEM, "intfactor: work item allocation failed");
+            LGF_CUDA(ctx,
+                     cudaMemcpy(plan->xy_items_dev, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
     }
         ctx->iplans.push_back(std::move(plan));
     *out = ctx->iplans.back().get();
@@ -464,7 +494,8 @@ static lgf_status run_sep_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, 
             }
             const int ph = prof_begin(ctx, s, "intfactor_pass_xy");
             bool done = false;
-            lgf_status st = launch_sep_xy<T>(ctx, b, pl->n2, jx, s, pl->nbr_xy_dev, nr, &done);
+            lgf_status st = launch_sep_xy<T>(ctx, b, pl->n_xy_items, jx, s, pl->nbr_xy_dev, pl->xy_items_dev, nr,
+                                             &done);
             if (st != LGF_OK) return st;
             if (!done) {
                 prof_end(ctx, s, ph);

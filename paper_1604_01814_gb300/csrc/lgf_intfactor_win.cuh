@@ -207,21 +207,28 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
     }
 }
 
-// Fused x and y passes: stage the (b + 2 RMAX)^2 neighbourhood of NS
-// z-planes of an output block from its 3x3 xy neighbours, run the x stencil
-// into an intermediate [NS][E][b] and then the y stencil to the output.
+// Fused x and y passes.  A CTA owns one output block, or two that are
+// neighbours in y (a pair shares the y halo between them: 2b + 2 RMAX staged
+// rows for 2b outputs instead of 2 (b + 2 RMAX)), and NS z-planes.  It stages
+// the neighbourhood from the xy neighbour blocks, runs the x stencil over
+// every staged row into an intermediate [NS][EY][b] and then the y stencil to
+// the output block(s).
 template <typename T, int LB, int RMAX>
 struct XYCfg {
     static constexpr int b = 1 << LB, E = b + 2 * RMAX;
-    static constexpr int per_plane = E * E + E * b;
+    static constexpr int EY1 = b + 2 * RMAX, EY = 2 * b + 2 * RMAX;   // staged rows: single, pair
+    static constexpr int per_plane = EY * E + EY * b;
     static constexpr int NS0 = 12288 / per_plane;
     static constexpr int NS = NS0 >= 8 ? 8 : NS0 >= 4 ? 4 : NS0 >= 2 ? 2 : 1;
     static constexpr int NSB = NS > b ? b : NS;
     static constexpr size_t SMEM = sizeof(T) * (size_t)NSB * per_plane;
 };
 
+// items: [n][2] output blocks (second -1 for a single block); nbr: for every
+// output block its (2nr+1)^2 xy neighbourhood of source blocks.
 template <typename T, int LB, int RMAX>
-__global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int *__restrict__ nbr, int nr)
+__global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int *__restrict__ nbr,
+                                                const int *__restrict__ items, int nr)
 {
     const SepJob<T> &J = jobs.j[blockIdx.z / jobs.nf];
     const int field = blockIdx.z % jobs.nf;
@@ -229,19 +236,28 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
     const int R = J.R;
     using C = XYCfg<T, LB, RMAX>;
     using VT = typename Vec<T>::V;
-    constexpr int b = C::b, bm = b - 1, NV = Vec<T>::N, NS = C::NSB, HL = RMAX, E = C::E;
+    constexpr int b = C::b, bm = b - 1, NV = Vec<T>::N, NS = C::NSB, HL = RMAX, E = C::E, EY = C::EY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *rg = reinterpret_cast<T *>(smem_raw);       // [NS][E][E]
-    T *im = rg + NS * E * E;                        // [NS][E][b]
-    const int o = blockIdx.x;
+    T *rg = reinterpret_cast<T *>(smem_raw);       // [NS][EY][E]
+    T *im = rg + NS * EY * E;                       // [NS][EY][b]
+    const int o1 = items[2 * blockIdx.x], o2 = items[2 * blockIdx.x + 1];
+    const bool pair = o2 >= 0;                      // uniform over the CTA
+    const int ny = pair ? 2 : 1;
+    const int rows = pair ? C::EY : C::EY1;         // staged rows per plane
     const int s0 = blockIdx.y * NS;
     const int nd = 2 * nr + 1;
-    const int *nb = nbr + (int64_t)o * nd * nd;
+    const int *nb1 = nbr + (int64_t)o1 * nd * nd;
+    const int *nb2 = pair ? nbr + (int64_t)o2 * nd * nd : nb1;
     const T *inf = J.in + field * J.in_stride;
     T *outf = J.out + field * J.out_stride;
+    // plane-local row -> (z-plane, staged row) with compile-time divisors
+    auto split = [&](int row, int &zl, int &yr) {
+        zl = pair ? row / C::EY : row / C::EY1;
+        yr = row - zl * rows;
+    };
     // ---- stage ----
     constexpr int vpr = E / NV;
-    constexpr int total = NS * E * vpr;
+    const int total = NS * rows * vpr;
     constexpr int U = 4;
     for (int base = threadIdx.x; base < total; base += U * 256) {
         VT v[U];
@@ -253,9 +269,14 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
             v[u] = VT{};
             if (it >= total) continue;
             const int row = it / vpr, cv = it - row * vpr;
-            const int ex = cv * NV - HL, ey = row % E - HL, z = s0 + row / E;
-            dst[u] = it * NV;
-            const int bi = nb[((ey + nr * b) >> LB) * nd + ((ex + nr * b) >> LB)];
+            int zl, yr;
+            split(row, zl, yr);
+            const int ex = cv * NV - HL, ey = yr - HL, z = s0 + zl;
+            dst[u] = (zl * EY + yr) * E + cv * NV;
+            // block row of ey relative to the first output block: -nr .. ny - 1 + nr
+            const int dyb = (ey + nr * b) >> LB;
+            const int *nbt = dyb <= 2 * nr ? nb1 + dyb * nd : nb2 + (dyb - 1) * nd;
+            const int bi = nbt[(ex + nr * b) >> LB];
             if (bi >= 0)
                 v[u] = *reinterpret_cast<const VT *>(inf + ((int64_t)bi << (3 * LB)) + (((z << LB) + (ey & bm)) << LB) +
                                                      (ex & bm));
@@ -269,10 +290,13 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
     for (int k = 0; k <= RMAX; ++k) w[k] = k <= R ? wg[k] : T(0);
     __syncthreads();
     // ---- x stencil: every staged row, kV outputs per item ----
-    constexpr int xitems = NS * E * (b / kV);
+    const int xitems = NS * rows * (b / kV);
     for (int it = threadIdx.x; it < xitems; it += 256) {
-        const int xv = it % (b / kV), row = it / (b / kV);   // row = zl * E + y_ext + HL
+        const int xv = it % (b / kV);
+        int zl, yr;
+        split(it / (b / kV), zl, yr);
         const int x0 = xv * kV;
+        const int row = zl * EY + yr;
         const T *r = rg + row * E + x0;                       // staged x_ext = x0 - HL ...
         T acc[kV];
 #pragma unroll
@@ -302,13 +326,14 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
     }
     __syncthreads();
     // ---- y stencil: NV adjacent x, kV consecutive y outputs per item ----
-    constexpr int yitems = NS * (b / NV) * (b / kV);
+    const int ypp = ny * (b / kV);                     // y items per plane and x column
+    const int yitems = NS * (b / NV) * ypp;
     for (int it = threadIdx.x; it < yitems; it += 256) {
         const int xv = it % (b / NV);
-        const int yv = (it / (b / NV)) % (b / kV);
-        const int zl = it / ((b / NV) * (b / kV));
-        const int x = xv * NV, y0 = yv * kV;
-        const T *col = im + (zl * E + y0) * b + x;            // y_ext = y0 - HL ...
+        const int yv = (it / (b / NV)) % ypp;
+        const int zl = it / ((b / NV) * ypp);
+        const int x = xv * NV, y0 = yv * kV;                  // output row among the ny * b
+        const T *col = im + (zl * EY + y0) * b + x;           // y_ext = y0 - HL ...
         T acc[kV][NV];
 #pragma unroll
         for (int v = 0; v < kV; ++v)
@@ -328,19 +353,22 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
             }
         }
         const int z = s0 + zl;
+        const int o = y0 < b ? o1 : o2;
+        const int yl = y0 & bm;
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             VT q;
             T *qq = reinterpret_cast<T *>(&q);
 #pragma unroll
             for (int e = 0; e < NV; ++e) qq[e] = acc[v][e];
-            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((z << LB) + y0 + v) << LB) + x) = q;
+            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((z << LB) + yl + v) << LB) + x) = q;
         }
     }
 }
 
 template <typename T, int LB, int RMAX>
-lgf_status launch_xy_m(lgf_ctx *ctx, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr, int nr)
+lgf_status launch_xy_m(lgf_ctx *ctx, int nitems, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr,
+                       const int *items, int nr)
 {
     using C = XYCfg<T, LB, RMAX>;
     auto kern = k_sep_xy<T, LB, RMAX>;
@@ -348,20 +376,20 @@ lgf_status launch_xy_m(lgf_ctx *ctx, int nout, const SepJobs<T> &jobs, cudaStrea
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
     }
-    dim3 grid(nout, C::b / C::NSB, jobs.n * jobs.nf);
-    kern<<<grid, 256, C::SMEM, s>>>(jobs, nbr, nr);
+    dim3 grid(nitems, C::b / C::NSB, jobs.n * jobs.nf);
+    kern<<<grid, 256, C::SMEM, s>>>(jobs, nbr, items, nr);
     return LGF_OK;
 }
 
 template <typename T, int LB>
-lgf_status launch_xy_r(lgf_ctx *ctx, int rmax, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr,
-                       int nr)
+lgf_status launch_xy_r(lgf_ctx *ctx, int rmax, int nitems, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr,
+                       const int *items, int nr)
 {
     switch (rmax) {
-    case 4: return launch_xy_m<T, LB, 4>(ctx, nout, jobs, s, nbr, nr);
-    case 8: return launch_xy_m<T, LB, 8>(ctx, nout, jobs, s, nbr, nr);
-    case 12: return launch_xy_m<T, LB, 12>(ctx, nout, jobs, s, nbr, nr);
-    default: return launch_xy_m<T, LB, 16>(ctx, nout, jobs, s, nbr, nr);
+    case 4: return launch_xy_m<T, LB, 4>(ctx, nitems, jobs, s, nbr, items, nr);
+    case 8: return launch_xy_m<T, LB, 8>(ctx, nitems, jobs, s, nbr, items, nr);
+    case 12: return launch_xy_m<T, LB, 12>(ctx, nitems, jobs, s, nbr, items, nr);
+    default: return launch_xy_m<T, LB, 16>(ctx, nitems, jobs, s, nbr, items, nr);
     }
 }
 
@@ -410,19 +438,20 @@ inline int window_rmax(const SepJobs<T> &jobs, int b, int nr)
     return rmax;
 }
 
-// Fused x+y pass (S -> Y2 with the (2nr+1)^2 xy neighbour table) for a job list;
-// *done tells whether the window kernels applied.
+// Fused x+y pass (S -> Y2 with the (2nr+1)^2 xy neighbour table, over the
+// single and y-paired output items) for a job list; *done tells whether the
+// window kernels applied.
 template <typename T>
-lgf_status launch_sep_xy(lgf_ctx *ctx, int b, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr,
-                         int nr, bool *done)
+lgf_status launch_sep_xy(lgf_ctx *ctx, int b, int nitems, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr,
+                         const int *items, int nr, bool *done)
 {
     const int rmax = window_rmax(jobs, b, nr);
     *done = rmax > 0;
     if (!*done) return LGF_OK;
     switch (b) {
-    case 8: return win::launch_xy_r<T, 3>(ctx, rmax, nout, jobs, s, nbr, nr);
-    case 16: return win::launch_xy_r<T, 4>(ctx, rmax, nout, jobs, s, nbr, nr);
-    default: return win::launch_xy_r<T, 5>(ctx, rmax, nout, jobs, s, nbr, nr);
+    case 8: return win::launch_xy_r<T, 3>(ctx, rmax, nitems, jobs, s, nbr, items, nr);
+    case 16: return win::launch_xy_r<T, 4>(ctx, rmax, nitems, jobs, s, nbr, items, nr);
+    default: return win::launch_xy_r<T, 5>(ctx, rmax, nitems, jobs, s, nbr, items, nr);
     }
 }
 

@@ -4,6 +4,6 @@
 namespace lgf {
 template lgf_status launch_sep_window<float>(lgf_ctx *, int, int, int, const SepJobs<float> &, cudaStream_t, const int *,
                                          int, bool *);
-template lgf_status launch_sep_xy<float>(lgf_ctx *, int, int, const SepJobs<float> &, cudaStream_t, const int *, int,
-                                     bool *);
+template lgf_status launch_sep_xy<float>(lgf_ctx *, int, int, const SepJobs<float> &, cudaStream_t, const int *,
+                                     const int *, int, bool *);
 }  // namespace lgf

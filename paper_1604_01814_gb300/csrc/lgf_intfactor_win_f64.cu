@@ -4,6 +4,6 @@
 namespace lgf {
 template lgf_status launch_sep_window<double>(lgf_ctx *, int, int, int, const SepJobs<double> &, cudaStream_t, const int *,
                                          int, bool *);
-template lgf_status launch_sep_xy<double>(lgf_ctx *, int, int, const SepJobs<double> &, cudaStream_t, const int *, int,
-                                     bool *);
+template lgf_status launch_sep_xy<double>(lgf_ctx *, int, int, const SepJobs<double> &, cudaStream_t, const int *,
+                                     const int *, int, bool *);
 }  // namespace lgf
