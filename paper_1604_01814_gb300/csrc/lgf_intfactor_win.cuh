@@ -10,6 +10,8 @@
 // Shared-memory traffic per output is (V + 2 RMAX) / V values instead of
 // 2R + 1.
 #pragma once
+#include <type_traits>
+
 #include "lgf_internal.cuh"
 
 namespace lgf {
@@ -29,6 +31,84 @@ struct Vec<double> {
 };
 
 constexpr int kV = 4;   // outputs per thread along the pass axis
+
+// Register copy of the weights w_0 .. w_RMAX (zero past the job's radius).
+// In FP32 each weight is held as the pair (w_k, w_k), the operand of the packed
+// FP32x2 FMA: one instruction forms two lane-wise fma.rn, each rounded exactly
+// as a scalar FFMA, so the packed loops give the scalar loops' bits.
+template <typename T, int RMAX>
+struct WinW {
+    T w[RMAX + 1];
+};
+template <int RMAX>
+struct WinW<float, RMAX> {
+    float2 w[RMAX + 1];
+};
+
+template <typename T, int RMAX>
+__device__ __forceinline__ void load_weights(WinW<T, RMAX> &W, const T *__restrict__ wg, int R)
+{
+#pragma unroll
+    for (int k = 0; k <= RMAX; ++k) {
+        const T v = k <= R ? wg[k] : T(0);
+        if constexpr (std::is_same<T, float>::value) W.w[k] = make_float2(v, v);
+        else W.w[k] = v;
+    }
+}
+
+template <int RMAX>
+__device__ __forceinline__ float wscalar(const WinW<float, RMAX> &W, int k) { return W.w[k].x; }
+template <int RMAX>
+__device__ __forceinline__ double wscalar(const WinW<double, RMAX> &W, int k) { return W.w[k]; }
+
+// kV consecutive outputs along a column of staged inputs (stride st between
+// axis positions; the window starts RMAX before the first output) for the
+// Vec<T>::N adjacent x values of one 16-byte vector.
+template <int RMAX>
+__device__ __forceinline__ void col_window(const float *col, int st, const WinW<float, RMAX> &W, float4 (&out)[kV])
+{
+    float2 acc[kV][2];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) acc[v][0] = acc[v][1] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int pos = 0; pos < kV + 2 * RMAX; ++pos) {
+        const float4 val = *reinterpret_cast<const float4 *>(col + pos * st);
+        const float2 lo = make_float2(val.x, val.y), hi = make_float2(val.z, val.w);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const int d = pos - RMAX - v;
+            if (d >= -RMAX && d <= RMAX) {
+                acc[v][0] = __ffma2_rn(W.w[d < 0 ? -d : d], lo, acc[v][0]);
+                acc[v][1] = __ffma2_rn(W.w[d < 0 ? -d : d], hi, acc[v][1]);
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) out[v] = make_float4(acc[v][0].x, acc[v][0].y, acc[v][1].x, acc[v][1].y);
+}
+
+template <int RMAX>
+__device__ __forceinline__ void col_window(const double *col, int st, const WinW<double, RMAX> &W,
+                                           double2 (&out)[kV])
+{
+    double acc[kV][2];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) acc[v][0] = acc[v][1] = 0.0;
+#pragma unroll
+    for (int pos = 0; pos < kV + 2 * RMAX; ++pos) {
+        const double2 val = *reinterpret_cast<const double2 *>(col + pos * st);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const int d = pos - RMAX - v;
+            if (d >= -RMAX && d <= RMAX) {
+                acc[v][0] += W.w[d < 0 ? -d : d] * val.x;
+                acc[v][1] += W.w[d < 0 ? -d : d] * val.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) out[v] = make_double2(acc[v][0], acc[v][1]);
+}
 
 }  // namespace win
 
@@ -127,14 +207,13 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
         for (int u = 0; u < U; ++u)
             if (dst[u] >= 0) *reinterpret_cast<VT *>(s + dst[u]) = v[u];
     }
-    T w[RMAX + 1];
-#pragma unroll
-    for (int k = 0; k <= RMAX; ++k) w[k] = k <= R ? wg[k] : T(0);
+    WinW<T, RMAX> W;
+    load_weights(W, wg, R);
     __syncthreads();
 
     // ---- stencil through the register window ----
     const int tid = threadIdx.x;
-    if (AX == 0) {
+    if constexpr (AX == 0) {
         // thread: kV consecutive x outputs of row (y, z)
         const int xv = tid % (b / kV);
         const int y = (tid / (b / kV)) & bm;
@@ -154,7 +233,7 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
 #pragma unroll
                 for (int v = 0; v < kV; ++v) {
                     const int d = pos - HL - v;
-                    if (d >= -RMAX && d <= RMAX) acc[v] += w[d < 0 ? -d : d] * vs[e];
+                    if (d >= -RMAX && d <= RMAX) acc[v] += wscalar(W, d < 0 ? -d : d) * vs[e];
                 }
             }
         }
@@ -176,33 +255,13 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
         // element (axis position p in [-HL, b + HL), slab-local sl, x)
         const int st = AX == 1 ? b : NS * b;
         const T *col = AX == 1 ? s + (sl * E + a0) * b + x : s + (a0 * NS + sl) * b + x;
-        T acc[kV][NV];
-#pragma unroll
-        for (int v = 0; v < kV; ++v)
-#pragma unroll
-            for (int e = 0; e < NV; ++e) acc[v][e] = T(0);
-#pragma unroll
-        for (int pos = 0; pos < kV + 2 * RMAX; ++pos) {
-            const VT val = *reinterpret_cast<const VT *>(col + pos * st);
-            const T *vs = reinterpret_cast<const T *>(&val);
-#pragma unroll
-            for (int v = 0; v < kV; ++v) {
-                const int d = pos - HL - v;
-                if (d >= -RMAX && d <= RMAX) {
-#pragma unroll
-                    for (int e = 0; e < NV; ++e) acc[v][e] += w[d < 0 ? -d : d] * vs[e];
-                }
-            }
-        }
+        VT r[kV];
+        col_window<RMAX>(col, st, W, r);
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
-            VT r;
-            T *rr = reinterpret_cast<T *>(&r);
-#pragma unroll
-            for (int e = 0; e < NV; ++e) rr[e] = acc[v][e];
             const int Y = AX == 1 ? a0 + v : s0 + sl;
             const int Z = AX == 1 ? s0 + sl : a0 + v;
-            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((Z << LB) + Y) << LB) + x) = r;
+            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((Z << LB) + Y) << LB) + x) = r[v];
         }
     }
 }
@@ -217,7 +276,12 @@ template <typename T, int LB, int RMAX>
 struct XYCfg {
     static constexpr int b = 1 << LB, E = b + 2 * RMAX;
     static constexpr int EY1 = b + 2 * RMAX, EY = 2 * b + 2 * RMAX;   // staged rows: single, pair
-    static constexpr int per_plane = EY * E + EY * b;
+    // FP32 stages row pairs interleaved, [EY/2][P2], with a 16-byte skew per
+    // row pair (pitch P2 = 2E + 4), so that the row pairs of a warp start on
+    // different bank groups.
+    static constexpr int P2 = 2 * E + 4;
+    static constexpr int RG = sizeof(T) == 4 ? (EY / 2) * P2 : EY * E;   // staged elements per plane
+    static constexpr int per_plane = RG + EY * b;
     static constexpr int NS0 = 12288 / per_plane;
     static constexpr int NS = NS0 >= 8 ? 8 : NS0 >= 4 ? 4 : NS0 >= 2 ? 2 : 1;
     static constexpr int NSB = NS > b ? b : NS;
@@ -238,8 +302,8 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
     using VT = typename Vec<T>::V;
     constexpr int b = C::b, bm = b - 1, NV = Vec<T>::N, NS = C::NSB, HL = RMAX, E = C::E, EY = C::EY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *rg = reinterpret_cast<T *>(smem_raw);       // [NS][EY][E]
-    T *im = rg + NS * EY * E;                       // [NS][EY][b]
+    T *rg = reinterpret_cast<T *>(smem_raw);       // [NS][EY][E] (FP32: [NS][EY/2][P2])
+    T *im = rg + NS * C::RG;                        // [NS][EY][b]
     const int o1 = items[2 * blockIdx.x], o2 = items[2 * blockIdx.x + 1];
     const bool pair = o2 >= 0;                      // uniform over the CTA
     const int ny = pair ? 2 : 1;
@@ -256,72 +320,119 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
         yr = row - zl * rows;
     };
     // ---- stage ----
+    // FP64: one staged row per item, layout [NS][EY][E].  FP32: rows 2j and
+    // 2j + 1 per item (the same source block: block edges and the halo are
+    // even), interleaved as [NS][EY/2][E][2] (row pairs P2 apart), so that the
+    // x stencil runs on the packed pair (row 2j, row 2j + 1) with one FP32x2
+    // FMA per weight.
+    constexpr bool PACK = std::is_same<T, float>::value;
+    constexpr int RPI = PACK ? 2 : 1;                  // staged rows per item
     constexpr int vpr = E / NV;
-    const int total = NS * rows * vpr;
+    const int total = NS * (rows / RPI) * vpr;
     constexpr int U = 4;
     for (int base = threadIdx.x; base < total; base += U * 256) {
-        VT v[U];
+        VT v[U][RPI];
         int dst[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int it = base + u * 256;
             dst[u] = -1;
-            v[u] = VT{};
+#pragma unroll
+            for (int q = 0; q < RPI; ++q) v[u][q] = VT{};
             if (it >= total) continue;
-            const int row = it / vpr, cv = it - row * vpr;
+            const int rr = it / vpr, cv = it - rr * vpr;
             int zl, yr;
-            split(row, zl, yr);
+            split(rr * RPI, zl, yr);
             const int ex = cv * NV - HL, ey = yr - HL, z = s0 + zl;
-            dst[u] = (zl * EY + yr) * E + cv * NV;
+            dst[u] = PACK ? (zl * (EY / 2) + yr / 2) * C::P2 + cv * NV * 2 : (zl * EY + yr) * E + cv * NV;
             // block row of ey relative to the first output block: -nr .. ny - 1 + nr
             const int dyb = (ey + nr * b) >> LB;
             const int *nbt = dyb <= 2 * nr ? nb1 + dyb * nd : nb2 + (dyb - 1) * nd;
             const int bi = nbt[(ex + nr * b) >> LB];
-            if (bi >= 0)
-                v[u] = *reinterpret_cast<const VT *>(inf + ((int64_t)bi << (3 * LB)) + (((z << LB) + (ey & bm)) << LB) +
-                                                     (ex & bm));
-        }
+            if (bi >= 0) {
+                const T *src = inf + ((int64_t)bi << (3 * LB)) + (((z << LB) + (ey & bm)) << LB) + (ex & bm);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (dst[u] >= 0) *reinterpret_cast<VT *>(rg + dst[u]) = v[u];
-    }
-    T w[RMAX + 1];
-#pragma unroll
-    for (int k = 0; k <= RMAX; ++k) w[k] = k <= R ? wg[k] : T(0);
-    __syncthreads();
-    // ---- x stencil: every staged row, kV outputs per item ----
-    const int xitems = NS * rows * (b / kV);
-    for (int it = threadIdx.x; it < xitems; it += 256) {
-        const int xv = it % (b / kV);
-        int zl, yr;
-        split(it / (b / kV), zl, yr);
-        const int x0 = xv * kV;
-        const int row = zl * EY + yr;
-        const T *r = rg + row * E + x0;                       // staged x_ext = x0 - HL ...
-        T acc[kV];
-#pragma unroll
-        for (int v = 0; v < kV; ++v) acc[v] = T(0);
-#pragma unroll
-        for (int i = 0; i < (kV + 2 * RMAX) / NV; ++i) {
-            const VT val = *reinterpret_cast<const VT *>(r + i * NV);
-            const T *vs = reinterpret_cast<const T *>(&val);
-#pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                const int pos = i * NV + e;
-#pragma unroll
-                for (int v = 0; v < kV; ++v) {
-                    const int d = pos - HL - v;
-                    if (d >= -RMAX && d <= RMAX) acc[v] += w[d < 0 ? -d : d] * vs[e];
-                }
+                for (int q = 0; q < RPI; ++q) v[u][q] = *reinterpret_cast<const VT *>(src + q * b);
             }
         }
 #pragma unroll
-        for (int v = 0; v < kV; v += NV) {
-            VT q;
-            T *qq = reinterpret_cast<T *>(&q);
+        for (int u = 0; u < U; ++u) {
+            if (dst[u] < 0) continue;
+            if constexpr (PACK) {
+                const float4 a = v[u][0], c = v[u][RPI - 1];
+                *reinterpret_cast<float4 *>(rg + dst[u]) = make_float4(a.x, c.x, a.y, c.y);
+                *reinterpret_cast<float4 *>(rg + dst[u] + 4) = make_float4(a.z, c.z, a.w, c.w);
+            } else {
+                *reinterpret_cast<VT *>(rg + dst[u]) = v[u][0];
+            }
+        }
+    }
+    WinW<T, RMAX> W;
+    load_weights(W, wg, R);
+    __syncthreads();
+    // ---- x stencil: every staged row, kV outputs per item (two rows in FP32) ----
+    // (Lanes 32 bytes apart in FP32: two-way bank conflicts on these loads.
+    // Mapping the items of a quarter-warp onto distinct bank groups made this
+    // kernel faster alone but the graph step, where it runs beside the FFT
+    // passes, slower: the shared-memory-bound form leaves their warps more
+    // issue slots.)
+    const int xitems = NS * (rows / RPI) * (b / kV);
+    for (int it = threadIdx.x; it < xitems; it += 256) {
+        const int xv = it % (b / kV);
+        int zl, yr;
+        split(it / (b / kV) * RPI, zl, yr);
+        const int x0 = xv * kV;
+        const int row = zl * EY + yr;
+        // staged x_ext = x0 - HL ...
+        const T *r = PACK ? rg + (zl * (EY / 2) + yr / 2) * C::P2 + 2 * x0 : rg + row * E + x0;
+        if constexpr (PACK) {
+            float2 acc[kV];                                    // (row, row + 1)
 #pragma unroll
-            for (int e = 0; e < NV; ++e) qq[e] = acc[v + e];
-            *reinterpret_cast<VT *>(im + row * b + x0 + v) = q;
+            for (int v = 0; v < kV; ++v) acc[v] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < (kV + 2 * RMAX) / 2; ++i) {
+                const float4 val = *reinterpret_cast<const float4 *>(r + 4 * i);
+                const float2 pr[2] = {make_float2(val.x, val.y), make_float2(val.z, val.w)};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int pos = 2 * i + e;
+#pragma unroll
+                    for (int v = 0; v < kV; ++v) {
+                        const int d = pos - HL - v;
+                        if (d >= -RMAX && d <= RMAX) acc[v] = __ffma2_rn(W.w[d < 0 ? -d : d], pr[e], acc[v]);
+                    }
+                }
+            }
+            static_assert(kV == 4, "one float4 per row");
+            *reinterpret_cast<float4 *>(im + row * b + x0) = make_float4(acc[0].x, acc[1].x, acc[2].x, acc[3].x);
+            *reinterpret_cast<float4 *>(im + (row + 1) * b + x0) =
+                make_float4(acc[0].y, acc[1].y, acc[2].y, acc[3].y);
+        } else {
+            T acc[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) acc[v] = T(0);
+#pragma unroll
+            for (int i = 0; i < (kV + 2 * RMAX) / NV; ++i) {
+                const VT val = *reinterpret_cast<const VT *>(r + i * NV);
+                const T *vs = reinterpret_cast<const T *>(&val);
+#pragma unroll
+                for (int e = 0; e < NV; ++e) {
+                    const int pos = i * NV + e;
+#pragma unroll
+                    for (int v = 0; v < kV; ++v) {
+                        const int d = pos - HL - v;
+                        if (d >= -RMAX && d <= RMAX) acc[v] += wscalar(W, d < 0 ? -d : d) * vs[e];
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < kV; v += NV) {
+                VT q;
+                T *qq = reinterpret_cast<T *>(&q);
+#pragma unroll
+                for (int e = 0; e < NV; ++e) qq[e] = acc[v + e];
+                *reinterpret_cast<VT *>(im + row * b + x0 + v) = q;
+            }
         }
     }
     __syncthreads();
@@ -334,35 +445,14 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
         const int zl = it / ((b / NV) * ypp);
         const int x = xv * NV, y0 = yv * kV;                  // output row among the ny * b
         const T *col = im + (zl * EY + y0) * b + x;           // y_ext = y0 - HL ...
-        T acc[kV][NV];
-#pragma unroll
-        for (int v = 0; v < kV; ++v)
-#pragma unroll
-            for (int e = 0; e < NV; ++e) acc[v][e] = T(0);
-#pragma unroll
-        for (int pos = 0; pos < kV + 2 * RMAX; ++pos) {
-            const VT val = *reinterpret_cast<const VT *>(col + pos * b);
-            const T *vs = reinterpret_cast<const T *>(&val);
-#pragma unroll
-            for (int v = 0; v < kV; ++v) {
-                const int d = pos - HL - v;
-                if (d >= -RMAX && d <= RMAX) {
-#pragma unroll
-                    for (int e = 0; e < NV; ++e) acc[v][e] += w[d < 0 ? -d : d] * vs[e];
-                }
-            }
-        }
+        VT q[kV];
+        col_window<RMAX>(col, b, W, q);
         const int z = s0 + zl;
         const int o = y0 < b ? o1 : o2;
         const int yl = y0 & bm;
 #pragma unroll
-        for (int v = 0; v < kV; ++v) {
-            VT q;
-            T *qq = reinterpret_cast<T *>(&q);
-#pragma unroll
-            for (int e = 0; e < NV; ++e) qq[e] = acc[v][e];
-            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((z << LB) + yl + v) << LB) + x) = q;
-        }
+        for (int v = 0; v < kV; ++v)
+            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((z << LB) + yl + v) << LB) + x) = q[v];
     }
 }
 
