@@ -8,7 +8,10 @@
 // input feeds the V accumulators it touches with the weight w(|d|) held in a
 // register (the distance d is a compile-time constant after unrolling).
 // Shared-memory traffic per output is (V + 2 RMAX) / V values instead of
-// 2R + 1.
+// 2R + 1.  In FP32 the accumulators go in pairs through the packed FP32x2 FMA
+// (two lane-wise fma.rn per instruction, the scalar loop's bits): adjacent x
+// values in the y and z passes, adjacent y rows in the x pass of the fused
+// x+y kernel.
 #pragma once
 #include <type_traits>
 
