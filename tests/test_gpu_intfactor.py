@@ -98,3 +98,29 @@ def test_invalid_alpha(ctx32):
     with pytest.raises(lgf.LgfError) as e:
         ctx32.intfactor_apply(float("nan"), b, [[0, 0, 0]], [[0, 0, 0]], f, u)
     assert e.value.status == 1
+
+
+def _window_class(R):
+    return next((c for c in (4, 8, 12, 16) if R <= c), 0)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("b,seed", [(32, 13), (16, 12)])
+def test_every_window_class_single_and_paired_blocks(ctx32, ctx64, oracle, prec, b, seed):
+    """The fused x+y kernel in each radius class (4, 8, 12, 16) on target sets
+    that hold both y-adjacent block pairs and lone blocks, every point against
+    the oracle.  FP32 runs the packed FP32x2 stencils (x stencil on
+    interleaved row pairs), FP64 the scalar ones."""
+    ctx = ctx64 if prec == "f64" else ctx32
+    p = li.random_sparse(seed, b=b, nsrc=5, ntgt=7, extent=(3, 3, 2), ncomp=2)
+    tgt = {tuple(t) for t in p.tgt.tolist()}
+    paired = any((x, y + 1, z) in tgt for x, y, z in tgt)
+    lone = any((x, y + 1, z) not in tgt and (x, y - 1, z) not in tgt for x, y, z in tgt)
+    assert paired and lone
+    seen = set()
+    for alpha in (0.02, 0.3, 1.0, 2.0):
+        R, _ = ctx.intfactor_weights(alpha)
+        seen.add(_window_class(R))
+        got = run_intf(ctx, p, alpha)
+        assert rel_linf(got, oracle_intf(oracle, p, alpha)) < TOL[prec], (alpha, R)
+    assert seen == {4, 8, 12, 16}
