@@ -1,5 +1,6 @@
 """Host-side logic of bench.py on the CPU: the multi-rank timing reduction
-(gloo, world size 2), the reference arm's JSON line and the clock parsing."""
+(gloo, world size 2), the split of a batch's problems across ranks, the
+reference arm's JSON line and the clock parsing."""
 import json
 import os
 import socket
@@ -100,3 +101,57 @@ def test_reference_arm_other_ranks_do_no_work():
         workload, ref_points, warmup, steps = "dense128", 4, 3, 1
 
     assert bench.run_reference(A, rank=1, world=2) is None
+
+
+def _plate_like_costs(n=64, seed=3):
+    """Poisson costs shaped like the plate batch: block counts log-uniform in
+    [8, 1200], transform volume of a box twice the blocks' extent."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    nb = np.exp(rng.uniform(np.log(8), np.log(1200), size=n))
+    return [float(v) for v in 3 * (2 * 16 * np.cbrt(nb)) ** 3]
+
+
+def test_shard_covers_the_batch_once_and_balances():
+    sys.path.insert(0, ROOT)
+    import bench
+    costs = _plate_like_costs()
+    assert bench.shard(costs, 1, 0) == list(range(len(costs)))
+    for world in (2, 3, 4, 8):
+        parts = [bench.shard(costs, world, r) for r in range(world)]
+        assert sorted(i for p in parts for i in p) == list(range(len(costs)))
+        loads = [sum(costs[i] for i in p) for p in parts]
+        assert max(loads) <= sum(costs) / world + max(costs)     # the longest-first greedy bound
+        assert max(loads) < 1.05 * sum(costs) / world            # and close to even on this batch
+
+
+def _shard_rank(rank, world, port, costs, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist = bench.dist_init(world, "gloo")
+    mine = bench.shard(costs, world, rank)
+    seen = [None] * world
+    dist.all_gather_object(seen, mine)      # the test's own check: the split itself needs no exchange
+    q.put((rank, mine, seen))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_split_the_batch_alike():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    costs = _plate_like_costs()
+    procs = [ctx.Process(target=_shard_rank, args=(r, 2, port, costs, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, mine0, seen0), (r1, mine1, seen1) = out
+    assert seen0 == seen1 == [mine0, mine1]
+    assert not set(mine0) & set(mine1)
+    assert sorted(mine0 + mine1) == list(range(len(costs)))
