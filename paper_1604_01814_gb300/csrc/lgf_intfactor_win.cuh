@@ -377,8 +377,8 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
     // (Lanes 32 bytes apart in FP32: two-way bank conflicts on these loads.
     // Mapping the items of a quarter-warp onto distinct bank groups made this
     // kernel faster alone but the graph step, where it runs beside the FFT
-    // passes, slower: the shared-memory-bound form leaves their warps more
-    // issue slots.)
+    // passes, slower, presumably because the shared-memory-bound form leaves
+    // their warps more issue slots.)
     const int xitems = NS * (rows / RPI) * (b / kV);
     for (int it = threadIdx.x; it < xitems; it += 256) {
         const int xv = it % (b / kV);
