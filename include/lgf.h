@@ -295,29 +295,67 @@ typedef struct {
    seen, and reset the totals. */
 LGF_API lgf_status lgf_profile_read(lgf_ctx *ctx, lgf_kernel_stat *out, int32_t cap, int32_t *n);
 
+/* Cache state of a context (host-side bookkeeping; no device work).
+   The context caches plans (block maps and neighbour tables per block-set
+   pair), kernel spectra (per transform shape and kernel) and the CUDA graphs
+   of recent batches.  A captured graph holds the device addresses of the
+   scratch buffers, plans and spectra it was captured with, so every cached
+   graph is destroyed whenever any such buffer is freed or reallocated
+   (scratch growth, an eviction, a table rebuild); `generation` counts those
+   invalidations and a later batch is captured afresh.  Plan and spectrum
+   caches are bounded (least recently used evicted first, never an entry the
+   running call uses), so an active set that changes every step (Sec. 4.1)
+   does not grow device memory without bound. */
+typedef struct {
+    int64_t graphs_cached;      /* captured batch graphs held now */
+    int64_t poisson_plans, intfactor_plans, curl_plans, ib_plans;
+    int64_t spectra;            /* kernel spectra held now */
+    int64_t generation;         /* graph-cache invalidations so far */
+    int64_t graphs_dropped;     /* graphs destroyed (invalidation or LRU bound) */
+    int64_t evictions;          /* plans and spectra released by the LRU bounds */
+    int64_t scratch_reallocs;   /* scratch buffers (re)allocated */
+    int64_t scratch_bytes;      /* bytes of scratch held now */
+    int64_t reserved[5];
+} lgf_stats;
+
+/* Fill *out with the context's cache state.  Errors: LGF_EINVAL (null). */
+LGF_API lgf_status lgf_ctx_stats(lgf_ctx *ctx, lgf_stats *out);
+
+/* Set the cache bounds: max_plans (per plan kind, >= 1; default 256 Poisson
+   and integrating-factor plans, 64 curl and IB plans), max_spectra (>= 1,
+   default 32) and max_graphs (>= 0, default 8; 0 runs every batch with direct
+   launches).  -1 keeps a bound.  Lowering a bound takes effect at the next
+   insertion.  Changing max_graphs drops the cached graphs.
+   Errors: LGF_EINVAL. */
+LGF_API lgf_status lgf_cache_limits(lgf_ctx *ctx, int32_t max_plans, int32_t max_spectra, int32_t max_graphs);
+
 /* Allocation-free integrating-factor apply.  The paper has no counterpart:
    this entry point exists for callers that must not allocate device memory
    while they run -- for example a time-stepping loop whose device memory is
    reserved up front by another allocator (a framework's caching allocator),
    where a cudaMalloc could fail or synchronise the whole device.  It computes
-   exactly what lgf_intfactor_apply computes (same kernels, same truncation
-   rule with `tol`, 0 = 1e-7 for LGF_F32 and 1e-13 for LGF_F64) on the
-   current device, without a context and without calling cudaMalloc,
-   cudaFree or any allocating routine.  Its scratch (weights, neighbour
-   tables and the two intermediate fields) is one 32 MiB __device__ array
-   that every GPU which loads the library holds until the process exits;
-   planning uses fixed host arrays, so the function is not thread safe.
+   what lgf_intfactor_apply computes -- the same truncation rule with `tol`
+   (0 = 1e-7 for LGF_F32, 1e-13 for LGF_F64) and the same separable stencil --
+   on the current device, without a context and without calling cudaMalloc,
+   cudaFree or any allocating routine.  It always runs three single-axis
+   passes (x, y, z), whereas the context path may fuse the x and y passes, so
+   FP32 results agree with lgf_intfactor_apply to rounding, not bit for bit.
+   Its scratch (weights, neighbour tables and the two intermediate fields) is
+   one 32 MiB __device__ array that every GPU which loads the library holds
+   until the process exits; planning uses fixed host arrays, so the function
+   is not thread safe.
    Limits (LGF_EUNSUPPORTED beyond them): at most 1024 source and 1024 target
    blocks, block sets within a 64-block box (after growing by the stencil
-   reach), at most 8192 blocks per intermediate set, and intermediate fields
-   of at most about 32 MiB in total (nfields x blocks x b^3 x element size).
+   reach), at most 8192 blocks per intermediate set, intermediate fields of
+   at most about 32 MiB in total (nfields x blocks x b^3 x element size), and
+   device ordinals below 64.
    The first call on each device takes the device address of the array with
-   cudaGetSymbolAddress; make that first call before any stream capture.
-   Every call reuses the same array: calls whose work overlaps on the GPU
-   (different streams, or the same array from two host threads) race.  Each
-   call synchronises `stream` once (to read the weights and choose the
-   radius).  err_msg (host, err_cap bytes, may be NULL) receives a message
-   on failure. */
+   cudaGetSymbolAddress.  Every call reads the weights back to the host and
+   synchronises `stream` once (to choose the radius), so it cannot be called
+   while `stream` is being captured into a CUDA graph.  Every call reuses the
+   same array: calls whose work overlaps on the GPU (different streams, or
+   the same array from two host threads) race.  err_msg (host, err_cap bytes,
+   may be NULL) receives a message on failure. */
 LGF_API lgf_status lgf_intfactor_apply_noalloc(int32_t prec, double tol, double alpha, const lgf_blockset *src,
                                                const lgf_blockset *tgt, const void *f_dev, void *u_dev,
                                                int32_t ncomp, int32_t nrhs, void *stream, char *err_msg,

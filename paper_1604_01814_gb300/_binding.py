@@ -24,7 +24,8 @@ LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR, LGF_OP_KINV = 0
 EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
            "lgf_kinv_lookup", "lgf_poisson_apply", "lgf_kinv_apply", "lgf_curl", "lgf_curl_adjoint",
            "lgf_velocity_refresh", "lgf_ib_spread", "lgf_ib_interp", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
-           "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_intfactor_apply_noalloc",
+           "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_ctx_stats", "lgf_cache_limits",
+           "lgf_intfactor_apply_noalloc",
            "lgf_status_string", "lgf_last_error", "lgf_version")
 
 
@@ -45,6 +46,14 @@ class lgf_problem(ctypes.Structure):
 
 class lgf_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class lgf_stats(ctypes.Structure):
+    _fields_ = [("graphs_cached", ctypes.c_int64), ("poisson_plans", ctypes.c_int64),
+                ("intfactor_plans", ctypes.c_int64), ("curl_plans", ctypes.c_int64), ("ib_plans", ctypes.c_int64),
+                ("spectra", ctypes.c_int64), ("generation", ctypes.c_int64), ("graphs_dropped", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("scratch_reallocs", ctypes.c_int64),
+                ("scratch_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
 
 
 class LgfError(RuntimeError):
@@ -87,6 +96,8 @@ def load(path: str = LIB_PATH):
         "lgf_residual": [vp, bsp, vp, vp, dbl, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp],
         "lgf_profile_enable": [vp, i32],
         "lgf_profile_read": [vp, ctypes.POINTER(lgf_kernel_stat), i32, ctypes.POINTER(i32)],
+        "lgf_ctx_stats": [vp, ctypes.POINTER(lgf_stats)],
+        "lgf_cache_limits": [vp, i32, i32, i32],
         "lgf_intfactor_apply_noalloc": [i32, dbl, dbl, bsp, bsp, vp, vp, i32, i32, vp, ctypes.c_char_p, i32],
         "lgf_status_string": [i32],
         "lgf_last_error": [vp],
@@ -329,6 +340,16 @@ class Context:
         return r, ma.value, mf.value
 
 
+    def stats(self) -> dict:
+        """Cache state (lgf_ctx_stats): graphs, plans, spectra, invalidations, scratch."""
+        st = lgf_stats()
+        self._check(self._L.lgf_ctx_stats(self._h, ctypes.byref(st)), "lgf_ctx_stats")
+        return {name: int(getattr(st, name)) for name, _ in lgf_stats._fields_ if name != "reserved"}
+
+    def cache_limits(self, max_plans: int = -1, max_spectra: int = -1, max_graphs: int = -1):
+        self._check(self._L.lgf_cache_limits(self._h, int(max_plans), int(max_spectra), int(max_graphs)),
+                    "lgf_cache_limits")
+
     def profile_enable(self, enable: bool = True):
         self._check(self._L.lgf_profile_enable(self._h, 1 if enable else 0), "lgf_profile_enable")
 
@@ -415,6 +436,14 @@ def lgf_profile_enable(ctx: Context, enable: bool = True):
 
 def lgf_profile_read(ctx: Context) -> dict:
     return ctx.profile_read()
+
+
+def lgf_ctx_stats(ctx: Context) -> dict:
+    return ctx.stats()
+
+
+def lgf_cache_limits(ctx: Context, max_plans: int = -1, max_spectra: int = -1, max_graphs: int = -1):
+    return ctx.cache_limits(max_plans, max_spectra, max_graphs)
 
 
 def lgf_intfactor_apply_noalloc(prec: str, alpha: float, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1,

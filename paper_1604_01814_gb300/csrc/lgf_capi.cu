@@ -24,9 +24,25 @@ lgf_status cuda_fail(lgf_ctx *ctx, cudaError_t e, const char *what)
     return fail(ctx, LGF_ECUDA, m);
 }
 
+void invalidate_graphs(lgf_ctx *ctx)
+{
+    ctx->graphs.invalidate([](cudaGraphExec_t g) { cudaGraphExecDestroy(g); }, &ctx->counters);
+}
+
+void before_evict(lgf_ctx *ctx)
+{
+    invalidate_graphs(ctx);
+    cudaDeviceSynchronize();
+}
+
 lgf_status ensure_scratch(lgf_ctx *ctx, void **p, size_t *have, size_t need)
 {
     if (need <= *have) return LGF_OK;
+    // a cached graph may hold the old buffer's address: drop them all
+    if (ctx) {
+        invalidate_graphs(ctx);
+        ++ctx->counters.scratch_reallocs;
+    }
     if (*p) {
         cudaError_t e = cudaFree(*p);
         *p = nullptr;
@@ -101,6 +117,7 @@ lgf_status enter(lgf_ctx *ctx)
     if (!ctx) return LGF_EINVAL;
     ctx->last_error.clear();
     ctx->cur = &ctx->scr[0];
+    ++ctx->counters.epoch;   // cache entries stamped with this call are kept until it returns
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     return LGF_OK;
@@ -216,13 +233,12 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
     if (!ctx) return LGF_EINVAL;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
-    ctx->graphs.clear();
+    invalidate_graphs(ctx);
     ctx->pplans.clear();
     ctx->iplans.clear();
     ctx->cplans.clear();
     ctx->ibplans.clear();
-    for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
+    ctx->spectra.clear();
     for (auto &kv : ctx->gk_tables) cudaFree(kv.second);
     for (auto &kv : ctx->tw32) cudaFree(kv.second);
     for (auto &kv : ctx->tw64) cudaFree(kv.second);
@@ -263,13 +279,12 @@ lgf_status lgf_table_build(lgf_ctx *ctx, int32_t max_offset, void *stream)
     if (ctx->table_dev && ctx->table_radius >= R) return LGF_OK;
     st = table_build(ctx, R, (cudaStream_t)stream);
     if (st != LGF_OK) return st;
-    // spectra and G_K tables built from an older table are stale
-    for (auto &kv : ctx->spectra) cudaFree(kv.second.dev);
+    // spectra and G_K tables built from an older table are stale (the graphs
+    // that read them go first)
+    before_evict(ctx);
     ctx->spectra.clear();
     for (auto &kv : ctx->gk_tables) cudaFree(kv.second);
     ctx->gk_tables.clear();
-    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
-    ctx->graphs.clear();
     return LGF_OK;
 }
 
@@ -752,21 +767,16 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     };
     // 3. the legacy default stream cannot be captured, and per-kernel timing
     //    needs direct launches: run without a graph
-    if (s == nullptr || ctx->prof) return enqueue();
-    for (auto &g : ctx->graphs)
-        if (g.key == key) {
-            g.used = ++ctx->graph_clock;
-            LGF_CUDA(ctx, cudaGraphLaunch(g.exec, s));
-            return LGF_OK;
-        }
-    constexpr size_t kMaxGraphs = 8;
-    if (ctx->graphs.size() >= kMaxGraphs) {
-        size_t lru = 0;
-        for (size_t i = 1; i < ctx->graphs.size(); ++i)
-            if (ctx->graphs[i].used < ctx->graphs[lru].used) lru = i;
-        cudaGraphExecDestroy(ctx->graphs[lru].exec);
-        ctx->graphs.erase(ctx->graphs.begin() + lru);
+    //    (and so does a context whose graph cache is switched off)
+    if (s == nullptr || ctx->prof || ctx->graphs.cap() == 0) return enqueue();
+    // every buffer the batch needs has its final address now (the prepare
+    // step above grew the scratch, which dropped any graph holding an older
+    // address), so a cached graph of this key is safe to replay
+    if (cudaGraphExec_t *g = ctx->graphs.find(key, ++ctx->graph_clock)) {
+        LGF_CUDA(ctx, cudaGraphLaunch(*g, s));
+        return LGF_OK;
     }
+    ctx->graphs.make_room([](cudaGraphExec_t g) { cudaGraphExecDestroy(g); }, &ctx->counters);
     LGF_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     lgf_status est = enqueue();
     cudaGraph_t graph = nullptr;
@@ -780,12 +790,48 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch: graph instantiation");
-    lgf_ctx::GraphEntry ge;
-    ge.key = std::move(key);
-    ge.exec = exec;
-    ge.used = ++ctx->graph_clock;
-    ctx->graphs.push_back(std::move(ge));
+    ctx->graphs.add(std::move(key), exec, ++ctx->graph_clock);
     LGF_CUDA(ctx, cudaGraphLaunch(exec, s));
+    return LGF_OK;
+}
+
+lgf_status lgf_ctx_stats(lgf_ctx *ctx, lgf_stats *out)
+{
+    if (!ctx || !out) return LGF_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->graphs_cached = (int64_t)ctx->graphs.size();
+    out->poisson_plans = (int64_t)ctx->pplans.size();
+    out->intfactor_plans = (int64_t)ctx->iplans.size();
+    out->curl_plans = (int64_t)ctx->cplans.size();
+    out->ib_plans = (int64_t)ctx->ibplans.size();
+    out->spectra = (int64_t)ctx->spectra.size();
+    out->generation = (int64_t)ctx->counters.generation;
+    out->graphs_dropped = (int64_t)ctx->counters.graphs_dropped;
+    out->evictions = (int64_t)ctx->counters.plans_evicted;
+    out->scratch_reallocs = (int64_t)ctx->counters.scratch_reallocs;
+    int64_t bytes = 0;
+    for (const auto &sc : ctx->scr) bytes += (int64_t)(sc.a + sc.b + sc.c + sc.d + sc.e + sc.f);
+    out->scratch_bytes = bytes;
+    return LGF_OK;
+}
+
+lgf_status lgf_cache_limits(lgf_ctx *ctx, int32_t max_plans, int32_t max_spectra, int32_t max_graphs)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (max_plans == 0 || max_plans < -1 || max_spectra == 0 || max_spectra < -1 || max_graphs < -1)
+        return fail(ctx, LGF_EINVAL, "cache_limits: plans and spectra >= 1, graphs >= 0, or -1 to keep");
+    if (max_plans > 0) {
+        ctx->pplans.set_cap((size_t)max_plans);
+        ctx->iplans.set_cap((size_t)max_plans);
+        ctx->cplans.set_cap((size_t)max_plans);
+        ctx->ibplans.set_cap((size_t)max_plans);
+    }
+    if (max_spectra > 0) ctx->spectra.set_cap((size_t)max_spectra);
+    if (max_graphs >= 0 && (size_t)max_graphs != ctx->graphs.cap()) {
+        invalidate_graphs(ctx);
+        ctx->graphs.set_cap((size_t)max_graphs);
+    }
     return LGF_OK;
 }
 

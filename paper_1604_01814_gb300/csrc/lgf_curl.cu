@@ -97,14 +97,16 @@ int log2_exact(int b)
 lgf_status curl_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, int dir, CurlPlan **out)
 {
     const int b = src->b;
-    for (auto &p : ctx->cplans)
-        if (p->b == b && p->dir == dir && (int)p->src.size() == 3 * src->nblocks &&
-            (int)p->tgt.size() == 3 * tgt->nblocks &&
-            std::equal(p->src.begin(), p->src.end(), src->coords) &&
-            std::equal(p->tgt.begin(), p->tgt.end(), tgt->coords)) {
-            *out = p.get();
-            return LGF_OK;
-        }
+    if (CurlPlan *hit = ctx->cplans.find(
+            [&](const CurlPlan &p) {
+                return p.b == b && p.dir == dir && (int)p.src.size() == 3 * src->nblocks &&
+                       (int)p.tgt.size() == 3 * tgt->nblocks && std::equal(p.src.begin(), p.src.end(), src->coords) &&
+                       std::equal(p.tgt.begin(), p.tgt.end(), tgt->coords);
+            },
+            ctx->counters.epoch)) {
+        *out = hit;
+        return LGF_OK;
+    }
     std::map<std::array<int, 3>, int> idx;
     for (int i = 0; i < src->nblocks; ++i)
         idx[{src->coords[3 * i], src->coords[3 * i + 1], src->coords[3 * i + 2]}] = i;
@@ -131,8 +133,8 @@ lgf_status curl_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *
         cudaError_t e = cudaMemcpy(p->nbr_dev, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "curl plan: copy");
     }
-    *out = p.get();
-    ctx->cplans.push_back(std::move(p));
+    *out = ctx->cplans.insert(std::move(p), ctx->counters.epoch, [&] { before_evict(ctx); },
+                              &ctx->counters.plans_evicted);
     return LGF_OK;
 }
 

@@ -126,12 +126,15 @@ __global__ void __launch_bounds__(256) k_ib_interp(IBGeom g, const double *__res
 
 lgf_status ib_plan(lgf_ctx *ctx, const lgf_blockset *set, IBPlan **out)
 {
-    for (auto &p : ctx->ibplans)
-        if (p->b == set->b && (int)p->coords.size() == 3 * set->nblocks &&
-            std::equal(p->coords.begin(), p->coords.end(), set->coords)) {
-            *out = p.get();
-            return LGF_OK;
-        }
+    if (IBPlan *hit = ctx->ibplans.find(
+            [&](const IBPlan &p) {
+                return p.b == set->b && (int)p.coords.size() == 3 * set->nblocks &&
+                       std::equal(p.coords.begin(), p.coords.end(), set->coords);
+            },
+            ctx->counters.epoch)) {
+        *out = hit;
+        return LGF_OK;
+    }
     auto p = std::make_unique<IBPlan>();
     p->b = set->b;
     p->coords.assign(set->coords, set->coords + 3 * (size_t)set->nblocks);
@@ -161,8 +164,8 @@ lgf_status ib_plan(lgf_ctx *ctx, const lgf_blockset *set, IBPlan **out)
         return fail(ctx, LGF_ENOMEM, "IB plan: cudaMalloc");
     cudaError_t e = cudaMemcpy(p->lut_dev, lut.data(), lut.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "IB plan: copy");
-    *out = p.get();
-    ctx->ibplans.push_back(std::move(p));
+    *out = ctx->ibplans.insert(std::move(p), ctx->counters.epoch, [&] { before_evict(ctx); },
+                               &ctx->counters.plans_evicted);
     return LGF_OK;
 }
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "lgf.h"
+#include "lgf_cache.h"
 #include "lgf_fft.cuh"
 
 namespace lgf {
@@ -57,6 +58,7 @@ struct PoissonPlan {
     int *srcmap_dev = nullptr, *tgtmap_dev = nullptr;
     unsigned long long *srcrow_dev = nullptr, *tgtrow_dev = nullptr;
     int64_t A_elems = 0, B_elems = 0; // complex elements per field
+    uint64_t used = 0;                // epoch of the last call that used it
     ~PoissonPlan();
 };
 
@@ -76,6 +78,7 @@ struct IntfPlan {
     int *nbr_xy_dev = nullptr; // [n2][(2nr+1)^2] source block at xy offset of each Y2 block, or -1
     int *xy_items_dev = nullptr; // [n_xy_items][2] Y2 blocks of each fused-pass CTA (second -1: single)
     int n_xy_items = 0;
+    uint64_t used = 0;
     ~IntfPlan();
 };
 
@@ -88,7 +91,13 @@ struct IntfWeights {
 
 struct Spectrum {
     std::array<int, 3> M{};
+    double alpha = 0.0;       // 0: G_L; > 0: G_K(alpha)
     void *dev = nullptr;      // (Mz/2+1)(My/2+1)(Mx/2+1) reals, context precision, scaled by 1/(MxMyMz)
+    uint64_t used = 0;
+    Spectrum() = default;
+    Spectrum(const Spectrum &) = delete;
+    Spectrum &operator=(const Spectrum &) = delete;
+    ~Spectrum();
 };
 
 // Grow-only scratch buffers: A, B for the Poisson passes, C, D for the
@@ -106,6 +115,7 @@ struct IBPlan {
     int b = 0, lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
     std::vector<int32_t> coords;
     int *lut_dev = nullptr;
+    uint64_t used = 0;
     ~IBPlan();
 };
 
@@ -115,6 +125,7 @@ struct CurlPlan {
     int b = 0, dir = 0;
     std::vector<int32_t> src, tgt;
     int *nbr_dev = nullptr;   // [ntgt][4]
+    uint64_t used = 0;
     ~CurlPlan();
 };
 constexpr int kBranches = 4;   // concurrent branches of a batch
@@ -140,13 +151,15 @@ struct lgf_ctx {
     std::map<double, double *> gk_tables;
 
     // kernel spectra per transform-box shape and kernel (alpha = 0: G_L,
-    // alpha > 0: G_K(alpha))
-    std::map<std::pair<std::array<int, 3>, double>, lgf::Spectrum> spectra;
-    std::vector<std::unique_ptr<lgf::PoissonPlan>> pplans;
-    std::vector<std::unique_ptr<lgf::IntfPlan>> iplans;
+    // alpha > 0: G_K(alpha)) and the plans, each cache bounded (least
+    // recently used evicted; entries of the current call are kept)
+    lgf::LruCache<lgf::Spectrum> spectra{32};
+    lgf::LruCache<lgf::PoissonPlan> pplans{256};
+    lgf::LruCache<lgf::IntfPlan> iplans{256};
     std::vector<std::unique_ptr<lgf::IntfWeights>> weights;
-    std::vector<std::unique_ptr<lgf::CurlPlan>> cplans;
-    std::vector<std::unique_ptr<lgf::IBPlan>> ibplans;
+    lgf::LruCache<lgf::CurlPlan> cplans{64};
+    lgf::LruCache<lgf::IBPlan> ibplans{64};
+    lgf::CacheCounters counters;
 
     // grow-only scratch, one set per concurrent branch of lgf_batch_apply
     // (branch 0 also serves the single applies); `cur` is the set the next
@@ -160,13 +173,9 @@ struct lgf_ctx {
     cudaEvent_t ev_join[lgf::kBranches] = {};
 
     // batch graph cache: the most recently used batches (key = everything that
-    // shapes the work), least recently used evicted
-    struct GraphEntry {
-        std::vector<unsigned char> key;
-        cudaGraphExec_t exec = nullptr;
-        uint64_t used = 0;
-    };
-    std::vector<GraphEntry> graphs;
+    // shapes the work), least recently used evicted; dropped whole whenever a
+    // buffer that a graph may have captured is freed or reallocated
+    lgf::GraphCache<cudaGraphExec_t> graphs{8};
     uint64_t graph_clock = 0;
 
     double *red_dev = nullptr;   // small reduction buffer (residual, table mismatch)
@@ -189,6 +198,11 @@ namespace lgf {
 lgf_status fail(lgf_ctx *ctx, lgf_status st, const std::string &msg);
 lgf_status cuda_fail(lgf_ctx *ctx, cudaError_t e, const char *what);
 lgf_status ensure_scratch(lgf_ctx *ctx, void **p, size_t *have, size_t need);
+// Drop every captured graph (their buffers are about to change).
+void invalidate_graphs(lgf_ctx *ctx);
+// Called before a cache evicts entries: drop the graphs and wait for the
+// device, so no queued or replayed work still reads what is freed.
+void before_evict(lgf_ctx *ctx);
 const void *twiddles(lgf_ctx *ctx, int M, bool dbl, lgf_status *st);
 
 #define LGF_CUDA(ctx, call)                                   \

@@ -246,11 +246,12 @@ lgf_status intf_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *
     const int nr = R == 0 ? 0 : (R + b - 1) / b;
     const std::vector<int32_t> sv(src->coords, src->coords + 3 * (size_t)src->nblocks);
     const std::vector<int32_t> tv(tgt->coords, tgt->coords + 3 * (size_t)tgt->nblocks);
-    for (auto &p : ctx->iplans)
-        if (p->b == b && p->nr == nr && p->src == sv && p->tgt == tv) {
-            *out = p.get();
-            return LGF_OK;
-        }
+    if (IntfPlan *hit = ctx->iplans.find(
+            [&](const IntfPlan &p) { return p.b == b && p.nr == nr && p.src == sv && p.tgt == tv; },
+            ctx->counters.epoch)) {
+        *out = hit;
+        return LGF_OK;
+    }
     std::unordered_map<int64_t, int> S, T;
     for (int i = 0; i < src->nblocks; ++i)
         if (!S.emplace(pack(sv[3 * i], sv[3 * i + 1], sv[3 * i + 2]), i).second)
@@ -369,8 +370,8 @@ lgf_status intf_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *
                      cudaMemcpy(plan->xy_items_dev, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
     }
-        ctx->iplans.push_back(std::move(plan));
-    *out = ctx->iplans.back().get();
+    *out = ctx->iplans.insert(std::move(plan), ctx->counters.epoch, [&] { before_evict(ctx); },
+                              &ctx->counters.plans_evicted);
     return LGF_OK;
 }
 
@@ -635,8 +636,8 @@ extern "C" LGF_API lgf_status lgf_intfactor_apply_noalloc(int32_t prec, double t
     }
     // set-up, once per device: the device address of the static scratch
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev >= kNoAllocMaxDevices)
-        return err(LGF_ECUDA, "cudaGetDevice failed");
+    if (cudaGetDevice(&dev) != cudaSuccess) return err(LGF_ECUDA, "cudaGetDevice failed");
+    if (dev >= kNoAllocMaxDevices) return err(LGF_EUNSUPPORTED, "device ordinal 64 or above");
     if (!g_noalloc_base[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)

@@ -39,6 +39,8 @@ int next_fft_size(int n)
     return 2 * kMaxFft;   // beyond the largest supported length: the plan rejects it
 }
 
+Spectrum::~Spectrum() { cudaFree(dev); }
+
 PoissonPlan::~PoissonPlan()
 {
     cudaFree(srcmap_dev);
@@ -147,11 +149,10 @@ lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockse
     const int b = src->b;
     const std::vector<int32_t> sv(src->coords, src->coords + 3 * (size_t)src->nblocks);
     const std::vector<int32_t> tv(tgt->coords, tgt->coords + 3 * (size_t)tgt->nblocks);
-    for (auto &p : ctx->pplans) {
-        if (p->b == b && p->src == sv && p->tgt == tv) {
-            *out = p.get();
-            return LGF_OK;
-        }
+    if (PoissonPlan *hit = ctx->pplans.find(
+            [&](const PoissonPlan &p) { return p.b == b && p.src == sv && p.tgt == tv; }, ctx->counters.epoch)) {
+        *out = hit;
+        return LGF_OK;
     }
     int slo[3], shi[3], tlo[3], thi[3], lo[3], hi[3];
     for (int d = 0; d < 3; ++d) {
@@ -242,18 +243,17 @@ lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockse
     if (rst != LGF_OK) return rst;
     g.fstride = (int64_t)src->nblocks * b * b * b;
     g.ustride = (int64_t)tgt->nblocks * b * b * b;
-        ctx->pplans.push_back(std::move(plan));
-    *out = ctx->pplans.back().get();
+    *out = ctx->pplans.insert(std::move(plan), ctx->counters.epoch, [&] { before_evict(ctx); },
+                              &ctx->counters.plans_evicted);
     return LGF_OK;
 }
 
 lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum **out, cudaStream_t s)
 {
     const std::array<int, 3> shape{M[0], M[1], M[2]};
-    const auto key = std::make_pair(shape, alpha);
-    auto it = ctx->spectra.find(key);
-    if (it != ctx->spectra.end()) {
-        *out = &it->second;
+    if (Spectrum *hit = ctx->spectra.find([&](const Spectrum &q) { return q.M == shape && q.alpha == alpha; },
+                                          ctx->counters.epoch)) {
+        *out = hit;
         return LGF_OK;
     }
     if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "poisson: lgf_table_build has not been called");
@@ -311,11 +311,12 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum
         cudaFree(spec);
         return st;
     }
-    Spectrum sp;
-    sp.M = shape;
-    sp.dev = spec;
-    auto ins = ctx->spectra.emplace(key, sp);
-    *out = &ins.first->second;
+    auto sp = std::make_unique<Spectrum>();
+    sp->M = shape;
+    sp->alpha = alpha;
+    sp->dev = spec;
+    *out = ctx->spectra.insert(std::move(sp), ctx->counters.epoch, [&] { before_evict(ctx); },
+                               &ctx->counters.plans_evicted);
     return LGF_OK;
 }
 

@@ -5,7 +5,10 @@ memory while they run (their device memory is reserved up front by another
 allocator, where a cudaMalloc could fail or stall the device); its scratch is a
 fixed __device__ array shared by every call.  Two calls in a row must each
 match lgf_intfactor_apply, so that whatever the first call leaves in the shared
-array cannot leak into the second.  Collected last on purpose (file name).
+array cannot leak into the second; both are also checked against the oracle
+(the untruncated E(alpha) of Sec. 2.3 and App. A, Eq. lgf_intfac), so that a
+mistake both GPU paths share would still fail.  Collected last on purpose
+(file name).
 """
 import numpy as np
 import pytest
@@ -30,8 +33,15 @@ def _apply_both(ctx, prec, p, alpha):
     return got.cpu().numpy(), ref.cpu().numpy()
 
 
+def _oracle(oracle, p, alpha):
+    """E(alpha) f on the target blocks, every field, FP64, untruncated."""
+    out = [oracle.intfactor_blocks(alpha, p.b, p.src, p.f[r, c], p.tgt).reshape(-1)
+           for r in range(p.nrhs) for c in range(p.ncomp)]
+    return np.concatenate(out)
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_noalloc_matches_context_apply_on_two_calls_in_a_row(prec, ctx64, ctx32):
+def test_noalloc_matches_context_apply_on_two_calls_in_a_row(prec, ctx64, ctx32, oracle):
     ctx = ctx64 if prec == "f64" else ctx32
     first = li.random_sparse(21, b=16, nsrc=6, ntgt=8, extent=(4, 3, 3), ncomp=2)
     second = li.random_sparse(22, b=8, nsrc=9, ntgt=5, extent=(5, 4, 3), nrhs=2)
@@ -39,6 +49,9 @@ def test_noalloc_matches_context_apply_on_two_calls_in_a_row(prec, ctx64, ctx32)
         got, ref = _apply_both(ctx, prec, p, alpha)
         assert not np.isnan(got).any()
         assert rel_linf(got, ref) < TOL[prec]
+        exact = _oracle(oracle, p, alpha)
+        assert rel_linf(got, exact) < TOL[prec]
+        assert rel_linf(ref, exact) < TOL[prec]
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
