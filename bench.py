@@ -1,30 +1,34 @@
 #!/usr/bin/env python
-"""Benchmark of the LGF Poisson apply (+ integrating factors) on one GB300.
+"""Benchmark of the LGF Poisson apply (+ integrating factor) on one GB300.
 
-Workload (default "dense128"): the dense 128^3 lattice box of Liska &
-Colonius-style smooth sources (8 Gaussian blobs, sigma = 6 cells, seed 1), FP32,
-32^3 blocks.  One step = one lgf_batch_apply call (one CUDA graph) holding the
-whole hot path for that input: the G_L Poisson apply u = G_L * f and the
-integrating factors E(0.05) f, E(0.5) f, E(2.0) f.  The metric counts the
-Poisson apply's active target lattice points (2,097,152 per step) over the
+Workload (default "plates64"): 64 independent block-adaptive flat-plate
+problems (16^3 blocks, active block counts log-uniform in [8, 1200], 3
+components, FP32, seed 3), the batched form of Liska & Colonius's plate runs.
+One step = one lgf_batch_apply call (one CUDA graph) that applies G_L and then
+E(0.25) to every problem.  The metric counts the Poisson apply's active
+target points (target lattice point x component) of all 64 problems over the
 whole step's time, so the integrating factors only lower the reported value.
-The kernel spectra and the G_L table are pre-processing (built before timing,
-once per simulation as in App. A).
+Kernel spectra and the G_L table are pre-processing (built before timing, once
+per simulation as in App. A).  Other workloads: dense128 (the 128^3 box of
+Gaussian blobs, G_L + three E(alpha)), wake512 (512x256x256 wake domain, 12
+fields), and the extra lines of EXTRA.
 
-Timing: W untimed warm-up steps; then K steps, each bracketed by CUDA events
-on the launch stream, with a 512 MiB buffer written between steps (L2 flush,
-the 8 MiB input is smaller than L2); barrier + synchronize around the timed
-region; max over ranks.  Multi-GPU runs (torchrun) of the dense box are
-independent replicas (the problem does not shard): value = ranks x points /
-max time.  The plate batch (--workload plates64) splits its independent
-problems across the ranks instead: value = the batch's points / max time.
+Timing: W untimed warm-up steps and a >= 1 s untimed soak with the clock
+sampler running; then K steps, each bracketed by CUDA events on the launch
+stream; barrier + synchronize around the timed region; max over ranks.  The
+plate batch's working set exceeds L2, so no flush is needed; dense128 writes
+a 512 MiB buffer between steps.  Under torchrun the plate batch's problems are
+split across ranks (longest first; value = the batch's points / the slowest
+rank's time); other workloads run as replicas.
 
-Other JSON keys: roofline of the dominant kernel (algorithmic bytes per
-launch / CUDA-event launch time, against MEASURED_PEAKS.json), e2e (the same
-metric with the host->device copy of f from pinned memory and the
-device->host copy of all outputs inside the timed region), cpu_baseline (the
-CPU oracle on a bounded sample, with its error against the GPU result) and the
-SM clocks sampled during the timed region.
+Other JSON keys: roofline of the Poisson apply (8 B per target point over the
+summed time of its five pass kernels, against MEASURED_PEAKS.json; with the
+ncu DRAM bytes of those kernels when profiles/ holds a capture of the current
+sources), roofline_step (8 B per point of every apply over the step time),
+roofline_dominant_kernel, e2e (host->device copies of every input and
+device->host copies of every output inside the timed region), cpu_baseline
+(the CPU oracle on a bounded sample), rel_err_vs_oracle, fp64_plain (the FP64
+single-problem form at the same truncation tolerance), clocks.
 
 `--impl reference` times the CPU oracle (direct summation) as the reference
 arm on the same workload, one bounded sample of target points per step.
@@ -159,20 +163,65 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# workload
+# workloads: one step = one lgf_batch_apply
 # ----------------------------------------------------------------------------
-ALPHAS = (0.05, 0.5, 2.0)
+METRIC = "active lattice points/sec for LGF Poisson apply at rel err 1e-5; % HBM roofline"
+DENSE_ALPHAS = (0.05, 0.5, 2.0)
+PLATE_ALPHA = 0.25
 
 
-def make_workload(name: str):
+class Workload:
+    """The batch of one step.  entries: dicts (p=Problem, op, alpha); several
+    entries may share one source field (same `fkey`)."""
+
+    def __init__(self, name, entries, desc):
+        self.name = name
+        self.entries = entries
+        self.desc = desc
+
+    @property
+    def poisson_entries(self):
+        return [e for e in self.entries if e["op"] in (0, 2, 3)]
+
+    def points(self):
+        """Poisson target points per step (one point = target lattice point x
+        component x right-hand side)."""
+        return float(sum(e["p"].tgt.shape[0] * e["p"].b ** 3 * e["p"].ncomp * e["p"].nrhs
+                         for e in self.poisson_entries))
+
+    def intf_points(self):
+        return float(sum(e["p"].tgt.shape[0] * e["p"].b ** 3 * e["p"].ncomp * e["p"].nrhs
+                         for e in self.entries if e["op"] in (1, 2)))
+
+
+def make_workload(name: str) -> Workload:
     import lgf_inputs as li
+    if name == "plates64":
+        probs = li.plate_batch()
+        ents = [dict(p=q, op=2, alpha=PLATE_ALPHA, fkey=i) for i, q in enumerate(probs)]
+        desc = {"workload": "64 independent flat-plate problems (16^3 blocks, N_b log-uniform in [8, 1200], "
+                            "AR 1/2/4, 30 deg, seed 3), 3 components, FP32; one lgf_batch_apply of G_L then "
+                            "E(0.25) for every problem per step (one CUDA graph)",
+                "problems": 64, "block": 16, "fields_per_problem": 3,
+                "target_blocks": int(sum(q.tgt.shape[0] for q in probs)),
+                "source_blocks": int(sum(q.src.shape[0] for q in probs)), "alpha": PLATE_ALPHA}
+        return Workload(name, ents, desc)
     if name == "dense128":
         p = li.dense_blobs(n=128, b=32, seed=1)
+        ents = [dict(p=p, op=0, alpha=0.0, fkey=0)] + [dict(p=p, op=1, alpha=a, fkey=0) for a in DENSE_ALPHAS]
         desc = {"workload": "dense 128^3 box, 8 Gaussian blobs (sigma 6, seed 1), 32^3 blocks, FP32; "
                             "G_L apply + E(0.05), E(0.5), E(2.0) per step",
                 "lattice": [128, 128, 128], "block": 32, "blocks": int(p.src.shape[0]), "fields": 1,
-                "alphas": list(ALPHAS)}
-        return p, desc
+                "alphas": list(DENSE_ALPHAS)}
+        return Workload(name, ents, desc)
+    if name == "wake512":
+        p = li.wake_domain()
+        ents = [dict(p=p, op=0, alpha=0.0, fkey=0)]
+        desc = {"workload": "512x256x256 wake domain, 32^3 blocks (384 active), curl-of-blobs source, "
+                            "3 components x 4 RK right-hand sides (12 fields), FP32; one G_L apply of all fields "
+                            "per step", "lattice": [512, 256, 256], "block": 32, "blocks": int(p.src.shape[0]),
+                "fields": 12}
+        return Workload(name, ents, desc)
     raise ValueError(f"unknown workload {name}")
 
 
@@ -192,50 +241,60 @@ def geometry(p):
     return [int(m) for m in M], Ls, Lt
 
 
-def algorithmic_bytes_per_step(p, nfields: int, n_intf: int) -> dict:
-    """Compulsory bytes per step of each kernel (FP32): every input element
-    read once, every output element written once.  n_intf integrating factors
-    on the dense box share each pass's launches (grouped jobs)."""
+def pass_io_bytes(p, nfields: int) -> dict:
+    """Bytes each Poisson pass reads and writes by this design (FP32): its
+    input and output arrays once, intermediates included.  A diagnostic of the
+    design, not the algorithmic cost of the apply (8 B per target point)."""
     M, Ls, Lt = geometry(p)
     K = M[0] // 2 + 1
-    c8 = 8  # complex64
+    c8 = 8
     b3 = p.b ** 3
     nsrc, ntgt = int(p.src.shape[0]), int(p.tgt.shape[0])
     spec = (M[2] // 2 + 1) * (M[1] // 2 + 1) * K * 4
-    by = {
+    return {
         "poisson_x_forward": nfields * (nsrc * b3 * 4 + Ls[2] * Ls[1] * K * c8),
         "poisson_y_forward": nfields * (Ls[2] * Ls[1] * K * c8 + Ls[2] * M[1] * K * c8),
         "poisson_z_convolve": nfields * (Ls[2] * M[1] * K * c8 + Lt[2] * M[1] * K * c8) + spec,
         "poisson_y_inverse": nfields * (Lt[2] * M[1] * K * c8 + Lt[2] * Lt[1] * K * c8),
         "poisson_x_inverse": nfields * (Lt[2] * Lt[1] * K * c8 + ntgt * b3 * 4),
     }
-    # integrating-factor passes on a dense box: every pass reads and writes the box once per apply
-    for ax in ("x", "y", "z", "xy"):
-        by[f"intfactor_pass_{ax}"] = n_intf * nfields * 2 * ntgt * b3 * 4
-    return by
+
+
+def z_pass_flops(p, nfields: int) -> float:
+    """FP32 flops of the z pass by the standard 5 N log2 N count per complex
+    transform of length N (forward and inverse along z for every (kx, ky)
+    column, times the 2-flop real spectral multiply per bin)."""
+    M, _, _ = geometry(p)
+    K = M[0] // 2 + 1
+    cols = K * M[1] * nfields
+    return float(cols * (2 * 5 * M[2] * math.log2(M[2]) + 2 * M[2]))
+
+
+POISSON_PASSES = ("poisson_x_forward", "poisson_y_forward", "poisson_z_convolve", "poisson_y_inverse",
+                  "poisson_x_inverse")
+INTF_PASSES = ("intfactor_pass_xy", "intfactor_pass_z", "intfactor_pass_x", "intfactor_pass_y")
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1604_01814_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
+        if fn.endswith((".cu", ".cuh", ".h")):
             h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+def load_traffic(workload: str):
+    """DRAM bytes per step of each kernel role from the committed ncu summary
+    of this workload, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"ncu_traffic_{workload}.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    k = d.get("kernels", {}).get(kernel)
-    return None if k is None else float(k["dram_bytes_per_launch"])
+    return {k: float(v["dram_bytes_per_step"]) for k, v in d.get("kernels", {}).items()}
 
 
 def measured_peaks():
@@ -246,136 +305,244 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# FP32 ALU peak of the z pass's roofline: 152 SMs x 128 FP32 lanes x 2 flops
+# (one FMA) x 2.07 GHz, the nominal unit count and maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ----------------------------------------------------------------------------
-def oracle_sample(p, npts: int, seed: int = 101):
+def oracle_sample(w: Workload, per_problem: int, seed: int = 101):
+    """The oracle's direct sum (single-field form, as it stands) at a bounded
+    random sample of Poisson targets: per_problem points of every Poisson
+    entry, every field.  Returns (samples, seconds, threads) with samples a
+    list of (entry index, field, point indices, values)."""
     from oracle import oracle
     rng = np.random.default_rng(seed)
-    ntot = p.tgt.shape[0] * p.b ** 3
-    idx = np.sort(rng.choice(ntot, size=npts, replace=False))
-    pts = oracle.block_points(p.b, p.tgt)[idx]
-    oracle.lgf_table(64)   # table build is pre-processing, outside the timing
-    t0 = time.perf_counter()
-    ref = oracle.poisson_direct(p.b, p.src, p.f[0, 0], pts, R=64)
-    dt = time.perf_counter() - t0
-    return idx, ref, dt, oracle.num_threads()
+    oracle.lgf_table(64)   # the table build is pre-processing, outside the timing
+    out, dt = [], 0.0
+    for k, e in enumerate(w.entries):
+        if e["op"] not in (0, 2):
+            continue
+        p = e["p"]
+        ntot = p.tgt.shape[0] * p.b ** 3
+        idx = np.sort(rng.choice(ntot, size=min(per_problem, ntot), replace=False))
+        pts = oracle.block_points(p.b, p.tgt)[idx]
+        for r in range(p.nrhs):
+            for c in range(p.ncomp):
+                t0 = time.perf_counter()
+                ref = oracle.poisson_direct(p.b, p.src, p.f[r, c], pts, R=64)
+                dt += time.perf_counter() - t0
+                out.append((k, r * p.ncomp + c, idx, ref))
+    return out, dt, oracle.num_threads()
+
+
+REF_SAMPLE = {"plates64": 16, "dense128": 1024, "wake512": 2}      # reference arm, per problem and field
+CPU_SAMPLE = {"plates64": 256, "dense128": 3072, "wake512": 16}    # cpu_baseline and the error check
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    p, desc = make_workload(args.workload)
-    npts = args.ref_points
-    times = []
+    w = make_workload(args.workload)
+    per = args.ref_points if args.ref_points > 0 else REF_SAMPLE[args.workload]
+    times, npts = [], 0
     for k in range(args.warmup + args.steps):
-        _, _, dt, cores = oracle_sample(p, npts, seed=1000 + k)
+        samples, dt, cores = oracle_sample(w, per, seed=1000 + k)
         if k >= args.warmup:
             times.append(dt)
+            npts = sum(len(s[2]) for s in samples)
     ms = 1e3 * float(np.mean(times))
     value = npts / (ms * 1e-3)
-    sample = f"{npts} random target points of the Poisson apply per step (direct summation over all sources)"
+    sample = (f"{per} random Poisson targets per problem and field ({npts} target points per step), direct "
+              f"summation over all sources")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": w.desc,
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return line
 
 
-METRIC = "active lattice points/sec for LGF Poisson apply at rel err 1e-5; % HBM roofline"
-
-
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def build_batch(lgf, w: Workload, dev, dtype, f_of=None, u_of=None, only_poisson=False):
+    """Device tensors and the batch list.  f_of / u_of override the tensors."""
+    import torch
+    fs, batch, outs = {}, [], []
+    for k, e in enumerate(w.entries):
+        p = e["p"]
+        if only_poisson and e["op"] not in (0, 2):
+            continue
+        if e["fkey"] not in fs:
+            fs[e["fkey"]] = (f_of(k) if f_of else
+                             torch.tensor(p.f.reshape(-1), dtype=dtype).to(dev))
+        n_out = p.nrhs * p.ncomp * p.tgt.shape[0] * p.b ** 3
+        u = u_of(k) if u_of else torch.empty(n_out, dtype=dtype, device=dev)
+        op = 0 if (only_poisson and e["op"] == 2) else e["op"]
+        batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=fs[e["fkey"]], u=u, ncomp=p.ncomp, nrhs=p.nrhs,
+                          op=op, alpha=e["alpha"], dx=1.0))
+        outs.append(u)
+    return fs, batch, outs
+
+
+def timed_steps(step, s, nsteps, flush=None):
+    """Per-step CUDA-event times (ms) on stream s."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    with torch.cuda.stream(s):
+        for a, b in evs:
+            if flush is not None:
+                flush.zero_()
+            a.record(s)
+            step()
+            b.record(s)
+    s.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import paper_1604_01814_gb300 as lgf
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    p, desc = make_workload(args.workload)
+    w = make_workload(args.workload)
+    points_all = w.points()
+    sharded = w.name == "plates64" and world > 1
+    if sharded:   # independent problems: each rank runs its share, no data-path collective
+        costs = [float(np.prod(geometry(e["p"])[0])) * e["p"].ncomp * e["p"].nrhs for e in w.entries]
+        mine = shard(costs, world, rank)
+        w = Workload(w.name, [w.entries[i] for i in mine], w.desc)
     ctx = lgf.Context("f32", device=dev.index)
     ctx.table_build(48)
-    f_host = torch.tensor(p.f.reshape(-1), dtype=torch.float32).pin_memory()
-    f = f_host.to(dev)
-    n_out = p.tgt.shape[0] * p.b ** 3
-    u = torch.empty(n_out, dtype=torch.float32, device=dev)
-    vs = [torch.empty(n_out, dtype=torch.float32, device=dev) for _ in ALPHAS]
-    batch = [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, op=lgf.LGF_OP_POISSON, dx=1.0)]
-    batch += [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=v, op=lgf.LGF_OP_INTFACTOR, alpha=a)
-              for a, v in zip(ALPHAS, vs)]
+    fs, batch, outs = build_batch(lgf, w, dev, torch.float32)
     s = torch.cuda.Stream(device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    points = float(n_out)   # Poisson target points per step (one field)
+    l2_note = ("flushed between timed steps (512 MiB write)" if w.name == "dense128" else
+               "not flushed: every step's working set (inputs, intermediates, outputs) exceeds the 129 MB L2")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev) if w.name == "dense128" else None
+
+    def step():
+        ctx.batch_apply(batch, stream=s)
 
     with torch.cuda.stream(s):
         for _ in range(max(3, args.warmup)):
-            ctx.batch_apply(batch, stream=s)
+            step()
     s.synchronize()
 
+    # ---- soak: >= 1 s of steps with the clock sampler running, untimed ----
+    clk = ClockSampler(dev.index)
+    clk.start()
+    t_end = time.perf_counter() + 1.0
+    with torch.cuda.stream(s):
+        while time.perf_counter() < t_end:
+            step()
+            s.synchronize()
     # ---- timed region (device time, CUDA events on the launch stream) ----
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clk = ClockSampler(dev.index)
-    clk.start()
-    time.sleep(0.3)
-    with torch.cuda.stream(s):
-        for a, b in evs:
-            flush.zero_()
-            a.record(s)
-            ctx.batch_apply(batch, stream=s)
-            b.record(s)
-    s.synchronize()
+    ms_steps = timed_steps(step, s, args.steps, flush)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = clk.stop()
-    ms_local = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    ms_local = float(np.mean(ms_steps))
     ms = reduce_max(ms_local, dist)
-    value = job_throughput(points, ms, world)
+    value = points_all / (ms * 1e-3) if sharded else job_throughput(w.points(), ms, world)
 
     # ---- per-kernel times (events around every launch, direct launches) ----
     ctx.profile_enable(True)
+    nprof = max(3, min(args.steps, 10))
     with torch.cuda.stream(s):
-        for _ in range(args.steps):
-            flush.zero_()
-            ctx.batch_apply(batch, stream=s)
+        for _ in range(nprof):
+            if flush is not None:
+                flush.zero_()
+            step()
     stats = ctx.profile_read()
     ctx.profile_enable(False)
-    launches_per_step = sum(n for n, _ in stats.values()) / args.steps
-    alg_step = algorithmic_bytes_per_step(p, 1, len(ALPHAS))
-    # bytes per launch = bytes per step / launches per step
-    alg = {k: alg_step[k] * args.steps / n for k, (n, _) in stats.items() if k in alg_step}
-    dom = max(stats, key=lambda k: stats[k][1])
-    dom_ms = stats[dom][1] / stats[dom][0]
-    peak, peak_kind = measured_peaks()
-    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
-    kernels = {k: {"launches_per_step": n / args.steps, "ms_per_launch": t / n,
-                   "share": t / sum(v[1] for v in stats.values()),
-                   "alg_bytes_per_launch": int(alg[k]) if k in alg else None,
-                   "alg_GBps": (alg[k] / (t / n * 1e-3) / 1e9) if k in alg else None}
+    launches_per_step = sum(n for n, _ in stats.values()) / nprof
+    tot_ms = sum(t for _, t in stats.values())
+    io = {}
+    for e in w.entries:
+        if e["op"] in (0, 2):
+            for k, v in pass_io_bytes(e["p"], e["p"].ncomp * e["p"].nrhs).items():
+                io[k] = io.get(k, 0) + v
+    kernels = {k: {"launches_per_step": n / nprof, "ms_per_step": t / nprof, "ms_per_launch": t / n,
+                   "share": t / tot_ms,
+                   "pass_io_GBps": (io[k] / (t / nprof * 1e-3) / 1e9) if k in io else None}
                for k, (n, t) in stats.items()}
+    peak, peak_kind = measured_peaks()
+    # roofline of the Poisson apply (SURVEY 8(d)(ii)): 8 B per target point
+    # (4 B read of f + 4 B write of u, FP32) over the summed time of its five
+    # pass kernels per step
+    pois_ms = sum(stats[k][1] for k in POISSON_PASSES if k in stats) / nprof
+    pois_bytes = 8.0 * w.points()
+    traffic = load_traffic(w.name)
+    pois_traffic = (sum(traffic.get(k, 0.0) for k in POISSON_PASSES) if traffic else None)
+    roofline = {"bound": "hbm", "kernel": "poisson apply (its five pass kernels)",
+                "achieved": pois_bytes / (pois_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": pois_bytes / (pois_ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
+                "traffic": pois_traffic, "alg_bytes_per_step": pois_bytes, "ms_per_step": pois_ms,
+                "alg_bytes_per_unit": 8, "unit_def": "target lattice point x component x rhs (FP32)",
+                "dram_frac": (pois_traffic / (pois_ms * 1e-3) / 1e9 / peak) if pois_traffic else None}
+    step_bytes = 8.0 * (w.points() + w.intf_points())
+    roofline_step = {"bound": "hbm", "achieved": step_bytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": step_bytes / (ms * 1e-3) / 1e9 / peak,
+                     "alg_bytes_per_step": step_bytes,
+                     "how": "8 B per target point of every Poisson and integrating-factor apply over the "
+                            "step's CUDA-event time"}
+    dom = max(stats, key=lambda k: stats[k][1])
+    roofline_dom = {"kernel": dom, "share": stats[dom][1] / tot_ms}
+    if dom == "poisson_z_convolve":
+        fl = sum(z_pass_flops(e["p"], e["p"].ncomp * e["p"].nrhs) for e in w.entries if e["op"] in (0, 2))
+        t = stats[dom][1] / nprof * 1e-3
+        roofline_dom.update({"bound": "alu", "achieved": fl / t / 1e12, "peak": FP32_PEAK_TFLOPS,
+                             "unit": "TFLOP/s", "frac": fl / t / 1e12 / FP32_PEAK_TFLOPS,
+                             "how": "5 N log2 N flops per complex transform, forward and inverse per column, "
+                                    "against 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"})
 
-    # ---- end to end: pinned host input -> apply -> outputs back to host ----
-    # A streaming pipeline with two device buffer sets: the host->device copy
-    # of step k+1 and the device->host copy of step k-1 run on their own
-    # streams while step k computes.  Every step still copies its whole input
-    # from pinned host memory and all four output fields back to pinned host
-    # memory; the time is first copy-in start to last copy-out end over K steps.
-    n_out_fields = 1 + len(ALPHAS)
+    # ---- error against the oracle: the Poisson part of the same step ----
+    # (the bench step writes E(0.25) G_L f; the Poisson values are taken from a
+    # Poisson-only batch of the same inputs in the same context)
+    samples, cpu_dt, cores = (None, None, None)
+    rel_err = None
+    if rank == 0 and not args.no_cpu:
+        per = args.cpu_points if args.cpu_points > 0 else CPU_SAMPLE[w.name]
+        samples, cpu_dt, cores = oracle_sample(w, per)
+        fsp, bp, outp = build_batch(lgf, w, dev, torch.float32, f_of=None, only_poisson=True)
+        with torch.cuda.stream(s):
+            ctx.batch_apply(bp, stream=s)
+        s.synchronize()
+        pois_idx = [k for k, e in enumerate(w.entries) if e["op"] in (0, 2)]
+        errs = []
+        for k, fld, idx, ref in samples:
+            p = w.entries[k]["p"]
+            got = outp[pois_idx.index(k)].view(p.nrhs * p.ncomp, -1)[fld].cpu().numpy().astype(np.float64)[idx]
+            errs.append((np.abs(got - ref).max(), np.abs(ref).max()))
+        # per field: max |err| over its samples / max |ref| over its samples
+        rel_err = float(max(a / b for a, b in errs if b > 0))
+        del fsp, bp, outp
+        npts = sum(len(x[2]) for x in samples)
+
+    # ---- end to end: pinned host inputs -> apply -> all outputs to host ----
+    # Two device buffer sets; the host->device copy of step k+1 and the
+    # device->host copy of step k-1 run on their own streams while step k
+    # computes.  Every step copies every problem's input from pinned host
+    # memory and every output field back to pinned host memory.
+    host_f = {}
+    for e in w.entries:
+        if e["fkey"] not in host_f:
+            host_f[e["fkey"]] = torch.tensor(e["p"].f.reshape(-1), dtype=torch.float32).pin_memory()
     sets = []
     for j in range(2):
-        fj = torch.empty_like(f)
-        oj = [torch.empty(n_out, dtype=torch.float32, device=dev) for _ in range(n_out_fields)]
-        bj = [dict(b=p.b, src=p.src, tgt=p.tgt, f=fj, u=oj[0], op=lgf.LGF_OP_POISSON, dx=1.0)]
-        bj += [dict(b=p.b, src=p.src, tgt=p.tgt, f=fj, u=o, op=lgf.LGF_OP_INTFACTOR, alpha=a)
-               for a, o in zip(ALPHAS, oj[1:])]
-        hj = [torch.empty(n_out, dtype=torch.float32).pin_memory() for _ in range(n_out_fields)]
+        fj, bj, oj = build_batch(lgf, w, dev, torch.float32)
+        hj = [torch.empty(o.numel(), dtype=torch.float32).pin_memory() for o in oj]
         sets.append((fj, oj, bj, hj))
+    h2d_bytes = int(sum(t.numel() * 4 for t in host_f.values()))
+    d2h_bytes = int(sum(o.numel() * 4 for o in outs))
     s_in = torch.cuda.Stream(device=dev)
     s_out = torch.cuda.Stream(device=dev)
 
@@ -389,7 +556,8 @@ def run_ours(args, rank, world, dist):
             if k >= 2:
                 s_in.wait_event(comp[k - 2])          # step k-2 no longer reads f_j
             with torch.cuda.stream(s_in):
-                fj.copy_(f_host, non_blocking=True)
+                for key, t in fj.items():
+                    t.copy_(host_f[key], non_blocking=True)
             h2d = torch.cuda.Event()
             h2d.record(s_in)
             s.wait_event(h2d)
@@ -412,114 +580,110 @@ def run_ours(args, rank, world, dist):
         dist.barrier()
     pipeline(args.steps, e0, e1)
     e2e_ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist)
-    e2e = {"value": job_throughput(points, e2e_ms, world), "unit": "points/s",
-           "h2d_bytes_per_step": int(f.numel() * 4), "d2h_bytes_per_step": int(n_out * 4 * n_out_fields),
+    e2e = {"value": (points_all / (e2e_ms * 1e-3) if sharded else job_throughput(w.points(), e2e_ms, world)),
+           "unit": "points/s", "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
            "ms_per_step": e2e_ms,
            "how": "two buffer sets; copy-in of step k+1 and copy-out of step k-1 overlap step k; "
-                  "no L2 flush (every input is re-copied from the host)"}
+                  "every input re-copied from pinned host memory and every output copied back each step"}
     # the end-to-end results must be the device-timed results
-    for o, d in zip(sets[(args.steps - 1) % 2][3], [u] + vs):
+    last = sets[(args.steps - 1) % 2][3]
+    for o, d in zip(last, outs):
         assert torch.equal(o, d.cpu()), "end-to-end output differs from the device-timed output"
+    del sets
 
-    # ---- the plain FP64 single-problem form on the same GPU ----
-    # Separate lgf_poisson_apply / lgf_intfactor_apply calls in an FP64 context
-    # (no batch, no graph, no concurrent branch), timed like the main loop.
+    # ---- the plain FP64 single-problem form on the same GPU, equal accuracy ----
+    # Both contexts truncate E at the same tol (1e-7, which keeps E within the
+    # 1e-5 bar); FP64 applies one problem per call (lgf_poisson_apply then
+    # lgf_intfactor_apply), no batch, no graph, no concurrent branch.
     fp64 = None
     if not args.no_fp64:
-        ctx64 = lgf.Context("f64", device=dev.index)
+        ctx64 = lgf.Context("f64", tol=1e-7, device=dev.index)
         ctx64.table_build(48)
-        f64 = f.double()
-        u64 = torch.empty(n_out, dtype=torch.float64, device=dev)
-        v64 = [torch.empty_like(u64) for _ in ALPHAS]
+        f64 = {k: t.double() for k, t in fs.items()}
+        o64 = [torch.empty_like(o, dtype=torch.float64) for o in outs]
+        tmp64 = [torch.empty_like(o, dtype=torch.float64) if e["op"] == 2 else None
+                 for e, o in zip(w.entries, outs)]
 
         def plain64():
-            ctx64.poisson_apply(p.b, p.src, p.tgt, f64, u64, stream=s)
-            for a, v in zip(ALPHAS, v64):
-                ctx64.intfactor_apply(a, p.b, p.src, p.tgt, f64, v, stream=s)
+            for e, o, t in zip(w.entries, o64, tmp64):
+                p = e["p"]
+                f = f64[e["fkey"]]
+                if e["op"] == 0:
+                    ctx64.poisson_apply(p.b, p.src, p.tgt, f, o, ncomp=p.ncomp, nrhs=p.nrhs, stream=s)
+                elif e["op"] == 1:
+                    ctx64.intfactor_apply(e["alpha"], p.b, p.src, p.tgt, f, o, ncomp=p.ncomp, nrhs=p.nrhs,
+                                          stream=s)
+                else:
+                    ctx64.poisson_apply(p.b, p.src, p.tgt, f, t, ncomp=p.ncomp, nrhs=p.nrhs, stream=s)
+                    ctx64.intfactor_apply(e["alpha"], p.b, p.tgt, p.tgt, t, o, ncomp=p.ncomp, nrhs=p.nrhs,
+                                          stream=s)
 
         with torch.cuda.stream(s):
             for _ in range(3):
                 plain64()
         s.synchronize()
-        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                for _ in range(args.steps)]
-        with torch.cuda.stream(s):
-            for a, b in ev64:
-                flush.zero_()
-                a.record(s)
-                plain64()
-                b.record(s)
-        s.synchronize()
-        ms64 = reduce_max(float(np.mean([a.elapsed_time(b) for a, b in ev64])), dist)
-        errs = [float((x.double() - y).abs().max() / y.abs().max()) for x, y in zip([u] + vs, [u64] + v64)]
-        fp64 = {"ms_per_step": ms64, "value": job_throughput(points, ms64, world), "unit": "points/s",
-                "speedup_of_fp32_batched": ms64 / ms, "fp32_vs_fp64_rel_err": max(errs),
-                "how": "FP64 context, one lgf_poisson_apply and three lgf_intfactor_apply calls per step "
-                       "(tol 1e-13), no batch or graph; the FP32 batched outputs agree with it to "
-                       "fp32_vs_fp64_rel_err (both within the 1e-5 bar)"}
+        n64 = max(3, min(args.steps, 10))
+        ms64 = reduce_max(float(np.mean(timed_steps(plain64, s, n64, flush))), dist)
+        errs = [float((x.double() - y).abs().max() / y.abs().max()) for x, y in zip(outs, o64)]
+        fp64 = {"ms_per_step": ms64, "steps": n64, "value": job_throughput(w.points(), ms64, world),
+                "unit": "points/s", "speedup_of_fp32_batched": ms64 / ms, "fp32_vs_fp64_rel_err": max(errs),
+                "tol": 1e-7,
+                "how": "FP64 context with the FP32 context's E truncation (tol 1e-7), one Poisson and one "
+                       "integrating-factor call per problem per step, no batch or graph; the FP32 batched "
+                       "outputs agree with it to fp32_vs_fp64_rel_err"}
         ctx64.close()
+        del f64, o64, tmp64
 
     line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(desc, l2="flushed between timed steps (512 MiB write); input 8 MiB < L2",
-                           parallelism="replicas" if world > 1 else "single GPU",
-                           kernels=kernels),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind,
-                         "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": dom_ms,
-                         "traffic": load_traffic(dom)},
+            "config": dict(w.desc, l2=l2_note,
+                           parallelism=("problems sharded across ranks, longest first" if sharded else
+                                        "replicas" if world > 1 else "single GPU"),
+                           points_per_step=points_all, kernels=kernels),
+            "roofline": roofline, "roofline_step": roofline_step, "roofline_dominant_kernel": roofline_dom,
             "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
-            "clocks": clocks}
+            "launches_per_step": launches_per_step, "clocks": clocks,
+            "timed_region_s": float(sum(ms_steps)) * 1e-3}
     if fp64 is not None:
         line["fp64_plain"] = fp64
-    # ---- CPU baseline: the oracle on a bounded sample, and the GPU error there ----
     if rank == 0 and not args.no_cpu:
-        idx, ref, dt, cores = oracle_sample(p, args.cpu_points)
-        got = u.cpu().numpy().astype(np.float64)[idx]
-        err = float(np.abs(got - ref).max() / np.abs(ref).max())
-        line["cpu_baseline"] = {"value": args.cpu_points / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{args.cpu_points} random target points of the Poisson apply "
-                                          f"(direct summation over all 2^21 sources), {dt:.1f} s"}
-        line["rel_err_vs_oracle"] = err
+        line["cpu_baseline"] = {"value": npts / cpu_dt, "unit": "points/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{per} random Poisson targets per problem and field "
+                                          f"({npts} target points; direct summation over every source), "
+                                          f"{cpu_dt:.1f} s"}
+        line["rel_err_vs_oracle"] = rel_err
+        line["rel_err_how"] = ("Poisson apply of the same inputs in the same context, at the cpu_baseline "
+                               "sample: per field max |gpu - oracle| / max |oracle|")
     ctx.close()
     return line
 
 
 def run_ncu_case(args):
-    """The bench step (one lgf_batch_apply on the legacy stream) run `--steps`
-    times untimed: the small, short case that ncu captures."""
+    """The bench step (one lgf_batch_apply on the legacy stream: direct
+    launches) run `--steps` times untimed: the case that ncu captures."""
     import torch
-    import lgf_inputs as li
     import paper_1604_01814_gb300 as lgf
     ctx = lgf.Context("f32")
     ctx.table_build(48)
     if args.workload == "wake512":
         # one right-hand side (3 fields, about 3 GB on the device): the wake
         # domain's transform shape at a size a full capture handles
+        import lgf_inputs as li
         p = li.wake_domain(nrhs=1)
-        f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
-        outs = [torch.empty(f.numel(), dtype=torch.float32, device="cuda")]
-        batch = [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=outs[0], ncomp=3, nrhs=1, op=lgf.LGF_OP_POISSON)]
+        w = Workload("wake512", [dict(p=p, op=0, alpha=0.0, fkey=0)], {})
     else:
-        p, _ = make_workload(args.workload)
-        f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
-        outs = [torch.empty_like(f) for _ in range(1 + len(ALPHAS))]
-        batch = [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=outs[0], op=lgf.LGF_OP_POISSON)]
-        batch += [dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=o, op=lgf.LGF_OP_INTFACTOR, alpha=a)
-                  for a, o in zip(ALPHAS, outs[1:])]
+        w = make_workload(args.workload)
+    _, batch, outs = build_batch(lgf, w, torch.device("cuda"), torch.float32)
     for _ in range(args.steps):
         ctx.batch_apply(batch, stream=0)
     torch.cuda.synchronize()
-    print("ncu case done:", [float(o.abs().max()) for o in outs], flush=True)
+    print("ncu case done:", len(batch), "problems, max |u|", max(float(o.abs().max()) for o in outs), flush=True)
     ctx.close()
 
 
 EXTRA = {
-    "wake512": "512x256x256 wake domain, 32^3 blocks (384 active), curl-of-blobs source, 3 components x 4 "
-               "RK right-hand sides (12 fields), FP32; one G_L apply of all fields per step",
-    "plates64": "64 flat-plate problems, 16^3 blocks, N_b log-uniform in [8, 1200], 3 components, FP32; "
-                "one lgf_batch_apply of G_L then E(0.25) for every problem per step",
     "refresh_sphere": "velocity refresh u <- -C^dagger L^{-1} C u (Eq. vel_refresh) on the sphere-plus-wake "
                       "active set (16^3 blocks), u = curl of a Gaussian-blob vector potential, FP32; one refresh "
                       "per step",
@@ -533,34 +697,16 @@ EXTRA = {
 
 
 def run_extra(args, rank, world, dist):
-    """The larger paper-shaped workloads (working sets far above L2) and the
-    rows beyond the Poisson/integrating-factor path: their own JSON line with
-    throughput and per-kernel algorithmic GB/s.  Not the bench line: the bench
-    workload is the dense 128^3 box."""
+    """The rows beyond the Poisson/integrating-factor path: their own JSON
+    line with throughput and per-kernel times.  Not the bench line."""
     import torch
     import lgf_inputs as li
     import paper_1604_01814_gb300 as lgf
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    probs = []
-    if args.workload == "wake512":
-        probs = [(li.wake_domain(), lgf.LGF_OP_POISSON, 0.0)]
-    elif args.workload == "plates64":
-        probs = [(q, lgf.LGF_OP_POISSON_THEN_INTFACTOR, 0.25) for q in li.plate_batch()]
-        points_all = float(sum(q.nrhs * q.ncomp * q.tgt.shape[0] * q.b ** 3 for q, _, _ in probs))
-        if world > 1:   # independent problems: each rank runs its share, no data-path collective
-            probs = [probs[i] for i in shard([poisson_cost(q) for q, _, _ in probs], world, rank)]
-    elif args.workload == "kinv_sphere":
-        q = li.sphere_ib()
-        q = li.Problem("sphere_surface", q.b, q.src, q.src.copy(), q.f, alphas=(0.25,))
-        probs = [(q, lgf.LGF_OP_KINV, 0.25)]
-    elif args.workload not in ("refresh_sphere", "ib_sphere"):
-        raise ValueError(f"unknown workload {args.workload}")
     ctx = lgf.Context("f32", device=dev.index)
     ctx.table_build(48)
-    batch, points = [], 0.0
-    alg_step = {}
     s = torch.cuda.Stream(device=dev)
     if args.workload == "refresh_sphere":
         q = li.sphere_ib()
@@ -569,17 +715,7 @@ def run_extra(args, rank, world, dist):
                                amps=np.array([[0.0, 0.0, 1.0], [0.5, -1.0, 0.0]]), sigma=8.0)
         ut = torch.tensor(u.reshape(-1), dtype=torch.float32, device=dev)
         uo = torch.empty_like(ut)
-        ncell = cells.shape[0] * q.b ** 3
-        points = float(3 * ncell)
-        # the Poisson part maps the cells to the cells and their +x, +y, +z neighbour blocks
-        grown = set(map(tuple, cells.tolist()))
-        for e in np.eye(3, dtype=np.int64):
-            grown |= set(map(tuple, (cells + e).tolist()))
-        grown = np.array(sorted(grown), dtype=np.int32)
-        pg = li.Problem("refresh", q.b, cells, grown, np.zeros((1, 3, cells.shape[0], 1)))
-        alg_step = algorithmic_bytes_per_step(pg, 3, 0)
-        alg_step["curl"] = 2 * 3 * 4 * ncell
-        alg_step["curl_adjoint"] = 2 * 3 * 4 * ncell
+        points = float(3 * cells.shape[0] * q.b ** 3)
 
         def step():
             ctx.velocity_refresh(q.b, cells, cells, ut, uo, stream=s)
@@ -591,43 +727,30 @@ def run_extra(args, rank, world, dist):
         fm = torch.empty(3 * q.src.shape[0] * q.b ** 3, dtype=torch.float32, device=dev)
         Um = torch.empty_like(gm)
         points = float(3 * nm)
-        # marker values and positions read, the field written (spread) or the 27 support values read (interp)
-        alg_step = {"ib_spread": 4 * 3 * nm + 24 * nm + 4 * fm.numel(), "ib_interp": 4 * 3 * nm * 28 + 24 * nm}
 
         def step():
             ctx.ib_spread(q.b, q.src, Xm, gm, fm, stream=s)
             ctx.ib_interp(q.b, q.src, Xm, fm, Um, stream=s)
-    else:
-        for p, op, a in probs:
-            nf = p.nrhs * p.ncomp
-            f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device=dev)
-            u = torch.empty(nf * p.tgt.shape[0] * p.b ** 3, dtype=torch.float32, device=dev)
-            batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, nrhs=p.nrhs, op=op, alpha=a))
-            points += float(u.numel())
-            n_intf = 1 if op in (lgf.LGF_OP_INTFACTOR, lgf.LGF_OP_POISSON_THEN_INTFACTOR) else 0
-            for k, v in algorithmic_bytes_per_step(p, nf, n_intf).items():
-                alg_step[k] = alg_step.get(k, 0) + v
+    elif args.workload == "kinv_sphere":
+        q = li.sphere_ib()
+        f = torch.tensor(q.f.reshape(-1), dtype=torch.float32, device=dev)
+        u = torch.empty_like(f)
+        batch = [dict(b=q.b, src=q.src, tgt=q.src, f=f, u=u, ncomp=3, nrhs=1, op=lgf.LGF_OP_KINV, alpha=0.25)]
+        points = float(u.numel())
 
         def step():
             ctx.batch_apply(batch, stream=s)
+    else:
+        raise ValueError(f"unknown workload {args.workload}")
     with torch.cuda.stream(s):
         for _ in range(max(3, args.warmup)):
             step()
     s.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     clk = ClockSampler(dev.index)
     clk.start()
-    with torch.cuda.stream(s):
-        for a, b in evs:
-            a.record(s)
-            step()
-            b.record(s)
-    s.synchronize()
+    ms_steps = timed_steps(step, s, args.steps)
     clocks = clk.stop()
-    ms = reduce_max(float(np.mean([a.elapsed_time(b) for a, b in evs])), dist)
+    ms = reduce_max(float(np.mean(ms_steps)), dist)
     ctx.profile_enable(True)
     with torch.cuda.stream(s):
         for _ in range(args.steps):
@@ -635,27 +758,13 @@ def run_extra(args, rank, world, dist):
     stats = ctx.profile_read()
     ctx.profile_enable(False)
     tot = sum(t for _, t in stats.values())
-    kernels = {}
-    for k, (n, t) in stats.items():
-        per_launch = alg_step.get(k, 0) * args.steps / n if k in alg_step else None
-        kernels[k] = {"launches_per_step": n / args.steps, "ms_per_launch": t / n, "share": t / tot,
-                      "alg_GBps": per_launch / (t / n * 1e-3) / 1e9 if per_launch else None}
-    peak, peak_kind = measured_peaks()
-    dom = max(stats, key=lambda k: stats[k][1]) if stats else None   # (a rank may hold no problem)
-    sharded = args.workload == "plates64" and world > 1
-    value = points_all / (ms * 1e-3) if sharded else job_throughput(points, ms, world)
+    kernels = {k: {"launches_per_step": n / args.steps, "ms_per_launch": t / n, "share": t / tot}
+               for k, (n, t) in stats.items()}
     line = {"workload": args.workload, "config": EXTRA[args.workload], "metric": METRIC,
-            "value": value, "unit": "points/s", "ms_per_step": ms,
-            "points_per_step": points_all if sharded else points, "steps": args.steps, "n_gpus": world,
-            "dtype": "f32",
-            "parallelism": ("problems sharded across ranks, longest first" if sharded else
-                            "replicas" if world > 1 else "single GPU"),
-            "scaling": "strong" if sharded else "weak",
-            "l2": "no flush: the working set of every pass exceeds the 129 MB L2",
-            "kernels": kernels, "dominant": dom,
-            "dominant_hbm_frac": (kernels[dom]["alg_GBps"] / peak) if dom and kernels[dom]["alg_GBps"] else None,
-            "peak_GBps": peak, "peak_kind": peak_kind, "clocks": clocks,
-            "note": "integrating-factor bytes counted as read + write of the target set per pass"}
+            "value": job_throughput(points, ms, world), "unit": "points/s", "ms_per_step": ms,
+            "points_per_step": points, "steps": args.steps, "n_gpus": world, "dtype": "f32",
+            "parallelism": "replicas" if world > 1 else "single GPU", "scaling": "weak",
+            "kernels": kernels, "clocks": clocks}
     ctx.close()
     return line
 
@@ -663,12 +772,14 @@ def run_extra(args, rank, world, dist):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dense128")
-    ap.add_argument("--cpu-points", type=int, default=3072)
-    ap.add_argument("--ref-points", type=int, default=1024)
+    ap.add_argument("--workload", default="plates64",
+                    help="plates64 (default, the bench line), dense128, wake512; or " + ", ".join(EXTRA))
+    ap.add_argument("--cpu-points", type=int, default=0,
+                    help="oracle sample per problem and field for cpu_baseline and the error check (0: default)")
+    ap.add_argument("--ref-points", type=int, default=0, help="reference arm sample per problem (0: default)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--ncu-case", action="store_true", help="run the step --steps times untimed (for ncu)")

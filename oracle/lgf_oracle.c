@@ -385,6 +385,100 @@ int orc_poisson_direct(int b, int nsrc, const int32_t *src_coords, const double 
     return 0;
 }
 
+/* The same sum for nf fields on one source block set at once (the fields'
+   values at a point share one evaluation of G_L): f [nf][nsrc][b^3],
+   out [nf][ntgt].  Points where every field is zero are skipped.
+   G_L depends only on (|n1|, |n2|, |n3|), so its values over the offsets the
+   targets and sources span are taken once from orc_lgf into a dense table
+   (the same numbers; skipped when the table would exceed 2^26 entries).  Each
+   field is summed with compensation: the exact rounding error of every
+   addition is formed by Knuth's TwoSum (branch-free, the same error that the
+   Neumaier branches form) and the errors are added up beside the sum. */
+int orc_poisson_direct_multi(int b, int nsrc, const int32_t *src_coords, int nf, const double *f,
+                             int64_t ntgt, const int32_t *tgt_pts, double dx,
+                             const double *table, int R, double *out)
+{
+    if (b <= 0 || nsrc < 0 || ntgt < 0 || nf < 1 || nf > 64) return -1;
+    const int64_t b3 = (int64_t)b * b * b;
+    const int64_t npts = (int64_t)nsrc * b3;
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < npts; ++i) {
+        int any = 0;
+        for (int j = 0; j < nf; ++j) any |= (f[j * npts + i] != 0.0);
+        nnz += any;
+    }
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(nnz + 1));
+    double *val = (double *)malloc(sizeof(double) * (size_t)nf * (size_t)(nnz + 1));
+    if (!pos || !val) { free(pos); free(val); return -2; }
+    int64_t k = 0;
+    for (int s = 0; s < nsrc; ++s)
+        for (int z = 0; z < b; ++z)
+            for (int y = 0; y < b; ++y)
+                for (int x = 0; x < b; ++x) {
+                    const int64_t i = s * b3 + ((int64_t)z * b + y) * b + x;
+                    int any = 0;
+                    for (int j = 0; j < nf; ++j) any |= (f[j * npts + i] != 0.0);
+                    if (!any) continue;
+                    pos[3 * k] = src_coords[3 * s] * b + x;
+                    pos[3 * k + 1] = src_coords[3 * s + 1] * b + y;
+                    pos[3 * k + 2] = src_coords[3 * s + 2] * b + z;
+                    for (int j = 0; j < nf; ++j) val[k * nf + j] = f[j * npts + i];
+                    ++k;
+                }
+    /* largest |offset| per axis between any target and any source point */
+    int64_t ext[3] = {0, 0, 0};
+    if (nnz > 0 && ntgt > 0)
+        for (int d = 0; d < 3; ++d) {
+            int32_t slo = pos[d], shi = pos[d], tlo = tgt_pts[d], thi = tgt_pts[d];
+            for (int64_t m = 1; m < nnz; ++m) {
+                if (pos[3 * m + d] < slo) slo = pos[3 * m + d];
+                if (pos[3 * m + d] > shi) shi = pos[3 * m + d];
+            }
+            for (int64_t t = 1; t < ntgt; ++t) {
+                if (tgt_pts[3 * t + d] < tlo) tlo = tgt_pts[3 * t + d];
+                if (tgt_pts[3 * t + d] > thi) thi = tgt_pts[3 * t + d];
+            }
+            const int64_t a1 = (int64_t)thi - slo, a2 = (int64_t)shi - tlo;
+            const int64_t m1 = a1 < 0 ? -a1 : a1, m2 = a2 < 0 ? -a2 : a2;
+            ext[d] = (m1 > m2 ? m1 : m2) + 1;
+        }
+    double *gd = NULL;
+    const int64_t ngd = ext[0] * ext[1] * ext[2];
+    if (ngd > 0 && ngd <= ((int64_t)1 << 26)) {
+        gd = (double *)malloc(sizeof(double) * (size_t)ngd);
+        if (gd) {
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < ngd; ++i)
+                gd[i] = orc_lgf(table, R, (int)(i % ext[0]), (int)((i / ext[0]) % ext[1]),
+                                (int)(i / (ext[0] * ext[1])));
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < ntgt; ++t) {
+        const int tx = tgt_pts[3 * t], ty = tgt_pts[3 * t + 1], tz = tgt_pts[3 * t + 2];
+        double sum[64], cmp[64];
+        for (int j = 0; j < nf; ++j) sum[j] = cmp[j] = 0.0;
+        for (int64_t m = 0; m < nnz; ++m) {
+            const int d0 = abs(tx - pos[3 * m]), d1 = abs(ty - pos[3 * m + 1]), d2 = abs(tz - pos[3 * m + 2]);
+            const double g = gd ? gd[((int64_t)d2 * ext[1] + d1) * ext[0] + d0] : orc_lgf(table, R, d0, d1, d2);
+            const double *v = val + m * nf;
+            for (int j = 0; j < nf; ++j) {
+                const double term = g * v[j];
+                const double s2 = sum[j] + term;       /* TwoSum: s2 + e == sum + term exactly */
+                const double bv = s2 - sum[j];
+                const double e = (sum[j] - (s2 - bv)) + (term - bv);
+                sum[j] = s2;
+                cmp[j] += e;
+            }
+        }
+        for (int j = 0; j < nf; ++j) out[j * ntgt + t] = dx * dx * (sum[j] + cmp[j]);
+    }
+    free(gd);
+    free(pos);
+    free(val);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Integrating factor.                                                       */
 /* ------------------------------------------------------------------------ */

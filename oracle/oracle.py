@@ -12,6 +12,7 @@ it follows; the C source documents the numerical method):
   lgf_asym           far-field expansion of G_L                  Sec. 2.2 / App. A footnote
   lgf_table          G_L over sorted offsets up to R             App. A (look-up table)
   poisson_direct     u = dx^2 sum_m G_L(n-m) f(m)                Sec. 2.2, Eq. dpoisson_conv
+  poisson_direct_multi  the same for several fields on one source set
   intfactor_weights  e^{-2a} I_n(2a), n = 0..nmax                App. A, Eq. lgf_intfac
   intfactor_box      u = E(alpha) f on a dense box (untruncated) Sec. 2.3 footnote
   lgf_r              R(alpha)(n) = int_0^alpha G_E(t)(n) dt      App. A (partition of G_K)
@@ -46,10 +47,12 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so (gcc -O2 -fopenmp).  Returns the library path."""
+    """Compile liboracle.so (gcc -O3 -fopenmp; no contraction of a*b+c into one rounding, so the
+    arithmetic is the same plain IEEE evaluation on every host).  Returns the library path."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O3", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -75,6 +78,8 @@ def lib():
             L.orc_lgf.restype = ctypes.c_double
             L.orc_poisson_direct.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_int64, _ip,
                                              ctypes.c_double, _dp, ctypes.c_int, _dp]
+            L.orc_poisson_direct_multi.argtypes = [ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp, ctypes.c_int64,
+                                                   _ip, ctypes.c_double, _dp, ctypes.c_int, _dp]
             L.orc_intfactor_weights.argtypes = [ctypes.c_double, ctypes.c_int, _dp]
             L.orc_intfactor_box.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
             L.orc_num_threads.restype = ctypes.c_int
@@ -157,6 +162,21 @@ def poisson_direct(b: int, src_coords, f, tgt_pts, dx: float = 1.0, R: int = 32)
                                   float(dx), _p(tab), int(R), _p(out))
     if rc != 0:
         raise RuntimeError(f"orc_poisson_direct failed ({rc})")
+    return out
+
+
+def poisson_direct_multi(b: int, src_coords, f, tgt_pts, dx: float = 1.0, R: int = 32) -> np.ndarray:
+    """poisson_direct for several fields on one source set: f [nf][nsrc][b^3]
+    -> [nf][ntgt] (one G_L evaluation per pair serves every field)."""
+    src = np.ascontiguousarray(src_coords, dtype=np.int32).reshape(-1, 3)
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1, src.shape[0], b ** 3)
+    tp = np.ascontiguousarray(tgt_pts, dtype=np.int32).reshape(-1, 3)
+    tab = lgf_table(R)
+    out = np.empty((f.shape[0], tp.shape[0]))
+    rc = lib().orc_poisson_direct_multi(int(b), src.shape[0], _p(src, _ip), f.shape[0], _p(f), tp.shape[0],
+                                        _p(tp, _ip), float(dx), _p(tab), int(R), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_poisson_direct_multi failed ({rc})")
     return out
 
 

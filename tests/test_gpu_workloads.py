@@ -1,11 +1,22 @@
-"""Parity on the paper-shaped workloads at full size, on sampled targets.
+"""Parity on the paper-shaped workloads at full size, judged by the oracle alone.
 
 - 64 uneven flat-plate problems (16^3 blocks, N_b log-uniform in [8, 1200],
-  3 components) through one lgf_batch_apply, FP32, 8 random targets per
-  problem and component against the oracle; G_L followed by E(0.25) equal to
-  the single applies bit for bit.
+  3 components), FP32, through one lgf_batch_apply:
+    * G_L: 512 random targets per problem plus, per component, the point where
+      the GPU field peaks, every component, against the FP64 direct sum
+      (Sec. 2.2, Eq. dpoisson_conv);
+    * G_L then E(0.25) (the bench step): every target point of three whole
+      problems against the oracle's E(0.25) (App. A, Eq. lgf_intfac) applied
+      to the oracle's own Poisson result, and the batch equal bit for bit to
+      the single applies on twelve problems.
 - the 512 x 256 x 256 wake domain (32^3 blocks, 3 components x 4 right-hand
-  sides), FP32, 6 random targets per field against the oracle.
+  sides), FP32: 2048 random targets, shared by the 12 fields, plus every
+  field's GPU peak point, against the direct sum.
+
+The error of a field is max |u_gpu - u_oracle| over its compared points
+divided by the largest |u_oracle| among them; the GPU's peak point is in the
+set, so the denominator is an oracle value at the field's maximum, never a
+GPU value.  Bar: 1e-5 (FP32 path).
 """
 import functools
 
@@ -17,12 +28,22 @@ import lgf_inputs as li
 import paper_1604_01814_gb300 as lgf
 pytestmark = pytest.mark.gpu
 
+TOL32 = 1e-5
 
-def rel_sampled(got_s, ref_s, field_max):
-    """max |got - ref| over the sampled targets, relative to the field's
-    largest |u| (a sample far from the sources sees a much smaller |u| than
-    the field, while FP32 transform error scales with the field)."""
-    return float(np.abs(np.asarray(got_s, np.float64) - ref_s).max() / max(np.abs(ref_s).max(), field_max))
+
+def field_errors(got, ref):
+    """got, ref: [nfields][npts] at the same points -> per-field relative error."""
+    got = np.asarray(got, np.float64)
+    return np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)
+
+
+def sample_points(oracle, p, got_fields, nsample, rng):
+    """Random target points plus each field's GPU arg-max point (lattice coords)."""
+    pts_all = oracle.block_points(p.b, p.tgt)
+    idx = set(rng.choice(pts_all.shape[0], size=min(nsample, pts_all.shape[0]), replace=False).tolist())
+    idx |= {int(np.abs(g).argmax()) for g in got_fields}
+    idx = np.array(sorted(idx))
+    return idx, pts_all[idx]
 
 
 @functools.lru_cache(maxsize=1)
@@ -30,64 +51,87 @@ def plates():
     return li.plate_batch()
 
 
-def test_plate_batch_poisson_sampled(ctx32, oracle):
-    probs = plates()
+def _batch(probs, op, alpha=0.0):
     batch = []
     for p in probs:
         f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
         u = torch.full((p.ncomp * p.tgt.shape[0] * p.b ** 3,), float("nan"), device="cuda")
-        batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, op=lgf.LGF_OP_POISSON))
+        batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, op=op, alpha=alpha))
+    return batch
+
+
+def _run(ctx, batch):
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        ctx32.batch_apply(batch, stream=s)
+        ctx.batch_apply(batch, stream=s)
     s.synchronize()
+
+
+def test_plate_batch_poisson_512_targets_per_problem(ctx32, oracle):
+    probs = plates()
+    batch = _batch(probs, lgf.LGF_OP_POISSON)
+    _run(ctx32, batch)
     rng = np.random.default_rng(33)
     worst = 0.0
-    for p, q in zip(probs, batch):
+    for k, (p, q) in enumerate(zip(probs, batch)):
         got = q["u"].cpu().numpy().reshape(p.ncomp, -1)
-        assert not np.isnan(got).any()
-        pts_all = oracle.block_points(p.b, p.tgt)
-        idx = rng.choice(pts_all.shape[0], size=8, replace=False)
-        for c in range(p.ncomp):
-            ref = oracle.poisson_direct(p.b, p.src, p.f[0, c], pts_all[idx], R=64)
-            worst = max(worst, rel_sampled(got[c, idx], ref, float(np.abs(got[c]).max())))
-    assert worst < 1e-5
+        assert not np.isnan(got).any(), k
+        idx, pts = sample_points(oracle, p, got, 512, rng)
+        ref = oracle.poisson_direct_multi(p.b, p.src, p.f[0], pts, R=64)
+        err = field_errors(got[:, idx], ref)
+        assert err.max() < TOL32, (k, err)
+        worst = max(worst, float(err.max()))
+    print(f"plate batch G_L: worst relative error {worst:.2e} over 64 problems x 3 components")
+
+
+def test_plate_batch_poisson_then_intfactor_whole_problems(ctx32, oracle):
+    probs = plates()
+    batch = _batch(probs, lgf.LGF_OP_POISSON_THEN_INTFACTOR, 0.25)
+    _run(ctx32, batch)
+    # three whole problems: the two smallest and one of about 60 blocks
+    sizes = np.array([p.tgt.shape[0] for p in probs])
+    order = np.argsort(sizes, kind="stable")
+    picks = [int(order[0]), int(order[1]), int(order[np.searchsorted(sizes[order], 60)])]
+    for k in picks:
+        p, q = probs[k], batch[k]
+        got = q["u"].cpu().numpy().reshape(p.ncomp, -1)
+        pts = oracle.block_points(p.b, p.tgt)
+        u_ref = oracle.poisson_direct_multi(p.b, p.src, p.f[0], pts, R=64)     # [3][ntgt * b^3]
+        v_ref = np.stack([oracle.intfactor_blocks(0.25, p.b, p.tgt, u_ref[c].reshape(p.tgt.shape[0], -1),
+                                                  p.tgt).reshape(-1) for c in range(p.ncomp)])
+        err = field_errors(got, v_ref)
+        assert err.max() < TOL32, (k, p.tgt.shape[0], err)
 
 
 def test_plate_batch_poisson_then_intfactor_equals_single_applies(ctx32):
     probs = plates()[:12]
-    batch, ref = [], []
-    for p in probs:
-        f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
-        n = p.ncomp * p.tgt.shape[0] * p.b ** 3
-        u = torch.full((n,), float("nan"), device="cuda")
-        batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp,
-                          op=lgf.LGF_OP_POISSON_THEN_INTFACTOR, alpha=0.25))
-        tmp = torch.empty(n, device="cuda")
-        r = torch.empty(n, device="cuda")
-        ctx32.poisson_apply(p.b, p.src, p.tgt, f, tmp, ncomp=p.ncomp)
+    batch = _batch(probs, lgf.LGF_OP_POISSON_THEN_INTFACTOR, 0.25)
+    ref = []
+    for p, q in zip(probs, batch):
+        tmp = torch.empty_like(q["u"])
+        r = torch.empty_like(q["u"])
+        ctx32.poisson_apply(p.b, p.src, p.tgt, q["f"], tmp, ncomp=p.ncomp)
         ctx32.intfactor_apply(0.25, p.b, p.tgt, p.tgt, tmp, r, ncomp=p.ncomp)
         ref.append(r)
-    s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        ctx32.batch_apply(batch, stream=s)
-    s.synchronize()
+    _run(ctx32, batch)
     for q, r in zip(batch, ref):
         assert torch.equal(q["u"], r)
 
 
-def test_wake_domain_sampled(ctx32, oracle):
+def test_wake_domain_2048_targets_per_field(ctx32, oracle):
     p = li.wake_domain()
+    nf = p.nrhs * p.ncomp
     f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
     u = torch.full_like(f, float("nan"))
     ctx32.poisson_apply(p.b, p.src, p.tgt, f, u, ncomp=p.ncomp, nrhs=p.nrhs)
     torch.cuda.synchronize()
-    got = u.cpu().numpy().reshape(p.nrhs, p.ncomp, -1)
+    got = u.cpu().numpy().reshape(nf, -1)
     del f, u
-    pts_all = oracle.block_points(p.b, p.tgt)
+    assert not np.isnan(got).any()
     rng = np.random.default_rng(44)
-    for r in range(p.nrhs):
-        for c in range(p.ncomp):
-            idx = rng.choice(pts_all.shape[0], size=6, replace=False)
-            ref = oracle.poisson_direct(p.b, p.src, p.f[r, c], pts_all[idx], R=64)
-            assert rel_sampled(got[r, c, idx], ref, float(np.abs(got[r, c]).max())) < 1e-5, (r, c)
+    idx, pts = sample_points(oracle, p, got, 2048, rng)
+    assert idx.size >= 2048
+    ref = oracle.poisson_direct_multi(p.b, p.src, p.f.reshape(nf, p.src.shape[0], -1), pts, R=64)
+    err = field_errors(got[:, idx], ref)
+    print(f"wake domain: per-field relative errors {np.array2string(err, precision=2)}")
+    assert err.max() < TOL32, err

@@ -175,6 +175,25 @@ def test_poisson_direct_linear_and_translation_invariant(oracle):
 
 
 # --------------------------------------------------------- integrating factor
+def test_poisson_direct_multi_equals_single_field_sums(oracle):
+    """The several-field direct sum (one G_L evaluation per pair, memoised per
+    |offset|, TwoSum compensation) reproduces the pinned single-field sum bit
+    for bit, through its dense G_L table and through its pointwise fallback
+    (offsets too large to tabulate), skipping exact zeros of every field."""
+    rng = np.random.default_rng(17)
+    b = 4
+    src = np.array([[0, 0, 0], [1, 0, 0], [0, 2, 1]])
+    f = rng.uniform(-1, 1, size=(3, src.shape[0], b ** 3))
+    f[:, 1, :10] = 0.0               # points that are zero in every field
+    f[0, 2, 20:40] = 0.0             # ... and in one field only
+    for shift in ((0, 0, 0), (1500, -700, 900)):   # table, then fallback (> 2^26 offsets)
+        tgt = rng.integers(-6, 12, size=(40, 3)) + np.array(shift)
+        multi = oracle.poisson_direct_multi(b, src, f, tgt, R=16)
+        for j in range(3):
+            single = oracle.poisson_direct(b, src, f[j], tgt, R=16)
+            assert np.array_equal(multi[j], single), (shift, j)
+
+
 @pytest.mark.parametrize("alpha", [0.0, 0.05, 0.1, 0.25, 0.5, 1.0, 2.0])
 def test_intfactor_weights_are_skellam(oracle, alpha):
     """e^{-2a} I_n(2a) is the Skellam(a, a) pmf: total mass 1, variance 2a."""
