@@ -339,7 +339,7 @@ def oracle_sample(w: Workload, per_problem: int, seed: int = 101):
 
 
 REF_SAMPLE = {"plates64": 16, "dense128": 1024, "wake512": 2}      # reference arm, per problem and field
-CPU_SAMPLE = {"plates64": 256, "dense128": 3072, "wake512": 16}    # cpu_baseline and the error check
+CPU_SAMPLE = {"plates64": 768, "dense128": 3072, "wake512": 16}    # cpu_baseline and the error check
 
 
 def run_reference(args, rank, world):

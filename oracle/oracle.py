@@ -25,6 +25,8 @@ it follows; the C source documents the numerical method):
   phi3               three-point kernel phi(r) (reading: Roma-Peskin-Berger)  Sec. 2.1
   ib_spread          (R g)^k(n) = sum_i g^k(i) delta_dx(x_F^k(n) - X_i)       Sec. 2.1 (operator R)
   ib_interp          (I v)^k(i) = dx^3 sum_n v^k(n) delta_dx(x_F^k(n) - X_i)  Sec. 2.1 (operator I)
+  nested_projection_stage  ip -> f -> pc -> vc of one IF-HERK stage   Sec. 3.1, Eq. nested_proj
+  force_schur        C = I H S I^dagger, S = I - G L_C^{-1} Dbar (dense)  Sec. 3.1, Eq. force_schur
 """
 from __future__ import annotations
 
@@ -473,3 +475,130 @@ def ib_interp(b: int, coords, X, v) -> np.ndarray:
                 out[:, k, i] += w * v[:, k, blk, loc]
     return out
 
+
+
+# ----------------------------------------------------------------------------
+# One IF-HERK stage's linear solve by the nested projection of Sec. 3.1
+# (Eq. nested_proj), on one flow block set D with sources and results
+# truncated to D (Table 1's truncation, reading 4).  The Poisson problems'
+# targets are D and its -x, -y, -z neighbour blocks (the cells that the
+# gradient on the faces of D reads).  Fields on D: r, u faces [3][nD][b^3];
+# cells [nD][b^3].  Markers X (stage i) and X_prev (stage i-1) in units of dx,
+# marker vectors [3][nm].  The force Schur complement's inverse is given as
+# factors: f_hat = W2 (W1 rhs), W2 = W1^T when omitted (the Cholesky form of
+# Sec. 3.2, C^-1 = W^T W).  Each step is a module function so that the
+# mutation tests can plant a mistake in one of them (`ops`).
+# ----------------------------------------------------------------------------
+def grown_backward(coords) -> np.ndarray:
+    """D followed by the blocks at -x, -y, -z of D that are not in D (sorted)."""
+    c = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
+    have = {tuple(r) for r in c}
+    extra = set()
+    for e in np.eye(3, dtype=np.int64):
+        extra |= {tuple(r) for r in c - e} - have
+    ext = np.array(sorted(extra), dtype=np.int64).reshape(-1, 3)
+    return np.concatenate([c, ext]).astype(np.int32)
+
+
+class _StageGeom:
+    def __init__(self, b, D):
+        self.b = b
+        self.D = np.asarray(D, dtype=np.int64).reshape(-1, 3)
+        self.Dm = grown_backward(self.D).astype(np.int64)
+        self.lo = self.Dm.min(axis=0)
+        hi = self.Dm.max(axis=0) + 1
+        self.shape = tuple(int(v) for v in ((hi - self.lo) * b)[::-1])
+
+    def faces_box(self, v):
+        return _vec_to_box(self.b, self.D, v, self.lo, self.shape)
+
+    def faces_on_D(self, box):
+        return _vec_from_box(self.b, self.D, box, self.lo)
+
+    def cells_box(self, q, coords):
+        return blocks_to_box(self.b, coords, q, self.lo, self.shape)[0]
+
+    def cells_on(self, box, coords):
+        return box_to_blocks(self.b, coords, box, self.lo)
+
+
+def stage_lap_inv(g: _StageGeom, q, dx, R):
+    """L_C^{-1} q = dx^2 G_L * q (Sec. 2.2): sources on the cells of D, values
+    on the cells of D and its backward neighbours."""
+    return poisson_direct(g.b, g.D, q, block_points(g.b, g.Dm), dx=dx, R=R).reshape(g.Dm.shape[0], -1)
+
+
+def stage_ip(g: _StageGeom, r, dx, R, ops):
+    """Eq. nested_proj-ip: L_C d* = -G^dagger r, and -G^dagger = Dbar (Sec. 2.1)."""
+    q = g.cells_on(ops.div_box(g.faces_box(r), dx), g.D)
+    return ops.stage_lap_inv(g, q, dx, R)
+
+
+def stage_f_rhs(g: _StageGeom, r, dstar, X, ub, alpha, dx, ops):
+    """Right side of Eq. nested_proj-f: I^i H^i [r - G d*] - u_Gamma (printed
+    H_C [r - G^dagger d*]; read as the face operators, see the readings)."""
+    v = g.faces_on_D(g.faces_box(r) - ops.grad_box(g.cells_box(dstar, g.Dm), dx))
+    w = np.stack([ops.intfactor_blocks(alpha, g.b, g.D, v[k], g.D) for k in range(3)])
+    return ops.ib_interp(g.b, g.D, X, w[None])[0] - np.asarray(ub, dtype=np.float64).reshape(3, -1)
+
+
+def stage_regularize(g: _StageGeom, X_prev, fhat, dx, ops):
+    """(I^{i-1})^dagger f_hat = dx^3 R f_hat on the faces of D (I = dx^3 R^dagger, Sec. 2.1)."""
+    return dx ** 3 * ops.ib_spread(g.b, g.D, X_prev, np.asarray(fhat).reshape(1, 3, -1), dx)[0]
+
+
+def stage_pc(g: _StageGeom, dstar, gfaces, dx, R, ops):
+    """Eq. nested_proj-pc: d_hat = d* + L_C^{-1} G^dagger (I^{i-1})^dagger f_hat,
+    G^dagger = -Dbar."""
+    q2 = -g.cells_on(ops.div_box(g.faces_box(gfaces), dx), g.D)
+    return dstar + ops.stage_lap_inv(g, q2, dx, R)
+
+
+def stage_vc(g: _StageGeom, r, dhat, gfaces, alpha, dx, ops):
+    """Eq. nested_proj-vc: u = H^i [r - G d_hat - (I^{i-1})^dagger f_hat]."""
+    v = g.faces_on_D(g.faces_box(r) - ops.grad_box(g.cells_box(dhat, g.Dm), dx) - g.faces_box(gfaces))
+    return np.stack([ops.intfactor_blocks(alpha, g.b, g.D, v[k], g.D) for k in range(3)])
+
+
+def nested_projection_stage(b: int, D, r, X_prev, X, ub, W1, W2=None, alpha: float = 0.0, dx: float = 1.0,
+                            R: int = 64, ops=None):
+    """Eq. nested_proj for one stage: ip -> f -> pc -> vc.  Returns (u [3][nD][b^3],
+    d_hat on the cells of D [nD][b^3], f_hat [3][nm])."""
+    import sys
+    ops = ops if ops is not None else sys.modules[__name__]
+    g = _StageGeom(b, D)
+    r = np.asarray(r, dtype=np.float64).reshape(3, g.D.shape[0], b ** 3)
+    dstar = ops.stage_ip(g, r, dx, R, ops)
+    rhs = ops.stage_f_rhs(g, r, dstar, X, ub, alpha, dx, ops)
+    W1 = np.asarray(W1, dtype=np.float64)
+    W2 = W1.T if W2 is None else np.asarray(W2, dtype=np.float64)
+    fhat = (W2 @ (W1 @ rhs.reshape(-1))).reshape(3, -1)
+    gf = ops.stage_regularize(g, X_prev, fhat, dx, ops)
+    dhat = ops.stage_pc(g, dstar, gf, dx, R, ops)
+    u = ops.stage_vc(g, r, dhat, gf, alpha, dx, ops)
+    return u, dhat[:g.D.shape[0]], fhat
+
+
+def force_schur(b: int, D, X_prev, X, alpha: float = 0.0, dx: float = 1.0, R: int = 64) -> np.ndarray:
+    """The force Schur complement C^i as a dense matrix, column by column, from
+    its form I^i H^i S (I^{i-1})^dagger with S = I - G L_C^{-1} Dbar (Sec. 3.1;
+    printed L_F^{-1}, read as the cell Laplacian), on the truncation of
+    nested_projection_stage.  Rows and columns in the [3][nm] order."""
+    g = _StageGeom(b, D)
+    nm = np.asarray(X).reshape(-1, 3).shape[0]
+    C = np.zeros((3 * nm, 3 * nm))
+    for j in range(3 * nm):
+        e = np.zeros(3 * nm)
+        e[j] = 1.0
+        s = stage_regularize(g, X_prev, e.reshape(3, nm), dx, sys_mod())
+        q = g.cells_on(div_box(g.faces_box(s), dx), g.D)          # Dbar s
+        p = stage_lap_inv(g, q, dx, R)                              # L_C^{-1} Dbar s
+        v = g.faces_on_D(g.faces_box(s) - grad_box(g.cells_box(p, g.Dm), dx))
+        w = np.stack([intfactor_blocks(alpha, b, g.D, v[k], g.D) for k in range(3)])
+        C[:, j] = ib_interp(b, g.D, X, w[None])[0].reshape(-1)
+    return C
+
+
+def sys_mod():
+    import sys
+    return sys.modules[__name__]

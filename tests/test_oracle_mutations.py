@@ -108,6 +108,22 @@ CASES = [
     ("interpolation with marker coordinates transposed",
      lambda o: dict(ib_interp=lambda b, c, X, v: o.ib_interp(b, c, np.asarray(X)[:, ::-1], v)),
      [(pins.test_ib_interp_exact_for_linear_fields, ())]),
+    ("stage: pressure correction with its sign flipped",
+     lambda o: dict(stage_pc=lambda g, ds, gf, dx, R, ops: 2 * ds - o.stage_pc(g, ds, gf, dx, R, ops)),
+     [(pins.test_nested_projection_satisfies_no_slip, (0.0,)),
+      (pins.test_nested_projection_is_divergence_free_inside, ())]),
+    ("stage: velocity correction without the regularised force",
+     lambda o: dict(stage_vc=lambda g, r, dh, gf, a, dx, ops: o.stage_vc(g, r, dh, 0 * gf, a, dx, ops)),
+     [(pins.test_nested_projection_satisfies_no_slip, (0.3,))]),
+    ("stage: force right side without the integrating factor",
+     lambda o: dict(stage_f_rhs=lambda g, r, ds, X, ub, a, dx, ops: o.stage_f_rhs(g, r, ds, X, ub, 0.0, dx, ops)),
+     [(pins.test_nested_projection_satisfies_no_slip, (0.0,))]),
+    ("stage: intermediate pressure with the sign of its source flipped",
+     lambda o: dict(stage_ip=lambda g, r, dx, R, ops: -o.stage_ip(g, r, dx, R, ops)),
+     [(pins.test_nested_projection_is_divergence_free_inside, ())]),
+    ("stage: regularisation without the dx^3 of I^dagger",
+     lambda o: dict(stage_regularize=lambda g, Xp, fh, dx, ops: o.stage_regularize(g, Xp, fh, dx, ops) / dx ** 3),
+     [(pins.test_nested_projection_satisfies_no_slip, (0.0,))]),
 ]
 
 

@@ -509,3 +509,55 @@ def test_ib_interp_exact_for_linear_fields(oracle):
     U = oracle.ib_interp(b, coords, X, v)
     for k in range(3):
         assert np.allclose(U[0, k], a + X @ c, rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------- nested projection stage
+def _stage_case(oracle, nb=2, b=8, nm=6, move=0.0, seed=5, r_blocks=None):
+    rng = np.random.default_rng(seed)
+    import lgf_inputs as li
+    D = li.box_blocks(nb, nb, nb)
+    c = nb * b / 2.0
+    ang = np.linspace(0, 2 * np.pi, nm, endpoint=False)
+    X = np.stack([c + 2.5 * np.cos(ang), c + 2.5 * np.sin(ang), c + 0.7 * np.cos(2 * ang)], axis=1)
+    Xp = X + move * np.array([1.0, -0.5, 0.25])
+    r = rng.uniform(-1, 1, size=(3, D.shape[0], b ** 3))
+    if r_blocks is not None:   # r only on the blocks listed
+        keep = np.zeros(D.shape[0], bool)
+        keep[r_blocks] = True
+        r[:, ~keep] = 0.0
+    ub = rng.normal(size=(3, nm))
+    return D, X, Xp, r, ub
+
+
+@pytest.mark.parametrize("move", [0.0, 0.3])
+def test_nested_projection_satisfies_no_slip(oracle, move):
+    """Row 3 of Eq. ibifherk_linsys_full, I^i u = u_Gamma: with f_hat = C^-1 rhs
+    for the force Schur complement of Eq. force_schur (built column by column
+    from its own form), the stage's u meets the no-slip condition at the
+    markers to rounding, also for a moving body (I^{i-1} != I^i, C not
+    symmetric).  A wrong sign or a dropped term in ip, f, pc or vc breaks it."""
+    b, alpha, dx = 8, 0.1, 0.5
+    D, X, Xp, r, ub = _stage_case(oracle, move=move)
+    C = oracle.force_schur(b, D, Xp, X, alpha, dx, R=16)
+    u, dhat, fhat = oracle.nested_projection_stage(b, D, r, Xp, X, ub, np.linalg.inv(C), np.eye(C.shape[0]),
+                                                   alpha=alpha, dx=dx, R=16, ops=oracle)
+    U = oracle.ib_interp(b, D, X, u[None])[0]
+    assert np.abs(U - ub).max() < 1e-10 * np.abs(ub).max()
+    assert np.abs(fhat).max() > 0.1      # the constraint force is active
+
+
+def test_nested_projection_is_divergence_free_inside(oracle):
+    """Row 2 of Eq. ibifherk_linsys_full, G^dagger u = 0: the stage's u has zero
+    discrete divergence at cells farther from the edge of D than the reach of
+    E(alpha) (its kernel falls below 1e-13 there), for any marker force."""
+    b, alpha, dx, nb = 8, 0.1, 1.0, 4
+    D, X, Xp, r, ub = _stage_case(oracle, nb=nb, nm=3, seed=6, r_blocks=[21, 22, 25, 26, 37, 38, 41, 42])
+    W = np.random.default_rng(7).normal(size=(9, 9)) * 0.3
+    u, dhat, fhat = oracle.nested_projection_stage(b, D, r, Xp, X, ub, W, alpha=alpha, dx=dx, R=16, ops=oracle)
+    box, lo = oracle.blocks_to_box(b, D, u[0])
+    ubox = np.stack([oracle.blocks_to_box(b, D, u[k], lo, box.shape)[0] for k in range(3)])
+    div = oracle.div_box(ubox, dx)
+    m = 10
+    inner = div[m:-m, m:-m, m:-m]
+    assert np.abs(inner).max() < 1e-11 * np.abs(ubox).max() / dx
+    assert np.abs(div).max() > 1e-6 * np.abs(ubox).max()    # not zero everywhere: truncation shows at the edge
