@@ -690,6 +690,10 @@ EXTRA = {
     "ib_sphere": "immersed-boundary regularisation R then interpolation I (Sec. 2.1) of 5120 icosphere markers "
                  "(radius 20 cells) on the 32 blocks of 16^3 their three-point support touches, 3 components, "
                  "FP32; throughput in marker-components per second",
+    "stage_sphere": "one IF-HERK stage solve by the nested projection (Eq. nested_proj: ip, f, pc, vc) on the "
+                    "sphere-plus-wake active set (556 blocks of 16^3), 5120 icosphere markers (radius 20 cells), "
+                    "FP32, random r, a dense 15360 x 15360 factor W (C^-1 = W^T W; random values, timing only), "
+                    "alpha 0.05; throughput in face points (3 per cell) per second",
     "kinv_sphere": "K(0.25)^{-1} on the surface blocks of the icosphere (5120 markers, radius 20 cells, 16^3 "
                    "blocks, source = target = the blocks the 3-point delta touches), 3 components, FP32; one "
                    "G_K(0.25) apply per step",
@@ -731,6 +735,23 @@ def run_extra(args, rank, world, dist):
         def step():
             ctx.ib_spread(q.b, q.src, Xm, gm, fm, stream=s)
             ctx.ib_interp(q.b, q.src, Xm, fm, Um, stream=s)
+    elif args.workload == "stage_sphere":
+        q = li.sphere_ib()
+        D = q.tgt
+        Xm = torch.tensor(li.icosphere_markers(5) * 20.0, dtype=torch.float64, device=dev)
+        nm = Xm.shape[0]
+        rng = np.random.default_rng(5)
+        r = torch.tensor(rng.uniform(-1, 1, size=3 * D.shape[0] * q.b ** 3), dtype=torch.float32, device=dev)
+        u = torch.empty_like(r)
+        dcell = torch.empty(D.shape[0] * q.b ** 3, dtype=torch.float32, device=dev)
+        ub = torch.zeros(3 * nm, dtype=torch.float32, device=dev)
+        fm = torch.empty(3 * nm, dtype=torch.float32, device=dev)
+        W = torch.randn(3 * nm, 3 * nm, device=dev, generator=torch.Generator(device=dev).manual_seed(5)) * 1e-3
+        points = float(r.numel())
+
+        def step():
+            ctx.nested_projection_stage(q.b, D, r, u, X_prev=Xm, X=Xm, ub=ub, W1=W, alpha=0.05, d=dcell, f=fm,
+                                        stream=s)
     elif args.workload == "kinv_sphere":
         q = li.sphere_ib()
         f = torch.tensor(q.f.reshape(-1), dtype=torch.float32, device=dev)

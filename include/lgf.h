@@ -243,6 +243,56 @@ LGF_API lgf_status lgf_curl_adjoint(lgf_ctx *ctx, const lgf_blockset *src, const
 LGF_API lgf_status lgf_velocity_refresh(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt,
                                         const void *u_dev, void *u_out_dev, int32_t nrhs, double dx, void *stream);
 
+/* One IF-HERK stage's linear solve by the nested projection of Sec. 3.1,
+   Eq. nested_proj (the operator-block LU of Eq. ibifherk_linsys_full):
+     ip:  L_C d* = -G^dagger r                       (Dbar = -G^dagger)
+     f :  C f_hat = I^i H [r - G d*] - u_Gamma,      f_hat = W2 (W1 rhs)
+     pc:  d_hat = d* + L_C^{-1} G^dagger (I^{i-1})^dagger f_hat
+     vc:  u = H [r - G d_hat - (I^{i-1})^dagger f_hat]
+   with H = E(alpha) (the stage's integrating factor, Eq. ibifherk_aux_1:
+   alpha = (c_i - c_{i-1}) dt / (dx^2 Re)), L_C^{-1} = dx^2 G_L * (the
+   Poisson engine), G and Dbar the staggered gradient and divergence of
+   Sec. 2.1 (cell n holds face k at (n + (1 - e_k)/2) dx:
+   (G q)_k(n) = [q(n) - q(n - e_k)] / dx, (Dbar u)(n) = sum_k [u_k(n + e_k)
+   - u_k(n)] / dx), I = dx^3 R^dagger and I^dagger = dx^3 R the IB operators
+   of lgf_ib_interp / lgf_ib_spread at the markers of stage i and i-1.  The
+   force Schur complement C is not formed: the caller passes the factors of
+   its inverse (Sec. 3.2 stores W = L^{-1} from the Cholesky factor of C, so
+   C^{-1} = W^T W: pass W1 = W, W2 = NULL; a moving body, whose C is not
+   symmetric, passes any two factors with C^{-1} = W2 W1).
+   Printed readings: Eq. nested_proj-f prints H_C [r - G^dagger d*]; the face
+   field r - G d* under the face operator H is the reading that follows from
+   Eq. nested_proj_naive.
+   Regions (the truncation of Table 1): every field lives on the one block
+   set `flow` (D); r is zero outside D; every Poisson problem has its sources
+   on the cells of D and its results on D and its -x, -y, -z neighbour blocks
+   (the cells G reads); H maps D to D; the IB operators act on the faces of D.
+   The GPU forms d_hat as L_C^{-1} Dbar (r - (I^{i-1})^dagger f_hat), equal to
+   pc by linearity.  Layouts: r_dev, u_dev [3][nD][b^3]; d_dev [nD][b^3]
+   (d_hat on the cells of D; may be NULL); X_prev_dev, X_dev [nm][3] double in
+   units of dx (device); ub_dev and f_dev [3][nm]; W1_dev, W2_dev [3nm][3nm]
+   row-major, rows and columns in the [3][nm] order.  Fields, ub, W and f in
+   the context precision.  nmarkers = 0 gives the plain projection
+   u = H [r - G d*].  Errors: LGF_EINVAL, LGF_ENOTABLE, LGF_EUNSUPPORTED,
+   LGF_ENOMEM, LGF_ECUDA. */
+typedef struct {
+    lgf_blockset flow;          /* D */
+    int64_t nmarkers;           /* nm >= 0 */
+    const double *X_prev_dev;   /* markers of stage i-1 (I^{i-1}) */
+    const double *X_dev;        /* markers of stage i (I^i) */
+    const void *ub_dev;         /* u_Gamma at stage i */
+    const void *W1_dev;         /* first factor of C^{-1} */
+    const void *W2_dev;         /* second factor, or NULL for W1^T */
+    const void *r_dev;          /* right-hand side r_k^i (faces of D) */
+    void *u_dev;                /* u_k^i (faces of D) */
+    void *d_dev;                /* pressure d_hat (cells of D) or NULL */
+    void *f_dev;                /* marker forces f_hat or NULL */
+    double alpha, dx;
+    int32_t reserved[4];        /* must be zero */
+} lgf_stage;
+
+LGF_API lgf_status lgf_nested_projection_stage(lgf_ctx *ctx, const lgf_stage *stage, void *stream);
+
 /* Immersed-boundary regularisation R (Sec. 2.1):
      f^k(n) = dx^-3 sum_i g^k(i) prod_d phi(x_F^k(n)_d - X_i,d)
    on the face lattices of `set` (face k of cell n at n + (1 - e_k)/2, in

@@ -444,7 +444,9 @@ def ib_spread(b: int, coords, X, g, dx: float = 1.0) -> np.ndarray:
     """f = R g on the face lattices of the blocks: g [nrhs][3][nm] -> [nrhs][3][nblk][b^3].
     Points outside the block set are dropped."""
     X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
-    g = np.asarray(g, dtype=np.float64).reshape(-1, 3, X.shape[0])
+    g = np.asarray(g, dtype=np.float64)
+    # no markers: one right-hand side of nothing to spread (an empty array has no size to infer it from)
+    g = g.reshape(-1, 3, X.shape[0]) if X.shape[0] else np.zeros((1, 3, 0))
     lut = _block_lookup(b, coords)
     out = np.zeros((g.shape[0], 3, len(lut), b ** 3))
     for i in range(X.shape[0]):

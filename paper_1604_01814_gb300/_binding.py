@@ -25,6 +25,7 @@ EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_in
            "lgf_kinv_lookup", "lgf_poisson_apply", "lgf_kinv_apply", "lgf_curl", "lgf_curl_adjoint",
            "lgf_velocity_refresh", "lgf_ib_spread", "lgf_ib_interp", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
            "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_ctx_stats", "lgf_cache_limits",
+           "lgf_nested_projection_stage",
            "lgf_intfactor_apply_noalloc",
            "lgf_status_string", "lgf_last_error", "lgf_version")
 
@@ -54,6 +55,14 @@ class lgf_stats(ctypes.Structure):
                 ("spectra", ctypes.c_int64), ("generation", ctypes.c_int64), ("graphs_dropped", ctypes.c_int64),
                 ("evictions", ctypes.c_int64), ("scratch_reallocs", ctypes.c_int64),
                 ("scratch_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
+
+
+class lgf_stage(ctypes.Structure):
+    _fields_ = [("flow", lgf_blockset), ("nmarkers", ctypes.c_int64), ("X_prev_dev", ctypes.c_void_p),
+                ("X_dev", ctypes.c_void_p), ("ub_dev", ctypes.c_void_p), ("W1_dev", ctypes.c_void_p),
+                ("W2_dev", ctypes.c_void_p), ("r_dev", ctypes.c_void_p), ("u_dev", ctypes.c_void_p),
+                ("d_dev", ctypes.c_void_p), ("f_dev", ctypes.c_void_p), ("alpha", ctypes.c_double),
+                ("dx", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
 
 
 class LgfError(RuntimeError):
@@ -98,6 +107,7 @@ def load(path: str = LIB_PATH):
         "lgf_profile_read": [vp, ctypes.POINTER(lgf_kernel_stat), i32, ctypes.POINTER(i32)],
         "lgf_ctx_stats": [vp, ctypes.POINTER(lgf_stats)],
         "lgf_cache_limits": [vp, i32, i32, i32],
+        "lgf_nested_projection_stage": [vp, ctypes.POINTER(lgf_stage), vp],
         "lgf_intfactor_apply_noalloc": [i32, dbl, dbl, bsp, bsp, vp, vp, i32, i32, vp, ctypes.c_char_p, i32],
         "lgf_status_string": [i32],
         "lgf_last_error": [vp],
@@ -340,6 +350,39 @@ class Context:
         return r, ma.value, mf.value
 
 
+    def nested_projection_stage(self, b: int, flow, r, u, X_prev=None, X=None, ub=None, W1=None, W2=None,
+                                alpha: float = 0.0, dx: float = 1.0, d=None, f=None, stream=None):
+        """One stage of Eq. nested_proj on the block set `flow` (see lgf.h):
+        r, u [3][nD][b^3]; d [nD][b^3]; markers X_prev, X [nm, 3] float64;
+        ub, f [3][nm]; W1, W2 [3nm, 3nm] (W2 None: W1^T)."""
+        bs, ba = _blockset(b, flow)
+        nm = 0 if X is None else int(X.shape[0])
+        if bs.nblocks:
+            self._field(r, bs.nblocks, b, 3, "r")
+            self._field(u, bs.nblocks, b, 3, "u")
+            if d is not None:
+                self._field(d, bs.nblocks, b, 1, "d")
+        if nm:
+            X = self._markers(X)
+            X_prev = self._markers(X_prev)
+            if X_prev.shape[0] != nm:
+                raise ValueError("X_prev and X must hold the same markers")
+            self._marker_values(ub, 3 * nm, "ub")
+            if f is not None:
+                self._marker_values(f, 3 * nm, "f")
+            for name, Wm in (("W1", W1), ("W2", W2)):
+                if Wm is not None and (Wm.numel() != 9 * nm * nm or Wm.dtype != self.dtype or not Wm.is_cuda
+                                       or not Wm.is_contiguous()):
+                    raise ValueError(f"{name} must be a contiguous CUDA [3nm, 3nm] tensor of the context dtype")
+            if W1 is None:
+                raise ValueError("W1 is required when there are markers")
+        st = lgf_stage(bs, nm, _ptr(X_prev) if nm else None, _ptr(X) if nm else None, _ptr(ub) if nm else None,
+                       _ptr(W1) if nm else None, _ptr(W2) if nm else None, _ptr(r), _ptr(u), _ptr(d),
+                       _ptr(f) if nm else None, float(alpha), float(dx))
+        self._check(self._L.lgf_nested_projection_stage(self._h, ctypes.byref(st), _stream_ptr(stream)),
+                    "lgf_nested_projection_stage")
+        return u
+
     def stats(self) -> dict:
         """Cache state (lgf_ctx_stats): graphs, plans, spectra, invalidations, scratch."""
         st = lgf_stats()
@@ -444,6 +487,10 @@ def lgf_ctx_stats(ctx: Context) -> dict:
 
 def lgf_cache_limits(ctx: Context, max_plans: int = -1, max_spectra: int = -1, max_graphs: int = -1):
     return ctx.cache_limits(max_plans, max_spectra, max_graphs)
+
+
+def lgf_nested_projection_stage(ctx: Context, *a, **kw):
+    return ctx.nested_projection_stage(*a, **kw)
 
 
 def lgf_intfactor_apply_noalloc(prec: str, alpha: float, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1,

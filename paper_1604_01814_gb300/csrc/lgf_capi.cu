@@ -1,9 +1,12 @@
 // C ABI of the library: argument checking, context life cycle, plan and
 // spectrum caches, the batched path and its CUDA-graph cache.
 #include <algorithm>
+#include <array>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -254,6 +257,7 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
         cudaFree(sc.D);
         cudaFree(sc.E);
         cudaFree(sc.F);
+        cudaFree(sc.G);
     }
     for (int b = 0; b < kBranches; ++b) {
         if (ctx->br[b]) cudaStreamDestroy(ctx->br[b]);
@@ -430,6 +434,108 @@ lgf_status lgf_velocity_refresh(lgf_ctx *ctx, const lgf_blockset *src, const lgf
     if ((st = curl_run(ctx, pc, u_dev, sc.E, nrhs, 1.0 / dx, s)) != LGF_OK) return st;
     if ((st = poisson_run(ctx, pp.plan, pp.spec, sc.E, sc.F, 3 * nrhs, dx, s)) != LGF_OK) return st;
     return curl_run(ctx, pa, sc.F, u_out_dev, nrhs, 1.0 / dx, s);
+}
+
+}  // extern "C"
+
+namespace {
+// D followed by the blocks at -x, -y, -z of D that are not in D (sorted): the
+// cells the gradient on the faces of D reads.
+std::vector<int32_t> grown_backward(const lgf_blockset *D)
+{
+    std::set<std::array<int, 3>> have, extra;
+    for (int t = 0; t < D->nblocks; ++t) have.insert({D->coords[3 * t], D->coords[3 * t + 1], D->coords[3 * t + 2]});
+    for (auto &c : have)
+        for (int k = 0; k < 3; ++k) {
+            std::array<int, 3> m = c;
+            --m[k];
+            if (!have.count(m)) extra.insert(m);
+        }
+    std::vector<int32_t> v(D->coords, D->coords + 3 * (size_t)D->nblocks);
+    for (auto &c : extra) v.insert(v.end(), c.begin(), c.end());
+    return v;
+}
+}  // namespace
+
+extern "C" {
+
+lgf_status lgf_nested_projection_stage(lgf_ctx *ctx, const lgf_stage *st, void *stream)
+{
+    lgf_status rc = enter(ctx);
+    if (rc != LGF_OK) return rc;
+    if (!st) return fail(ctx, LGF_EINVAL, "stage: null description");
+    const lgf_blockset *D = &st->flow;
+    if ((rc = check_blockset(ctx, D, "stage flow set")) != LGF_OK) return rc;
+    for (int i = 0; i < 4; ++i)
+        if (st->reserved[i] != 0) return fail(ctx, LGF_EINVAL, "stage: reserved fields must be zero");
+    if (!(st->dx > 0.0) || !std::isfinite(st->dx)) return fail(ctx, LGF_EINVAL, "dx must be positive and finite");
+    if (!(st->alpha >= 0.0) || !std::isfinite(st->alpha)) return fail(ctx, LGF_EINVAL, "alpha must be >= 0 and finite");
+    const int64_t nm = st->nmarkers;
+    if (nm < 0 || 3 * nm > INT32_MAX) return fail(ctx, LGF_EINVAL, "stage: bad marker count");
+    if (nm > 0 && (!st->X_dev || !st->X_prev_dev || !st->ub_dev || !st->W1_dev))
+        return fail(ctx, LGF_EINVAL, "stage: null marker array or force factor");
+    if (D->nblocks == 0) {
+        if (nm > 0 && st->f_dev)
+            LGF_CUDA(ctx, cudaMemsetAsync(st->f_dev, 0, (size_t)3 * nm * elem_size(ctx), (cudaStream_t)stream));
+        return LGF_OK;
+    }
+    if (!st->r_dev || !st->u_dev) return fail(ctx, LGF_EINVAL, "stage: null r or u");
+    if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "lgf_table_build has not been called");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int b = D->b;
+    const size_t b3 = (size_t)b * b * b, nD = (size_t)D->nblocks;
+    const std::vector<int32_t> dm = grown_backward(D);
+    const lgf_blockset Dm{b, (int32_t)(dm.size() / 3), dm.data()};
+    // plans: Dbar on D (dir +1), G from the cells of Dm to the faces of D
+    // (dir -1), L^{-1} from D to Dm, H = E(alpha) on D, the IB operators on D
+    CurlPlan *pdiv = nullptr, *pgrad = nullptr;
+    if ((rc = curl_plan(ctx, D, D, 1, &pdiv)) != LGF_OK) return rc;
+    if ((rc = curl_plan(ctx, &Dm, D, -1, &pgrad)) != LGF_OK) return rc;
+    PreparedPoisson pp;
+    if ((rc = prepare_poisson(ctx, D, &Dm, 1, 0.0, s, &pp)) != LGF_OK) return rc;
+    PreparedIntf pi;
+    if ((rc = prepare_intf(ctx, st->alpha, D, D, 3, s, &pi)) != LGF_OK) return rc;
+    IBPlan *pib = nullptr;
+    if (nm > 0 && (rc = ib_plan(ctx, D, &pib)) != LGF_OK) return rc;
+    // stage buffers: q (cells of D), dd (cells of Dm), v, w, g (faces of D),
+    // U, rhs, y, fh (3 nm each), each 256-byte aligned
+    const size_t esz = elem_size(ctx);
+    auto al = [](size_t n) { return (n + 255) & ~size_t(255); };
+    const size_t n_q = al(nD * b3 * esz), n_d = al(Dm.nblocks * b3 * esz), n_v = al(3 * nD * b3 * esz),
+                 n_m = al((size_t)3 * nm * esz + 1);
+    Scratch &sc = ctx->scr[0];
+    if ((rc = ensure_scratch(ctx, &sc.G, &sc.g, n_q + n_d + 3 * n_v + 4 * n_m)) != LGF_OK) return rc;
+    unsigned char *base = (unsigned char *)sc.G;
+    void *q = base, *dd = base + n_q, *v = base + n_q + n_d, *w = base + n_q + n_d + n_v,
+         *g = base + n_q + n_d + 2 * n_v;
+    unsigned char *mk = base + n_q + n_d + 3 * n_v;
+    void *U = mk, *rhs = mk + n_m, *y = mk + 2 * n_m, *fh = mk + 3 * n_m;
+    const double dx = st->dx;
+    // ip (Eq. nested_proj-ip): L_C d* = -G^dagger r = Dbar r
+    if ((rc = stage_div(ctx, pdiv, st->r_dev, nullptr, q, dx, s)) != LGF_OK) return rc;
+    if ((rc = poisson_run(ctx, pp.plan, pp.spec, q, dd, 1, dx, s)) != LGF_OK) return rc;
+    const void *gforce = nullptr;
+    if (nm > 0) {
+        // f (Eq. nested_proj-f): C f_hat = I^i H [r - G d*] - u_Gamma, f_hat = W2 (W1 rhs)
+        if ((rc = stage_grad(ctx, pgrad, dd, st->r_dev, nullptr, v, dx, s)) != LGF_OK) return rc;
+        if ((rc = intf_run(ctx, pi.plan, pi.w, v, w, 3, s)) != LGF_OK) return rc;
+        if ((rc = ib_run(ctx, pib, false, nm, st->X_dev, w, U, 1, 1.0, s)) != LGF_OK) return rc;
+        if ((rc = stage_force(ctx, U, st->ub_dev, st->W1_dev, st->W2_dev, rhs, y, fh, (int)(3 * nm), s)) != LGF_OK)
+            return rc;
+        // (I^{i-1})^dagger f_hat = dx^3 R f_hat: the bare kernel sum (R at dx = 1)
+        if ((rc = ib_run(ctx, pib, true, nm, st->X_prev_dev, fh, g, 1, 1.0, s)) != LGF_OK) return rc;
+        gforce = g;
+        // pc (Eq. nested_proj-pc): d_hat = d* + L_C^{-1} G^dagger g = L_C^{-1} Dbar (r - g)
+        // (one Poisson apply of the summed source, by linearity)
+        if ((rc = stage_div(ctx, pdiv, st->r_dev, g, q, dx, s)) != LGF_OK) return rc;
+        if ((rc = poisson_run(ctx, pp.plan, pp.spec, q, dd, 1, dx, s)) != LGF_OK) return rc;
+        if (st->f_dev) LGF_CUDA(ctx, cudaMemcpyAsync(st->f_dev, fh, 3 * nm * esz, cudaMemcpyDeviceToDevice, s));
+    }
+    // vc (Eq. nested_proj-vc): u = H [r - G d_hat - g]
+    if ((rc = stage_grad(ctx, pgrad, dd, st->r_dev, gforce, v, dx, s)) != LGF_OK) return rc;
+    if ((rc = intf_run(ctx, pi.plan, pi.w, v, st->u_dev, 3, s)) != LGF_OK) return rc;
+    if (st->d_dev) LGF_CUDA(ctx, cudaMemcpyAsync(st->d_dev, dd, nD * b3 * esz, cudaMemcpyDeviceToDevice, s));
+    return LGF_OK;
 }
 
 }  // extern "C"
@@ -810,7 +916,7 @@ lgf_status lgf_ctx_stats(lgf_ctx *ctx, lgf_stats *out)
     out->evictions = (int64_t)ctx->counters.plans_evicted;
     out->scratch_reallocs = (int64_t)ctx->counters.scratch_reallocs;
     int64_t bytes = 0;
-    for (const auto &sc : ctx->scr) bytes += (int64_t)(sc.a + sc.b + sc.c + sc.d + sc.e + sc.f);
+    for (const auto &sc : ctx->scr) bytes += (int64_t)(sc.a + sc.b + sc.c + sc.d + sc.e + sc.f + sc.g);
     out->scratch_bytes = bytes;
     return LGF_OK;
 }

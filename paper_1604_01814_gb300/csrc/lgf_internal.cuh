@@ -107,6 +107,8 @@ struct Scratch {
     size_t a = 0, b = 0, c = 0, d = 0;
     void *E = nullptr, *F = nullptr;   // velocity refresh: vorticity and its potential
     size_t e = 0, f = 0;
+    void *G = nullptr;                 // nested-projection stage: its fields and marker vectors
+    size_t g = 0;
 };
 
 // Block look-up for the immersed-boundary operators: dense table over the
@@ -255,6 +257,14 @@ lgf_status curl_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *
 lgf_status curl_run(lgf_ctx *ctx, const CurlPlan *pl, const void *in, void *out, int nrhs, double scale,
                     cudaStream_t s);
 std::vector<int32_t> grown_forward(const lgf_blockset *tgt);
+
+// Nested-projection stage kernels (lgf_stage.cu)
+lgf_status stage_div(lgf_ctx *ctx, const CurlPlan *pl, const void *a, const void *c, void *out, double dx,
+                     cudaStream_t s);
+lgf_status stage_grad(lgf_ctx *ctx, const CurlPlan *pl, const void *d, const void *a, const void *c, void *out,
+                      double dx, cudaStream_t s);
+lgf_status stage_force(lgf_ctx *ctx, const void *U, const void *ub, const void *W1, const void *W2, void *rhs, void *y,
+                       void *fh, int n, cudaStream_t s);
 
 // Immersed-boundary operators (lgf_ib.cu)
 lgf_status ib_plan(lgf_ctx *ctx, const lgf_blockset *set, IBPlan **out);
