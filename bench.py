@@ -230,14 +230,20 @@ FFT_SIZES = (32, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024, 
 
 
 def geometry(p):
-    """Transform-box geometry of the Poisson plan (mirrors the library's plan)."""
+    """Transform-box geometry of the Poisson plan (mirrors the library's plan:
+    even embedding, M >= 2L - 1 on the union extent L, except along x where
+    the shifted window M >= Ls + Lt - 1 is shorter and Ls <= M/2)."""
     b = p.b
     allc = np.concatenate([p.src, p.tgt])
     lo, hi = allc.min(0), allc.max(0)
     L = (hi - lo + 1) * b
-    M = [next(m for m in FFT_SIZES if m >= 2 * l - 1) for l in L]
+    nxt = lambda n: next(m for m in FFT_SIZES if m >= n)
+    M = [nxt(2 * l - 1) for l in L]
     Ls = [int(v) for v in (p.src.max(0) - p.src.min(0) + 1) * b]
     Lt = [int(v) for v in (p.tgt.max(0) - p.tgt.min(0) + 1) * b]
+    Ma = nxt(Ls[0] + Lt[0] - 1)
+    if Ma < M[0] and 2 * Ls[0] <= Ma:
+        M[0] = Ma
     return [int(m) for m in M], Ls, Lt
 
 

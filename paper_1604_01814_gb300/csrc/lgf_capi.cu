@@ -150,7 +150,7 @@ lgf_status prepare_poisson(lgf_ctx *ctx, const lgf_blockset *src, const lgf_bloc
     if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "lgf_table_build has not been called");
     lgf_status st = poisson_plan(ctx, src, tgt, &pp->plan);
     if (st != LGF_OK) return st;
-    st = poisson_spectrum(ctx, pp->plan->g.M, kalpha, &pp->spec, s);
+    st = poisson_spectrum(ctx, pp->plan->g, kalpha, &pp->spec, s);
     if (st != LGF_OK) return st;
     st = poisson_prepare_scratch(ctx, pp->plan, nfields);
     if (st != LGF_OK) return st;

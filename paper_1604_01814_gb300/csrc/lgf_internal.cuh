@@ -47,7 +47,11 @@ struct PoissonGeom {
     int64_t Astride;    // complex elements per field in scratch A
     int64_t Bstride;    // complex elements per field in scratch B
     int ldA_y;          // rows per z-plane in A (max(Ls_y, Lt_y))
-    int ldB_z;          // unused padding field (kept for alignment)
+    // embedding along x: 0 = even (M >= 2L - 1, real spectrum); 1 = shifted
+    // window (M >= Ls + Lt - 1, source and target both placed at 0, complex
+    // spectrum): h[m] = G_L(m + xc) for m < xP, G_L(m - M + xc) above
+    int xasym;
+    int xc, xP;
     double scale;       // dx^2
 };
 
@@ -92,7 +96,10 @@ struct IntfWeights {
 struct Spectrum {
     std::array<int, 3> M{};
     double alpha = 0.0;       // 0: G_L; > 0: G_K(alpha)
-    void *dev = nullptr;      // (Mz/2+1)(My/2+1)(Mx/2+1) reals, context precision, scaled by 1/(MxMyMz)
+    int xasym = 0, xc = 0, xP = 0;   // the x embedding of PoissonGeom
+    // (Mz/2+1)(My/2+1)(Mx/2+1) values, context precision, scaled by
+    // 1/(MxMyMz): reals for the even x embedding, complex for the shifted one
+    void *dev = nullptr;
     uint64_t used = 0;
     Spectrum() = default;
     Spectrum(const Spectrum &) = delete;
@@ -136,6 +143,7 @@ constexpr int kBranches = 4;   // concurrent branches of a batch
 
 struct lgf_ctx {
     lgf_options opt{};
+    bool opt_xshift = true;   // allow the shifted x embedding in new Poisson plans
     int device = 0;
     int prec = LGF_F32;
     double tol = 1e-7;
@@ -229,12 +237,13 @@ lgf_status table_build(lgf_ctx *ctx, int radius, cudaStream_t s);
 lgf_status gk_table(lgf_ctx *ctx, double alpha, const double **out, cudaStream_t s);
 lgf_status table_lookup(lgf_ctx *ctx, const double *table, const int32_t *off, int64_t n, double *out,
                         cudaStream_t s);
-lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], double *box, cudaStream_t s);
+lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], int xc, int xP, double *box,
+                         cudaStream_t s);
 lgf_status bessel_weights(lgf_ctx *ctx, double z, int nmax, double *out_dev, cudaStream_t s);
 
 // Poisson (lgf_poisson.cu)
 lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, PoissonPlan **out);
-lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum **out, cudaStream_t s);
+lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, Spectrum **out, cudaStream_t s);
 lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const void *f, void *u, int nfields,
                        double dx, cudaStream_t s);
 lgf_status poisson_prepare_scratch(lgf_ctx *ctx, const PoissonPlan *pl, int nfields);

@@ -64,6 +64,23 @@ __global__ void k_twiddles(int M, void *out, int dbl)
     }
 }
 
+// Spectrum of the shifted x window: the complex forward transform (even in
+// ky and kz) at kx <= Mx/2, ky <= My/2, kz <= Mz/2, scaled by 1/(Mx My Mz).
+template <typename T>
+__global__ void k_extract_c(const Cx<double> *__restrict__ B, Cx<T> *__restrict__ spec, int Mx, int My, int Mz)
+{
+    const int K = Mx / 2 + 1, Khy = My / 2 + 1, Khz = Mz / 2 + 1;
+    const int64_t n = (int64_t)K * Khy * Khz;
+    const double sc = 1.0 / ((double)Mx * My * Mz);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % K);
+        const int ky = (int)((i / K) % Khy);
+        const int kz = (int)(i / ((int64_t)K * Khy));
+        const Cx<double> v = B[((int64_t)kz * My + ky) * K + kx];
+        spec[i] = Cx<T>{T(v.x * sc), T(v.y * sc)};
+    }
+}
+
 // Spectrum extraction: real part of the forward transform of the embedded
 // kernel at kx <= Mx/2, ky <= My/2, kz <= Mz/2, scaled by 1/(Mx My Mz).
 template <typename T>
@@ -189,6 +206,24 @@ lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockse
         g.nbs[d] = shi[d] - slo[d] + 1;
         g.nbt[d] = thi[d] - tlo[d] + 1;
     }
+    // x: the shifted window needs only M >= Ls + Lt - 1 (every source-target
+    // offset distinct modulo M) instead of M >= 2 max|offset|; it pays where
+    // source and target extents differ (a small body and its long wake).
+    // The forward pass still skips its zero upper inputs (Ls <= M/2).
+    g.xasym = 0;
+    g.xc = 0;
+    g.xP = g.M[0] / 2;
+    {
+        const int Ma = next_fft_size(g.Ls[0] + g.Lt[0] - 1);
+        if (Ma < g.M[0] && 2 * g.Ls[0] <= Ma && ctx->opt_xshift) {
+            g.xasym = 1;
+            g.xc = (tlo[0] - slo[0]) * b;   // target start minus source start
+            g.M[0] = Ma;
+            g.xP = g.Lt[0] + (Ma - g.Ls[0] + 1 - g.Lt[0]) / 2;
+            g.s0[0] = 0;
+            g.t0[0] = 0;
+        }
+    }
     g.Kx = g.M[0] / 2 + 1;
     g.ldA_y = std::max(g.Ls[1], g.Lt[1]);
     plan->A_elems = (int64_t)std::max(g.Ls[2], g.Lt[2]) * g.ldA_y * g.Kx;
@@ -248,11 +283,15 @@ lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockse
     return LGF_OK;
 }
 
-lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum **out, cudaStream_t s)
+lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, Spectrum **out, cudaStream_t s)
 {
+    const int *M = pg.M;
     const std::array<int, 3> shape{M[0], M[1], M[2]};
-    if (Spectrum *hit = ctx->spectra.find([&](const Spectrum &q) { return q.M == shape && q.alpha == alpha; },
-                                          ctx->counters.epoch)) {
+    if (Spectrum *hit = ctx->spectra.find(
+            [&](const Spectrum &q) {
+                return q.M == shape && q.alpha == alpha && q.xasym == pg.xasym && q.xc == pg.xc && q.xP == pg.xP;
+            },
+            ctx->counters.epoch)) {
         *out = hit;
         return LGF_OK;
     }
@@ -280,7 +319,7 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum
     double *box = nullptr;
     Cx<double> *A = nullptr, *B = nullptr;
     void *spec = nullptr;
-    const size_t spec_elems = (size_t)g.Kx * (M[1] / 2 + 1) * (M[2] / 2 + 1);
+    const size_t spec_elems = (size_t)g.Kx * (M[1] / 2 + 1) * (M[2] / 2 + 1) * (pg.xasym ? 2 : 1);
     const size_t esz = ctx->prec == LGF_F64 ? 8 : 4;
     auto cleanup = [&]() {
         cudaFree(box);
@@ -294,14 +333,20 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum
         cudaFree(spec);
         return fail(ctx, LGF_ENOMEM, "poisson: kernel spectrum scratch allocation failed");
     }
-    lgf_status st = kernel_window(ctx, table, M, box, s);
+    lgf_status st = kernel_window(ctx, table, M, pg.xc, pg.xP, box, s);
     if (st == LGF_OK)
         st = run_passes<double>(ctx, g, box, nullptr, A, B, nullptr, 1, M[0], true, s);
     if (st == LGF_OK) {
-        if (esz == 8)
+        if (pg.xasym) {
+            if (esz == 8)
+                k_extract_c<double><<<152 * 4, 256, 0, s>>>(B, (Cx<double> *)spec, M[0], M[1], M[2]);
+            else
+                k_extract_c<float><<<152 * 4, 256, 0, s>>>(B, (Cx<float> *)spec, M[0], M[1], M[2]);
+        } else if (esz == 8) {
             k_extract<double><<<152 * 4, 256, 0, s>>>(B, (double *)spec, M[0], M[1], M[2]);
-        else
+        } else {
             k_extract<float><<<152 * 4, 256, 0, s>>>(B, (float *)spec, M[0], M[1], M[2]);
+        }
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(ctx, e, "poisson: kernel spectrum");
@@ -314,6 +359,9 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const int M[3], double alpha, Spectrum
     auto sp = std::make_unique<Spectrum>();
     sp->M = shape;
     sp->alpha = alpha;
+    sp->xasym = pg.xasym;
+    sp->xc = pg.xc;
+    sp->xP = pg.xP;
     sp->dev = spec;
     *out = ctx->spectra.insert(std::move(sp), ctx->counters.epoch, [&] { before_evict(ctx); },
                                &ctx->counters.plans_evicted);

@@ -14,6 +14,8 @@
 // The inverse sweep mirrors this (adjoint stages, conjugate twiddles).  One
 // shared-memory transpose per stage boundary, one __syncthreads per boundary.
 #pragma once
+#include <type_traits>
+
 #include "lgf_internal.cuh"
 
 namespace lgf {
@@ -369,11 +371,15 @@ struct ConvOcc {
     static constexpr int value = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 320 || ML == 384 || ML == 512 ? 3 : ML == 640 || ML == 1536 || ML == 2560 || ML == 3072 ? 2 : 1) : 1;
 };
 
-template <typename T, int ML, int W>
-__global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML>::value) k_col_convolve(Cx<T> *__restrict__ B, const T *__restrict__ spec,
+// CPLX: the spectrum of the shifted x window (complex values, complex
+// multiply); otherwise the real spectrum of the even embedding.
+template <typename T, int ML, int W, bool CPLX>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML>::value) k_col_convolve(Cx<T> *__restrict__ B, const void *__restrict__ specv,
                                                                       int K, int My, int s0, int ns, int t0, int nt,
                                                                       int64_t field, const Cx<T> *__restrict__ twg)
 {
+    using SpecT = typename std::conditional<CPLX, Cx<T>, T>::type;
+    const SpecT *__restrict__ spec = reinterpret_cast<const SpecT *>(specv);
     using P = Plan<ML>;
     constexpr int M = P::M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -422,16 +428,16 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML>::value) k_co
     constexpr int S = M / RL;   // frequency step of the last stage's digit
     const int Khy = My / 2 + 1;
     const int kyr = ky <= My - ky ? ky : My - ky;
-    const T *sp = spec + (int64_t)kyr * K + kx;
+    const SpecT *sp = spec + (int64_t)kyr * K + kx;
     const int64_t sp_plane = (int64_t)Khy * K;
 #pragma unroll
     for (int g = t; g < P::GL; g += P::TPC) {
         // frequency of digit q: kb + q S; its mirror M - kb - q S once past M/2
         const int kb = freq_of<ML>(g * P::RL);
-        const T *spl = sp + (int64_t)kb * sp_plane;
-        const T *sph = sp + (int64_t)(M - kb) * sp_plane;
+        const SpecT *spl = sp + (int64_t)kb * sp_plane;
+        const SpecT *sph = sp + (int64_t)(M - kb) * sp_plane;
         Cx<T> c[RL];
-        T gk[RL];
+        SpecT gk[RL];
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
             gk[q] = q < RL / 2 ? spl[(int64_t)(q * S) * sp_plane] : sph[-(int64_t)(q * S) * sp_plane];
@@ -440,8 +446,12 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML>::value) k_co
         Dft<RL, -1, T>::run(c);
 #pragma unroll
         for (int q = 0; q < RL; ++q) {
-            c[q].x *= gk[q];
-            c[q].y *= gk[q];
+            if constexpr (CPLX) {
+                c[q] = cmul(c[q], gk[q]);
+            } else {
+                c[q].x *= gk[q];
+                c[q].y *= gk[q];
+            }
         }
         Dft<RL, 1, T>::run(c);
 #pragma unroll
@@ -580,7 +590,10 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward(const T *__
 
 // Inverse: rows (y, y+1) of target plane z from their half spectra; x in
 // [t0x, t0x + Ltx) scaled by dx^2 and scattered to the target block layout.
-template <typename T, int ML, int LPC>
+// HALF_OUT: the target x lies in [0, M/2) (even embedding), so only the
+// lower half of the last stage's outputs is formed; otherwise (the shifted x
+// window, targets up to M) every output is.
+template <typename T, int ML, int LPC, bool HALF_OUT>
 __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T> *__restrict__ A, T *__restrict__ u,
                                                                        PoissonGeom g, const Cx<T> *__restrict__ twg,
                                                                        int npairs, int lb)
@@ -651,16 +664,16 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T>
     const int *mrow = g.tgtmap + ((zi >> lb) * g.nbt[1] + (yi >> lb)) * g.nbt[0];
     const int inner = (((zi & bm) << lb) + (yi & bm)) << lb;
     constexpr int R0 = P::R0;
-    // target x lies in [0, M/2): only the lower half of the last outputs
+    constexpr int NOUT = HALF_OUT ? R0 / 2 : R0;
 #pragma unroll
     for (int gg = t; gg < P::G0; gg += P::TPC) {
         Cx<T> a[R0];
 #pragma unroll
         for (int q = 0; q < R0; ++q) a[q] = s[ad(l, q * P::G0 + gg)];
-        dit_group<P::R0, 1, true>(a, gg, tw);
+        dit_group<P::R0, 1, HALF_OUT>(a, gg, tw);
         const int xr = gg - g.t0[0];
 #pragma unroll
-        for (int p = 0; p < R0 / 2; ++p) {
+        for (int p = 0; p < NOUT; ++p) {
             const int xi = xr + p * P::G0;
             if ((unsigned)xi >= (unsigned)g.Lt[0]) continue;
             const int bi0 = mrow[xi >> lb];
@@ -763,9 +776,10 @@ lgf_status row_inverse_m(lgf_ctx *ctx, const PoissonGeom &g, const Cx<T> *A, T *
                          int lb, cudaStream_t s)
 {
     using C = RowCfg<T, ML>;
-    auto kern = k_row_inverse<T, ML, C::LPC>;
-    if (g.t0[0] < 0 || 2 * (g.t0[0] + g.Lt[0]) > g.M[0])
-        return fail(ctx, LGF_EINVAL, "row inverse: target beyond half the transform length");
+    auto kern = k_row_inverse<T, ML, C::LPC, true>;
+    if (g.t0[0] < 0 || g.t0[0] + g.Lt[0] > g.M[0])
+        return fail(ctx, LGF_EINVAL, "row inverse: target beyond the transform length");
+    if (2 * (g.t0[0] + g.Lt[0]) > g.M[0]) kern = k_row_inverse<T, ML, C::LPC, false>;
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
     const int npairs = (g.Lt[1] / 2) * g.Lt[2];
@@ -826,7 +840,7 @@ lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T 
                           cudaStream_t s)
 {
     using C = ColCfg<T, ML>;
-    auto kern = k_col_convolve<T, ML, C::W>;
+    auto kern = g.xasym ? k_col_convolve<T, ML, C::W, true> : k_col_convolve<T, ML, C::W, false>;
     if (g.s0[2] < 0 || g.t0[2] < 0 || 2 * (g.s0[2] + g.Ls[2]) > g.M[2] || 2 * (g.t0[2] + g.Lt[2]) > g.M[2])
         return fail(ctx, LGF_EINVAL, "z pass: planes beyond half the transform length");
     lgf_status st = set_smem(ctx, kern, C::SMEM);

@@ -209,3 +209,31 @@ def test_longest_lengths_sampled(prec, nbx, length, ctx64, ctx32, oracle):
     idx = rng.choice(pts.shape[0], size=300, replace=False)
     ref = oracle.poisson_direct(b, src, f[0, 0], pts[idx], R=64)
     assert rel_linf(got[idx], ref) < TOL[prec]
+
+
+def _line_problem(seed, b, src_x, tgt_x, yz=((0, 0), (0, 1)), ncomp=1, nrhs=1):
+    """Blocks along x: sources at src_x (y, z from yz[0]), targets at tgt_x (y, z
+    from yz[1] and its neighbour row), f ~ U[-1, 1]."""
+    rng = np.random.default_rng(seed)
+    src = np.array([[x, yz[0][0], yz[0][1]] for x in src_x], dtype=np.int32)
+    tgt = np.array([[x, yz[1][0] + dy, yz[1][1]] for x in tgt_x for dy in (0, 1)], dtype=np.int32)
+    f = rng.uniform(-1, 1, size=(nrhs, ncomp, src.shape[0], b ** 3))
+    return li.Problem("line", b, src, tgt, f)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("case", ["body_and_wake", "source_after_target", "far_apart", "long_source"])
+def test_shifted_x_window_every_point(prec, case, ctx64, ctx32, oracle):
+    """Source and target extents along x that differ: the plan embeds x with
+    the shifted window (M >= Ls + Lt - 1, complex spectrum) where that is
+    shorter than the even one, with targets past M/2 (every output of the
+    inverse x stage formed); a long source keeps the even embedding."""
+    ctx = ctx64 if prec == "f64" else ctx32
+    b = 8
+    p = {"body_and_wake": _line_problem(21, b, [0, 1], range(-1, 11), ncomp=2),
+         "source_after_target": _line_problem(22, b, [10, 11], range(0, 10), yz=((1, 0), (0, 0))),
+         "far_apart": _line_problem(23, b, [0], range(6, 10), nrhs=2),
+         "long_source": _line_problem(24, b, range(0, 6), [3], yz=((0, 0), (0, 0)))}[case]
+    got = run_poisson(ctx, p)
+    ref = oracle_fields(oracle, p)
+    assert rel_linf(got, ref) < TOL[prec]
