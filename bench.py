@@ -230,9 +230,10 @@ FFT_SIZES = (32, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024, 
 
 
 def geometry(p):
-    """Transform-box geometry of the Poisson plan (mirrors the library's plan:
-    even embedding, M >= 2L - 1 on the union extent L, except along x where
-    the shifted window M >= Ls + Lt - 1 is shorter and Ls <= M/2)."""
+    """Transform-box geometry of the Poisson plan (mirrors the library's
+    default plan: even embedding, M >= 2L - 1 on the union extent L, except
+    along x and y where the shifted window M >= Ls + Lt - 1 is shorter and
+    Ls <= M/2)."""
     b = p.b
     allc = np.concatenate([p.src, p.tgt])
     lo, hi = allc.min(0), allc.max(0)
@@ -241,9 +242,10 @@ def geometry(p):
     M = [nxt(2 * l - 1) for l in L]
     Ls = [int(v) for v in (p.src.max(0) - p.src.min(0) + 1) * b]
     Lt = [int(v) for v in (p.tgt.max(0) - p.tgt.min(0) + 1) * b]
-    Ma = nxt(Ls[0] + Lt[0] - 1)
-    if Ma < M[0] and 2 * Ls[0] <= Ma:
-        M[0] = Ma
+    for d in (0, 1):
+        Ma = nxt(Ls[d] + Lt[d] - 1)
+        if Ma < M[d] and 2 * Ls[d] <= Ma:
+            M[d] = Ma
     return [int(m) for m in M], Ls, Lt
 
 

@@ -47,17 +47,34 @@ struct PoissonGeom {
     int64_t Astride;    // complex elements per field in scratch A
     int64_t Bstride;    // complex elements per field in scratch B
     int ldA_y;          // rows per z-plane in A (max(Ls_y, Lt_y))
-    // embedding along x: 0 = even (M >= 2L - 1, real spectrum); 1 = shifted
-    // window (M >= Ls + Lt - 1, source and target both placed at 0, complex
-    // spectrum): h[m] = G_L(m + xc) for m < xP, G_L(m - M + xc) above
-    int xasym;
-    int xc, xP;
+    // embedding along x and y: 0 = even (M >= 2L - 1 on the union extent,
+    // real spectrum along that axis); 1 = shifted window (M >= Ls + Lt - 1,
+    // source and target both placed at 0, complex spectrum):
+    // h[m] = G_L(m + c) for m < P, G_L(m - M + c) above.  z is always even.
+    int xasym, xc, xP;
+    int yasym, yc, yP;
+    int zvar;           // z-pass variant: 0 default, 1 one more CTA per SM (tighter register cap)
     double scale;       // dx^2
+};
+
+// The free choices of a Poisson plan (the tuner's knobs).
+struct PoissonChoice {
+    int shift[2] = {0, 0};   // x, y: shifted window instead of the even embedding
+    int bump[3] = {0, 0, 0}; // transform length: the bump-th supported length above the smallest valid one
+    int zvar = 0;
+    bool operator==(const PoissonChoice &o) const
+    {
+        return shift[0] == o.shift[0] && shift[1] == o.shift[1] && bump[0] == o.bump[0] && bump[1] == o.bump[1] &&
+               bump[2] == o.bump[2] && zvar == o.zvar;
+    }
 };
 
 struct PoissonPlan {
     int b = 0;
     std::vector<int32_t> src, tgt;   // block coordinates, for cache matching
+    int slo[3], shi[3], tlo[3], thi[3];   // block extents of the source and target sets
+    PoissonChoice choice;            // the geometry's free choices (default or tuned)
+    int tuned_nf = 0;                // field count the choice was tuned for (0: not tuned)
     PoissonGeom g{};
     int *srcmap_dev = nullptr, *tgtmap_dev = nullptr;
     unsigned long long *srcrow_dev = nullptr, *tgtrow_dev = nullptr;
@@ -96,7 +113,8 @@ struct IntfWeights {
 struct Spectrum {
     std::array<int, 3> M{};
     double alpha = 0.0;       // 0: G_L; > 0: G_K(alpha)
-    int xasym = 0, xc = 0, xP = 0;   // the x embedding of PoissonGeom
+    int xasym = 0, xc = 0, xP = 0;   // the x and y embeddings of PoissonGeom
+    int yasym = 0, yc = 0, yP = 0;
     // (Mz/2+1)(My/2+1)(Mx/2+1) values, context precision, scaled by
     // 1/(MxMyMz): reals for the even x embedding, complex for the shifted one
     void *dev = nullptr;
@@ -237,12 +255,20 @@ lgf_status table_build(lgf_ctx *ctx, int radius, cudaStream_t s);
 lgf_status gk_table(lgf_ctx *ctx, double alpha, const double **out, cudaStream_t s);
 lgf_status table_lookup(lgf_ctx *ctx, const double *table, const int32_t *off, int64_t n, double *out,
                         cudaStream_t s);
-lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], int xc, int xP, double *box,
-                         cudaStream_t s);
+lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], int xc, int xP, int yc, int yP,
+                         double *box, cudaStream_t s);
 lgf_status bessel_weights(lgf_ctx *ctx, double z, int nmax, double *out_dev, cudaStream_t s);
 
 // Poisson (lgf_poisson.cu)
 lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, PoissonPlan **out);
+// The geometry of `ch` for the plan's block extents (false: the choice is not
+// valid for them); fills g's sizes, offsets and embeddings, *A, *B the
+// scratch elements per field.
+bool poisson_geometry(const PoissonPlan &pl, const PoissonChoice &ch, PoissonGeom *g, int64_t *A, int64_t *B);
+// Default choice: the shifted window on x and y where it is shorter.
+PoissonChoice poisson_default_choice(const PoissonPlan &pl, bool allow_shift);
+// Apply a choice to the plan (geometry and scratch sizes).
+void poisson_set_choice(PoissonPlan *pl, const PoissonChoice &ch);
 lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, Spectrum **out, cudaStream_t s);
 lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const void *f, void *u, int nfields,
                        double dx, cudaStream_t s);

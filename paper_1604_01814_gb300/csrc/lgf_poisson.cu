@@ -29,14 +29,93 @@
 
 namespace lgf {
 
-int next_fft_size(int n)
+namespace {
+// 2^k, 3 * 2^k and 5 * 2^k: the box pays at most 1.34x its extent per axis
+const int kFftSizes[] = {32,  64,  80,  96,   128,  160,  192,  256,  320,  384,
+                         512, 640, 768, 1024, 1280, 1536, 2048, 2560, 3072, 4096};
+constexpr int kNumFftSizes = sizeof(kFftSizes) / sizeof(kFftSizes[0]);
+
+// The bump-th supported length above the smallest one >= n (2 kMaxFft if none).
+int fft_size_bumped(int n, int bump)
 {
-    // 2^k, 3 * 2^k and 5 * 2^k: the box pays at most 1.34x its extent per axis
-    static const int sizes[] = {32,  64,  80,  96,   128,  160,  192,  256,  320,  384,
-                                512, 640, 768, 1024, 1280, 1536, 2048, 2560, 3072, 4096};
-    for (int m : sizes)
-        if (m >= n) return m;
-    return 2 * kMaxFft;   // beyond the largest supported length: the plan rejects it
+    for (int i = 0; i < kNumFftSizes; ++i)
+        if (kFftSizes[i] >= n) return i + bump < kNumFftSizes ? kFftSizes[i + bump] : 2 * kMaxFft;
+    return 2 * kMaxFft;
+}
+}  // namespace
+
+int next_fft_size(int n) { return fft_size_bumped(n, 0); }
+
+bool poisson_geometry(const PoissonPlan &pl, const PoissonChoice &ch, PoissonGeom *gp, int64_t *A, int64_t *B)
+{
+    PoissonGeom &g = *gp;
+    const int b = pl.b;
+    g.b = b;
+    for (int d = 0; d < 3; ++d) {
+        const int lo = std::min(pl.slo[d], pl.tlo[d]), hi = std::max(pl.shi[d], pl.thi[d]);
+        const int64_t L = ((int64_t)hi - lo + 1) * b;
+        g.Ls[d] = (pl.shi[d] - pl.slo[d] + 1) * b;
+        g.Lt[d] = (pl.thi[d] - pl.tlo[d] + 1) * b;
+        g.nbs[d] = pl.shi[d] - pl.slo[d] + 1;
+        g.nbt[d] = pl.thi[d] - pl.tlo[d] + 1;
+        const bool shift = d < 2 && ch.shift[d];
+        if (!shift) {
+            // even embedding on the union extent: every offset within +-(L - 1)
+            if (L > kMaxFft / 2) return false;
+            g.M[d] = fft_size_bumped((int)(2 * L - 1), ch.bump[d]);
+            g.s0[d] = (pl.slo[d] - lo) * b;
+            g.t0[d] = (pl.tlo[d] - lo) * b;
+        } else {
+            // shifted window: the Ls + Lt - 1 distinct offsets, source and
+            // target both at 0; the forward pass keeps its half-zero inputs
+            g.M[d] = fft_size_bumped(g.Ls[d] + g.Lt[d] - 1, ch.bump[d]);
+            if (2 * g.Ls[d] > g.M[d]) return false;
+            g.s0[d] = 0;
+            g.t0[d] = 0;
+        }
+        if (g.M[d] > kMaxFft) return false;
+    }
+    g.xasym = ch.shift[0];
+    g.xc = ch.shift[0] ? (pl.tlo[0] - pl.slo[0]) * b : 0;
+    g.xP = ch.shift[0] ? g.Lt[0] + (g.M[0] - g.Ls[0] + 1 - g.Lt[0]) / 2 : g.M[0] / 2;
+    g.yasym = ch.shift[1];
+    g.yc = ch.shift[1] ? (pl.tlo[1] - pl.slo[1]) * b : 0;
+    g.yP = ch.shift[1] ? g.Lt[1] + (g.M[1] - g.Ls[1] + 1 - g.Lt[1]) / 2 : g.M[1] / 2;
+    g.zvar = ch.zvar;
+    g.Kx = g.M[0] / 2 + 1;
+    g.ldA_y = std::max(g.Ls[1], g.Lt[1]);
+    *A = (int64_t)std::max(g.Ls[2], g.Lt[2]) * g.ldA_y * g.Kx;
+    *B = (int64_t)std::max(g.Ls[2], g.Lt[2]) * g.M[1] * g.Kx;
+    return true;
+}
+
+PoissonChoice poisson_default_choice(const PoissonPlan &pl, bool allow_shift)
+{
+    PoissonChoice ch;
+    if (!allow_shift) return ch;
+    // the shifted window along x and y where it gives a shorter transform
+    // (it pays where source and target extents differ: a small body and its
+    // long wake)
+    for (int d = 0; d < 2; ++d) {
+        PoissonChoice e = ch, s = ch;
+        s.shift[d] = 1;
+        PoissonGeom ge{}, gs{};
+        int64_t a, bb;
+        if (poisson_geometry(pl, s, &gs, &a, &bb) && poisson_geometry(pl, e, &ge, &a, &bb) && gs.M[d] < ge.M[d])
+            ch.shift[d] = 1;
+    }
+    return ch;
+}
+
+void poisson_set_choice(PoissonPlan *pl, const PoissonChoice &ch)
+{
+    PoissonGeom g = pl->g;   // keeps the device maps and strides
+    int64_t A = 0, B = 0;
+    poisson_geometry(*pl, ch, &g, &A, &B);
+    pl->g = g;
+    pl->choice = ch;
+    pl->A_elems = A;
+    pl->B_elems = B;
 }
 
 Spectrum::~Spectrum() { cudaFree(dev); }
@@ -64,12 +143,14 @@ __global__ void k_twiddles(int M, void *out, int dbl)
     }
 }
 
-// Spectrum of the shifted x window: the complex forward transform (even in
-// ky and kz) at kx <= Mx/2, ky <= My/2, kz <= Mz/2, scaled by 1/(Mx My Mz).
+// Spectrum of a shifted window: the complex forward transform at
+// kx <= Mx/2, ky < nky (My/2 + 1 when the window is even in y, My when it
+// is shifted in y), kz <= Mz/2 (even in z), scaled by 1/(Mx My Mz).
 template <typename T>
-__global__ void k_extract_c(const Cx<double> *__restrict__ B, Cx<T> *__restrict__ spec, int Mx, int My, int Mz)
+__global__ void k_extract_c(const Cx<double> *__restrict__ B, Cx<T> *__restrict__ spec, int Mx, int My, int Mz,
+                            int nky)
 {
-    const int K = Mx / 2 + 1, Khy = My / 2 + 1, Khz = Mz / 2 + 1;
+    const int K = Mx / 2 + 1, Khy = nky, Khz = Mz / 2 + 1;
     const int64_t n = (int64_t)K * Khy * Khz;
     const double sc = 1.0 / ((double)Mx * My * Mz);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -130,7 +211,11 @@ lgf_status run_passes(lgf_ctx *ctx, const PoissonGeom &g, const T *f, T *u, Cx<T
     if (spectrum_mode)
         return launch_col_forward<T>(ctx, Mz, K, My, nf, B, B, 0, Mz, planeB, planeB, K, K, g.Bstride, g.Bstride, twz,
                                      pk::RowFlags{}, s, "spectrum_z_forward");
-    if ((st = launch_col_convolve<T>(ctx, g, B, spec, twz, nf, s)) != LGF_OK) return st;
+    // the z pass for the spectrum's layout (even, shifted x, shifted y)
+    st = g.yasym ? launch_col_convolve<T, 2>(ctx, g, B, spec, twz, nf, s)
+       : g.xasym ? launch_col_convolve<T, 1>(ctx, g, B, spec, twz, nf, s)
+                 : launch_col_convolve<T, 0>(ctx, g, B, spec, twz, nf, s);
+    if (st != LGF_OK) return st;
     if ((st = launch_col_inverse<T>(ctx, My, K, g.Lt[2], nf, B, A, g.t0[1], g.Lt[1], K, K, planeB, planeA, g.Bstride,
                                     g.Astride, twy, s, "poisson_y_inverse")) != LGF_OK)
         return st;
@@ -190,44 +275,21 @@ lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockse
     plan->b = b;
     plan->src = sv;
     plan->tgt = tv;
-    PoissonGeom &g = plan->g;
-    g.b = b;
     for (int d = 0; d < 3; ++d) {
+        plan->slo[d] = slo[d];
+        plan->shi[d] = shi[d];
+        plan->tlo[d] = tlo[d];
+        plan->thi[d] = thi[d];
         lo[d] = std::min(slo[d], tlo[d]);
         hi[d] = std::max(shi[d], thi[d]);
-        const int64_t L = ((int64_t)hi[d] - lo[d] + 1) * b;
-        if (L > kMaxFft / 2)
+        if (((int64_t)hi[d] - lo[d] + 1) * b > kMaxFft / 2)
             return fail(ctx, LGF_EUNSUPPORTED, "poisson: union of source and target spans more than 2048 points");
-        g.M[d] = next_fft_size((int)(2 * L - 1));
-        g.s0[d] = (slo[d] - lo[d]) * b;
-        g.Ls[d] = (shi[d] - slo[d] + 1) * b;
-        g.t0[d] = (tlo[d] - lo[d]) * b;
-        g.Lt[d] = (thi[d] - tlo[d] + 1) * b;
-        g.nbs[d] = shi[d] - slo[d] + 1;
-        g.nbt[d] = thi[d] - tlo[d] + 1;
     }
-    // x: the shifted window needs only M >= Ls + Lt - 1 (every source-target
-    // offset distinct modulo M) instead of M >= 2 max|offset|; it pays where
-    // source and target extents differ (a small body and its long wake).
-    // The forward pass still skips its zero upper inputs (Ls <= M/2).
-    g.xasym = 0;
-    g.xc = 0;
-    g.xP = g.M[0] / 2;
-    {
-        const int Ma = next_fft_size(g.Ls[0] + g.Lt[0] - 1);
-        if (Ma < g.M[0] && 2 * g.Ls[0] <= Ma && ctx->opt_xshift) {
-            g.xasym = 1;
-            g.xc = (tlo[0] - slo[0]) * b;   // target start minus source start
-            g.M[0] = Ma;
-            g.xP = g.Lt[0] + (Ma - g.Ls[0] + 1 - g.Lt[0]) / 2;
-            g.s0[0] = 0;
-            g.t0[0] = 0;
-        }
-    }
-    g.Kx = g.M[0] / 2 + 1;
-    g.ldA_y = std::max(g.Ls[1], g.Lt[1]);
-    plan->A_elems = (int64_t)std::max(g.Ls[2], g.Lt[2]) * g.ldA_y * g.Kx;
-    plan->B_elems = (int64_t)std::max(g.Ls[2], g.Lt[2]) * g.M[1] * g.Kx;
+    PoissonGeom &g = plan->g;
+    const PoissonChoice ch = poisson_default_choice(*plan, ctx->opt_xshift);
+    if (!poisson_geometry(*plan, ch, &g, &plan->A_elems, &plan->B_elems))
+        return fail(ctx, LGF_EUNSUPPORTED, "poisson: no supported transform length for the block sets");
+    plan->choice = ch;
     std::vector<int> smap((size_t)g.nbs[0] * g.nbs[1] * g.nbs[2], -1);
     std::vector<int> tmap((size_t)g.nbt[0] * g.nbt[1] * g.nbt[2], -1);
     for (int i = 0; i < src->nblocks; ++i) {
@@ -289,7 +351,8 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, S
     const std::array<int, 3> shape{M[0], M[1], M[2]};
     if (Spectrum *hit = ctx->spectra.find(
             [&](const Spectrum &q) {
-                return q.M == shape && q.alpha == alpha && q.xasym == pg.xasym && q.xc == pg.xc && q.xP == pg.xP;
+                return q.M == shape && q.alpha == alpha && q.xasym == pg.xasym && q.xc == pg.xc && q.xP == pg.xP &&
+                       q.yasym == pg.yasym && q.yc == pg.yc && q.yP == pg.yP;
             },
             ctx->counters.epoch)) {
         *out = hit;
@@ -319,7 +382,11 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, S
     double *box = nullptr;
     Cx<double> *A = nullptr, *B = nullptr;
     void *spec = nullptr;
-    const size_t spec_elems = (size_t)g.Kx * (M[1] / 2 + 1) * (M[2] / 2 + 1) * (pg.xasym ? 2 : 1);
+    // layouts: even x and y: reals [kz][ky <= My/2][kx]; shifted x: complex,
+    // same shape; shifted y: complex [kz][ky < My][kx] (no symmetry in ky)
+    const int nky = pg.yasym ? M[1] : M[1] / 2 + 1;
+    const bool cplx = pg.xasym || pg.yasym;
+    const size_t spec_elems = (size_t)g.Kx * nky * (M[2] / 2 + 1) * (cplx ? 2 : 1);
     const size_t esz = ctx->prec == LGF_F64 ? 8 : 4;
     auto cleanup = [&]() {
         cudaFree(box);
@@ -333,15 +400,15 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, S
         cudaFree(spec);
         return fail(ctx, LGF_ENOMEM, "poisson: kernel spectrum scratch allocation failed");
     }
-    lgf_status st = kernel_window(ctx, table, M, pg.xc, pg.xP, box, s);
+    lgf_status st = kernel_window(ctx, table, M, pg.xc, pg.xP, pg.yc, pg.yP, box, s);
     if (st == LGF_OK)
         st = run_passes<double>(ctx, g, box, nullptr, A, B, nullptr, 1, M[0], true, s);
     if (st == LGF_OK) {
-        if (pg.xasym) {
+        if (cplx) {
             if (esz == 8)
-                k_extract_c<double><<<152 * 4, 256, 0, s>>>(B, (Cx<double> *)spec, M[0], M[1], M[2]);
+                k_extract_c<double><<<152 * 4, 256, 0, s>>>(B, (Cx<double> *)spec, M[0], M[1], M[2], nky);
             else
-                k_extract_c<float><<<152 * 4, 256, 0, s>>>(B, (Cx<float> *)spec, M[0], M[1], M[2]);
+                k_extract_c<float><<<152 * 4, 256, 0, s>>>(B, (Cx<float> *)spec, M[0], M[1], M[2], nky);
         } else if (esz == 8) {
             k_extract<double><<<152 * 4, 256, 0, s>>>(B, (double *)spec, M[0], M[1], M[2]);
         } else {
@@ -362,6 +429,9 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, S
     sp->xasym = pg.xasym;
     sp->xc = pg.xc;
     sp->xP = pg.xP;
+    sp->yasym = pg.yasym;
+    sp->yc = pg.yc;
+    sp->yP = pg.yP;
     sp->dev = spec;
     *out = ctx->spectra.insert(std::move(sp), ctx->counters.epoch, [&] { before_evict(ctx); },
                                &ctx->counters.plans_evicted);

@@ -289,9 +289,10 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_forward(const Cx<T> *
 
 // Inverse along the column: spectrum rows (natural order, row k at
 // in + k * rs) in; rows [lo, lo + n) of the result written to
-// out + (m - lo) * os.  The written rows lie in [0, M/2), so the last stage
-// forms only the lower half of its outputs.
-template <typename T, int ML, int W>
+// out + (m - lo) * os.  HALF_OUT: the written rows lie in [0, M/2), so the
+// last stage forms only the lower half of its outputs (otherwise, the
+// shifted y window with targets past M/2, all of them).
+template <typename T, int ML, int W, bool HALF_OUT>
 __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
                                                                      int K, int nplanes, int lo, int n, int64_t rs,
                                                                      int64_t os, int64_t in_plane, int64_t out_plane,
@@ -337,18 +338,19 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
         __syncthreads();
     }
     constexpr int R0 = P::R0;
+    constexpr int NOUT = HALF_OUT ? R0 / 2 : R0;
     const int64_t ostep = (int64_t)P::G0 * os;
 #pragma unroll
     for (int g = t; g < P::G0; g += P::TPC) {
         Cx<T> a[R0];
 #pragma unroll
         for (int q = 0; q < R0; ++q) a[q] = s[ad(w, q * P::G0 + g)];
-        dit_group<P::R0, 1, true>(a, g, tw);
+        dit_group<P::R0, 1, HALF_OUT>(a, g, tw);
         if (live) {
             const int r = g - lo;
             int64_t off = (int64_t)r * os;
 #pragma unroll
-            for (int p = 0; p < R0 / 2; ++p) {
+            for (int p = 0; p < NOUT; ++p) {
                 if ((unsigned)(r + p * P::G0) < (unsigned)n) ob[off] = a[p];
                 off += ostep;
             }
@@ -366,18 +368,24 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
 // Resident CTAs per SM that the register allocation must allow (FP32 at the
 // lengths 256 (32 warps), 320, 384 and 512 (24 warps) and the long mixed
 // lengths (2 CTAs); no spills).
-template <typename T, int ML>
+// ZV = 1 (the tuner's alternative, FP32 only) asks for one more resident CTA
+// per SM than the default, i.e. a tighter register cap (3 where the default
+// leaves the choice to the compiler).
+template <typename T, int ML, int ZV = 0>
 struct ConvOcc {
-    static constexpr int value = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 320 || ML == 384 || ML == 512 ? 3 : ML == 640 || ML == 1536 || ML == 2560 || ML == 3072 ? 2 : 1) : 1;
+    static constexpr int base = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 320 || ML == 384 || ML == 512 ? 3 : ML == 640 || ML == 1536 || ML == 2560 || ML == 3072 ? 2 : 1) : 1;
+    static constexpr int value = ZV == 0 ? base : (base == 1 ? 3 : base + 1);
 };
 
-// CPLX: the spectrum of the shifted x window (complex values, complex
-// multiply); otherwise the real spectrum of the even embedding.
-template <typename T, int ML, int W, bool CPLX>
-__global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML>::value) k_col_convolve(Cx<T> *__restrict__ B, const void *__restrict__ specv,
+// SPEC: 0 the real spectrum of the even embedding ([kz][ky <= My/2][kx]);
+// 1 the complex spectrum of the shifted x window (same layout); 2 the complex
+// spectrum of the shifted y window ([kz][ky < My][kx], no mirror in ky).
+template <typename T, int ML, int W, int SPEC, int ZV>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML, ZV>::value) k_col_convolve(Cx<T> *__restrict__ B, const void *__restrict__ specv,
                                                                       int K, int My, int s0, int ns, int t0, int nt,
                                                                       int64_t field, const Cx<T> *__restrict__ twg)
 {
+    constexpr bool CPLX = SPEC > 0;
     using SpecT = typename std::conditional<CPLX, Cx<T>, T>::type;
     const SpecT *__restrict__ spec = reinterpret_cast<const SpecT *>(specv);
     using P = Plan<ML>;
@@ -426,8 +434,8 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML>::value) k_co
     }
     constexpr int RL = P::RL;
     constexpr int S = M / RL;   // frequency step of the last stage's digit
-    const int Khy = My / 2 + 1;
-    const int kyr = ky <= My - ky ? ky : My - ky;
+    const int Khy = SPEC == 2 ? My : My / 2 + 1;
+    const int kyr = SPEC == 2 ? ky : (ky <= My - ky ? ky : My - ky);
     const SpecT *sp = spec + (int64_t)kyr * K + kx;
     const int64_t sp_plane = (int64_t)Khy * K;
 #pragma unroll
@@ -726,7 +734,7 @@ template <typename T>
 lgf_status launch_col_inverse(lgf_ctx *ctx, int M, int K, int nplanes, int nfields, const Cx<T> *in, Cx<T> *out,
                               int lo, int n, int64_t rs, int64_t os, int64_t in_plane, int64_t out_plane,
                               int64_t in_field, int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name);
-template <typename T>
+template <typename T, int SPEC>
 lgf_status launch_col_convolve(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw,
                                int nfields, cudaStream_t s);
 
@@ -822,8 +830,9 @@ lgf_status col_inverse_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx
                          int64_t out_field, const Cx<T> *tw, cudaStream_t s, const char *name)
 {
     using C = ColCfg<T, ML>;
-    auto kern = k_col_inverse<T, ML, C::W>;
-    if (lo < 0 || lo + n > ML / 2) return fail(ctx, LGF_EINVAL, "column inverse: rows beyond half the length");
+    auto kern = k_col_inverse<T, ML, C::W, true>;
+    if (lo < 0 || lo + n > ML) return fail(ctx, LGF_EINVAL, "column inverse: rows beyond the length");
+    if (lo + n > ML / 2) kern = k_col_inverse<T, ML, C::W, false>;
     lgf_status st = set_smem(ctx, kern, C::SMEM);
     if (st != LGF_OK) return st;
     dim3 grid(col_ctas<C::W>(K, nplanes), nfields);
@@ -835,12 +844,14 @@ lgf_status col_inverse_m(lgf_ctx *ctx, int K, int nplanes, int nfields, const Cx
     return LGF_OK;
 }
 
-template <typename T, int ML>
+template <typename T, int ML, int SPEC>
 lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw, int nfields,
                           cudaStream_t s)
 {
     using C = ColCfg<T, ML>;
-    auto kern = g.xasym ? k_col_convolve<T, ML, C::W, true> : k_col_convolve<T, ML, C::W, false>;
+    // the register variant is an FP32 choice (FP64 runs one CTA per SM)
+    auto kern = (sizeof(T) == 4 && g.zvar) ? k_col_convolve<T, ML, C::W, SPEC, sizeof(T) == 4 ? 1 : 0>
+                                           : k_col_convolve<T, ML, C::W, SPEC, 0>;
     if (g.s0[2] < 0 || g.t0[2] < 0 || 2 * (g.s0[2] + g.Ls[2]) > g.M[2] || 2 * (g.t0[2] + g.Lt[2]) > g.M[2])
         return fail(ctx, LGF_EINVAL, "z pass: planes beyond half the transform length");
     lgf_status st = set_smem(ctx, kern, C::SMEM);
@@ -916,11 +927,11 @@ lgf_status launch_col_inverse(lgf_ctx *ctx, int M, int K, int nplanes, int nfiel
                                                                s, name)));
 }
 
-template <typename T>
+template <typename T, int SPEC>
 lgf_status launch_col_convolve(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw,
                                int nfields, cudaStream_t s)
 {
-    LGF_DISPATCH_ML(g.M[2], (pk::col_convolve_m<T, LM>(ctx, g, B, spec, tw, nfields, s)));
+    LGF_DISPATCH_ML(g.M[2], (pk::col_convolve_m<T, LM, SPEC>(ctx, g, B, spec, tw, nfields, s)));
 }
 
 }  // namespace lgf

@@ -219,10 +219,11 @@ __global__ void k_lookup(const double *table, int R, const int32_t *off, int64_t
 
 // Even circular embedding of G_L on an Mx x My x Mz box:
 // box[z][y][x] = G_L(min(x, Mx-x), min(y, My-y), min(z, Mz-z)).
-// Circular embedding of G_L on an Mx x My x Mz box: even along y and z
-// (h[m] = G_L(min(m, M - m))); along x the window h[m] = G_L(m + xc) for
-// m < xP and G_L(m - Mx + xc) above (xc = 0, xP = Mx/2 is the even one).
-__global__ void k_window(const double *table, int R, int Mx, int My, int Mz, int xc, int xP, double *box)
+// Circular embedding of G_L on an Mx x My x Mz box: even along z
+// (h[m] = G_L(min(m, M - m))); along x and y the window h[m] = G_L(m + c) for
+// m < P and G_L(m - M + c) above (c = 0, P = M/2 is the even one).
+__global__ void k_window(const double *table, int R, int Mx, int My, int Mz, int xc, int xP, int yc, int yP,
+                         double *box)
 {
     const int64_t n = (int64_t)Mx * My * Mz;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -230,7 +231,8 @@ __global__ void k_window(const double *table, int R, int Mx, int My, int Mz, int
         const int y = (int)((i / Mx) % My);
         const int z = (int)(i / ((int64_t)Mx * My));
         const int dxo = x < xP ? x + xc : x - Mx + xc;
-        box[i] = lgf_value(table, R, abs(dxo), min(y, My - y), min(z, Mz - z));
+        const int dyo = y < yP ? y + yc : y - My + yc;
+        box[i] = lgf_value(table, R, abs(dxo), abs(dyo), min(z, Mz - z));
     }
 }
 
@@ -398,10 +400,10 @@ lgf_status table_lookup(lgf_ctx *ctx, const double *table, const int32_t *off, i
     return LGF_OK;
 }
 
-lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], int xc, int xP, double *box,
-                         cudaStream_t s)
+lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], int xc, int xP, int yc, int yP,
+                         double *box, cudaStream_t s)
 {
-    k_window<<<152 * 8, 256, 0, s>>>(table, ctx->table_radius, M[0], M[1], M[2], xc, xP, box);
+    k_window<<<152 * 8, 256, 0, s>>>(table, ctx->table_radius, M[0], M[1], M[2], xc, xP, yc, yP, box);
     LGF_CHECK_LAUNCH(ctx, "window kernel");
     return LGF_OK;
 }

@@ -221,19 +221,40 @@ def _line_problem(seed, b, src_x, tgt_x, yz=((0, 0), (0, 1)), ncomp=1, nrhs=1):
     return li.Problem("line", b, src, tgt, f)
 
 
+def _transposed(p):
+    """The same problem with x and y exchanged (a wake along y)."""
+    sw = lambda c: np.ascontiguousarray(c[:, [1, 0, 2]])
+    b = p.b
+    f = p.f.reshape(p.nrhs, p.ncomp, -1, b, b, b).transpose(0, 1, 2, 3, 5, 4).reshape(p.f.shape)
+    return li.Problem(p.name + "_yx", b, sw(p.src), sw(p.tgt), np.ascontiguousarray(f))
+
+
+def _blob_problem(seed, b, src, tgt):
+    rng = np.random.default_rng(seed)
+    src = np.array(src, dtype=np.int32)
+    tgt = np.array(tgt, dtype=np.int32)
+    return li.Problem("blob", b, src, tgt, rng.uniform(-1, 1, size=(1, 1, src.shape[0], b ** 3)))
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("case", ["body_and_wake", "source_after_target", "far_apart", "long_source"])
-def test_shifted_x_window_every_point(prec, case, ctx64, ctx32, oracle):
-    """Source and target extents along x that differ: the plan embeds x with
-    the shifted window (M >= Ls + Lt - 1, complex spectrum) where that is
-    shorter than the even one, with targets past M/2 (every output of the
-    inverse x stage formed); a long source keeps the even embedding."""
+@pytest.mark.parametrize("case", ["body_and_wake", "source_after_target", "far_apart", "long_source",
+                                  "wake_along_y", "wake_along_x_and_y"])
+def test_shifted_window_every_point(prec, case, ctx64, ctx32, oracle):
+    """Source and target extents that differ along x or y: the plan embeds
+    that axis with the shifted window (M >= Ls + Lt - 1, complex spectrum;
+    no symmetry in ky for y) where that is shorter than the even one, with
+    targets past M/2 (every output of that axis's inverse stage formed); a
+    long source keeps the even embedding."""
     ctx = ctx64 if prec == "f64" else ctx32
     b = 8
-    p = {"body_and_wake": _line_problem(21, b, [0, 1], range(-1, 11), ncomp=2),
-         "source_after_target": _line_problem(22, b, [10, 11], range(0, 10), yz=((1, 0), (0, 0))),
-         "far_apart": _line_problem(23, b, [0], range(6, 10), nrhs=2),
-         "long_source": _line_problem(24, b, range(0, 6), [3], yz=((0, 0), (0, 0)))}[case]
+    cases = {"body_and_wake": lambda: _line_problem(21, b, [0, 1], range(-1, 11), ncomp=2),
+             "source_after_target": lambda: _line_problem(22, b, [10, 11], range(0, 10), yz=((1, 0), (0, 0))),
+             "far_apart": lambda: _line_problem(23, b, [0], range(6, 10), nrhs=2),
+             "long_source": lambda: _line_problem(24, b, range(0, 6), [3], yz=((0, 0), (0, 0))),
+             "wake_along_y": lambda: _transposed(_line_problem(25, b, [0, 1], range(-1, 11), ncomp=2)),
+             "wake_along_x_and_y": lambda: _blob_problem(26, b, [[0, 0, 0], [1, 0, 0]],
+                                                         [[x, y, 0] for x in range(-1, 9) for y in range(-1, 7)])}
+    p = cases[case]()
     got = run_poisson(ctx, p)
     ref = oracle_fields(oracle, p)
     assert rel_linf(got, ref) < TOL[prec]
