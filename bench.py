@@ -426,6 +426,10 @@ def run_ours(args, rank, world, dist):
         w = Workload(w.name, [w.entries[i] for i in mine], w.desc)
     ctx = lgf.Context("f32", device=dev.index)
     ctx.table_build(48)
+    # the autotuner picks each plan's geometry and the batch's branch count in
+    # the first warm-up step (persisted to $LGF_TUNE_CACHE when set)
+    if not args.no_tune:
+        ctx.autotune(lgf.LGF_TUNE_ON)
     fs, batch, outs = build_batch(lgf, w, dev, torch.float32)
     s = torch.cuda.Stream(device=dev)
     l2_note = ("flushed between timed steps (512 MiB write)" if w.name == "dense128" else
@@ -435,10 +439,16 @@ def run_ours(args, rank, world, dist):
     def step():
         ctx.batch_apply(batch, stream=s)
 
+    t_tune = time.perf_counter()
     with torch.cuda.stream(s):
-        for _ in range(max(3, args.warmup)):
+        step()
+    s.synchronize()
+    t_tune = time.perf_counter() - t_tune
+    with torch.cuda.stream(s):
+        for _ in range(max(3, args.warmup) - 1):
             step()
     s.synchronize()
+    tuning = dict(ctx.tune_report(), first_step_s=t_tune, mode="off" if args.no_tune else "on")
 
     # ---- soak: >= 1 s of steps with the clock sampler running, untimed ----
     clk = ClockSampler(dev.index)
@@ -649,7 +659,7 @@ def run_ours(args, rank, world, dist):
             "config": dict(w.desc, l2=l2_note,
                            parallelism=("problems sharded across ranks, longest first" if sharded else
                                         "replicas" if world > 1 else "single GPU"),
-                           points_per_step=points_all, kernels=kernels),
+                           points_per_step=points_all, kernels=kernels, tuning=tuning),
             "roofline": roofline, "roofline_step": roofline_step, "roofline_dominant_kernel": roofline_dom,
             "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
             "launches_per_step": launches_per_step, "clocks": clocks,
@@ -811,6 +821,7 @@ def main(argv=None):
     ap.add_argument("--ref-points", type=int, default=0, help="reference arm sample per problem (0: default)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-tune", action="store_true", help="library defaults instead of the autotuner's choices")
     ap.add_argument("--ncu-case", action="store_true", help="run the step --steps times untimed (for ncu)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -379,6 +379,43 @@ LGF_API lgf_status lgf_ctx_stats(lgf_ctx *ctx, lgf_stats *out);
    Errors: LGF_EINVAL. */
 LGF_API lgf_status lgf_cache_limits(lgf_ctx *ctx, int32_t max_plans, int32_t max_spectra, int32_t max_graphs);
 
+/* Autotuner.  A Poisson plan's geometry has free choices that the method
+   leaves open (Sec. 2.2 fixes only the convolution): the embedding of x and
+   of y (the even circular embedding of G_L, M >= 2L - 1 on the union extent
+   L, or the shifted window, M >= Ls + Lt - 1), the transform length along
+   each axis (the smallest supported length, or the next one, whose radix
+   plan may run faster), and the register cap of the z pass (FP32); a batch
+   also has its branch count (1, 2 or 4 concurrent streams).  With tuning on,
+   each new plan's first apply times candidates on the caller's stream
+   (coordinate descent from the default: one knob changed at a time, a change
+   kept when it cuts the median time of the passes by at least 3 %), and each
+   new batch shape times its branch counts; the choices are kept in the
+   context and, when `cache_path` names a file (NULL: the LGF_TUNE_CACHE
+   environment variable, if set), appended to it as "key -> value" lines and
+   read back by later contexts.  LGF_TUNE_CACHED uses the file's choices and
+   the defaults elsewhere, timing nothing.  Results do not depend on the
+   choices beyond floating-point rounding.  Tuning runs synchronously in the
+   call that first meets a plan, so tune before capturing a stream into a
+   CUDA graph.  Errors: LGF_EINVAL (mode), LGF_ECUDA. */
+enum { LGF_TUNE_OFF = 0, LGF_TUNE_ON = 1, LGF_TUNE_CACHED = 2 };
+
+LGF_API lgf_status lgf_autotune(lgf_ctx *ctx, int32_t mode, const char *cache_path);
+
+typedef struct {
+    int64_t plans_tuned;        /* plans whose choice was timed in this context */
+    int64_t plans_from_cache;   /* plans whose choice came from the file */
+    int64_t candidates_timed;   /* candidate geometries timed */
+    int64_t batches_tuned;      /* batch shapes whose branch count was chosen */
+    int64_t last_branches;      /* branch count of the last batch */
+    int64_t shifted_x, shifted_y, longer_x, longer_y, longer_z, z_variant;   /* counts over the context's plans */
+    double tune_ms;             /* GPU time spent timing candidates */
+    int64_t reserved[4];
+} lgf_tune_info;
+
+/* The tuner's counters and a summary of the choices of the context's plans.
+   Errors: LGF_EINVAL. */
+LGF_API lgf_status lgf_tune_report(lgf_ctx *ctx, lgf_tune_info *out);
+
 /* Allocation-free integrating-factor apply.  The paper has no counterpart:
    this entry point exists for callers that must not allocate device memory
    while they run -- for example a time-stepping loop whose device memory is

@@ -7,7 +7,8 @@ hand-written CUDA kernels for sm_103a behind the C ABI of include/lgf.h.  This
 package is the thin Python binding of that ABI (see _binding.py); importing it
 loads liblgf.so and raises if the library has not been built.
 """
-from ._binding import (EXPORTS, LGF_F32, LGF_F64, LGF_OP_INTFACTOR, LGF_OP_KINV, LGF_OP_POISSON,  # noqa: F401
+from ._binding import (EXPORTS, LGF_F32, LGF_F64, LGF_TUNE_CACHED, LGF_TUNE_OFF, LGF_TUNE_ON, lgf_autotune,
+                       lgf_tune_report, LGF_OP_INTFACTOR, LGF_OP_KINV, LGF_OP_POISSON,  # noqa: F401
                        LGF_OP_POISSON_THEN_INTFACTOR, LIB_PATH, Context, LgfError, lgf_batch_apply,
                        lgf_cache_limits, lgf_ctx_create, lgf_ctx_destroy, lgf_ctx_stats, lgf_curl, lgf_curl_adjoint, lgf_intfactor_apply,
                        lgf_intfactor_apply_noalloc, lgf_velocity_refresh, lgf_ib_spread, lgf_ib_interp,

@@ -19,13 +19,14 @@ LIB_PATH = os.path.join(_PKG, "liblgf.so")
 LGF_OK, LGF_EINVAL, LGF_ENOMEM, LGF_ECUDA, LGF_ETIMEOUT, LGF_EUNSUPPORTED, LGF_ENOTABLE = range(7)
 LGF_F32, LGF_F64 = 0, 1
 LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR, LGF_OP_KINV = 0, 1, 2, 3
+LGF_TUNE_OFF, LGF_TUNE_ON, LGF_TUNE_CACHED = 0, 1, 2
 
 # Every symbol include/lgf.h declares (checked by the symbol test).
 EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
            "lgf_kinv_lookup", "lgf_poisson_apply", "lgf_kinv_apply", "lgf_curl", "lgf_curl_adjoint",
            "lgf_velocity_refresh", "lgf_ib_spread", "lgf_ib_interp", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
            "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_ctx_stats", "lgf_cache_limits",
-           "lgf_nested_projection_stage",
+           "lgf_nested_projection_stage", "lgf_autotune", "lgf_tune_report",
            "lgf_intfactor_apply_noalloc",
            "lgf_status_string", "lgf_last_error", "lgf_version")
 
@@ -63,6 +64,14 @@ class lgf_stage(ctypes.Structure):
                 ("W2_dev", ctypes.c_void_p), ("r_dev", ctypes.c_void_p), ("u_dev", ctypes.c_void_p),
                 ("d_dev", ctypes.c_void_p), ("f_dev", ctypes.c_void_p), ("alpha", ctypes.c_double),
                 ("dx", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+
+
+class lgf_tune_info(ctypes.Structure):
+    _fields_ = [("plans_tuned", ctypes.c_int64), ("plans_from_cache", ctypes.c_int64),
+                ("candidates_timed", ctypes.c_int64), ("batches_tuned", ctypes.c_int64),
+                ("last_branches", ctypes.c_int64), ("shifted_x", ctypes.c_int64), ("shifted_y", ctypes.c_int64),
+                ("longer_x", ctypes.c_int64), ("longer_y", ctypes.c_int64), ("longer_z", ctypes.c_int64),
+                ("z_variant", ctypes.c_int64), ("tune_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
 
 
 class LgfError(RuntimeError):
@@ -108,6 +117,8 @@ def load(path: str = LIB_PATH):
         "lgf_ctx_stats": [vp, ctypes.POINTER(lgf_stats)],
         "lgf_cache_limits": [vp, i32, i32, i32],
         "lgf_nested_projection_stage": [vp, ctypes.POINTER(lgf_stage), vp],
+        "lgf_autotune": [vp, i32, ctypes.c_char_p],
+        "lgf_tune_report": [vp, ctypes.POINTER(lgf_tune_info)],
         "lgf_intfactor_apply_noalloc": [i32, dbl, dbl, bsp, bsp, vp, vp, i32, i32, vp, ctypes.c_char_p, i32],
         "lgf_status_string": [i32],
         "lgf_last_error": [vp],
@@ -383,6 +394,18 @@ class Context:
                     "lgf_nested_projection_stage")
         return u
 
+    def autotune(self, mode: int = LGF_TUNE_ON, cache_path: Optional[str] = None):
+        """Tuning mode (LGF_TUNE_OFF / ON / CACHED) and the file of persisted
+        choices (None: $LGF_TUNE_CACHE, if set)."""
+        self._check(self._L.lgf_autotune(self._h, int(mode), None if cache_path is None else cache_path.encode()),
+                    "lgf_autotune")
+
+    def tune_report(self) -> dict:
+        t = lgf_tune_info()
+        self._check(self._L.lgf_tune_report(self._h, ctypes.byref(t)), "lgf_tune_report")
+        return {name: (float(getattr(t, name)) if name == "tune_ms" else int(getattr(t, name)))
+                for name, _ in lgf_tune_info._fields_ if name != "reserved"}
+
     def stats(self) -> dict:
         """Cache state (lgf_ctx_stats): graphs, plans, spectra, invalidations, scratch."""
         st = lgf_stats()
@@ -487,6 +510,14 @@ def lgf_ctx_stats(ctx: Context) -> dict:
 
 def lgf_cache_limits(ctx: Context, max_plans: int = -1, max_spectra: int = -1, max_graphs: int = -1):
     return ctx.cache_limits(max_plans, max_spectra, max_graphs)
+
+
+def lgf_autotune(ctx: Context, mode: int = LGF_TUNE_ON, cache_path: Optional[str] = None):
+    return ctx.autotune(mode, cache_path)
+
+
+def lgf_tune_report(ctx: Context) -> dict:
+    return ctx.tune_report()
 
 
 def lgf_nested_projection_stage(ctx: Context, *a, **kw):

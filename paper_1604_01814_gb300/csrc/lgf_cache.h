@@ -91,6 +91,20 @@ public:
         return items_.back().get();
     }
 
+    // Destroy every entry matching `pred` (the caller has made sure nothing
+    // in flight or captured still uses them).
+    template <class Pred>
+    size_t erase_if(Pred pred)
+    {
+        size_t n = 0;
+        for (size_t i = items_.size(); i-- > 0;)
+            if (pred(*items_[i])) {
+                items_.erase(items_.begin() + (std::ptrdiff_t)i);
+                ++n;
+            }
+        return n;
+    }
+
     std::vector<std::unique_ptr<T>> &items() { return items_; }
 
 private:

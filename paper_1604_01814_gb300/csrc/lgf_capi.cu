@@ -5,12 +5,14 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <set>
 #include <string>
 #include <vector>
 
 #include "lgf_internal.cuh"
+#include "lgf_tune.h"
 
 namespace lgf {
 
@@ -150,6 +152,7 @@ lgf_status prepare_poisson(lgf_ctx *ctx, const lgf_blockset *src, const lgf_bloc
     if (ctx->table_dev == nullptr) return fail(ctx, LGF_ENOTABLE, "lgf_table_build has not been called");
     lgf_status st = poisson_plan(ctx, src, tgt, &pp->plan);
     if (st != LGF_OK) return st;
+    if ((st = tune_poisson(ctx, pp->plan, nfields, kalpha, s)) != LGF_OK) return st;
     st = poisson_spectrum(ctx, pp->plan->g, kalpha, &pp->spec, s);
     if (st != LGF_OK) return st;
     st = poisson_prepare_scratch(ctx, pp->plan, nfields);
@@ -685,10 +688,14 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     if (nprob < 0 || (nprob > 0 && !probs)) return fail(ctx, LGF_EINVAL, "batch: bad problem list");
     cudaStream_t s = (cudaStream_t)stream;
     // 1. validate and build a key of everything that shapes the work
-    std::vector<unsigned char> key;
+    std::vector<unsigned char> key, shape;   // shape: the key without buffers and stream
     auto put = [&](const void *p, size_t n) {
         const unsigned char *c = (const unsigned char *)p;
         key.insert(key.end(), c, c + n);
+    };
+    auto put_shape = [&](const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        shape.insert(shape.end(), c, c + n);
     };
     for (int i = 0; i < nprob; ++i) {
         const lgf_problem &p = probs[i];
@@ -712,6 +719,13 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         put(&p.u_dev, sizeof(void *));
         put(&p.ncomp, 4 * sizeof(int32_t));
         put(&p.alpha, 2 * sizeof(double));
+        put_shape(&p.src.b, sizeof(int32_t));
+        put_shape(&p.src.nblocks, sizeof(int32_t));
+        put_shape(p.src.coords, 3 * sizeof(int32_t) * (size_t)p.src.nblocks);
+        put_shape(&p.tgt.nblocks, sizeof(int32_t));
+        put_shape(p.tgt.coords, 3 * sizeof(int32_t) * (size_t)p.tgt.nblocks);
+        put_shape(&p.ncomp, 4 * sizeof(int32_t));
+        put_shape(&p.alpha, 2 * sizeof(double));
     }
     put(&s, sizeof(s));
     // 2. prepare every plan, spectrum, weight set and the largest scratch;
@@ -790,42 +804,51 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
             post.push_back((int)k);
         }
     }
-    const int nb = ctx->prof ? 1 : std::min<int>(kBranches, std::max<int>(1, (int)units.size()));
-    {
+    const int nb_max = std::min<int>(kBranches, std::max<int>(1, (int)units.size()));
+    int nb = ctx->prof ? 1 : nb_max;
+    // units onto nbv branches (longest first onto the least loaded), each
+    // branch's scratch grown for its units, its stream and events made
+    auto setup = [&](int nbv) -> lgf_status {
         std::vector<int> order(units.size());
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
         std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return units[a].cost > units[c].cost; });
         double load[kBranches] = {0, 0, 0, 0};
         for (int i : order) {
             int best = 0;
-            for (int b = 1; b < nb; ++b)
+            for (int b = 1; b < nbv; ++b)
                 if (load[b] < load[best]) best = b;
             units[i].branch = best;
             load[best] += units[i].cost;
         }
-    }
-    for (auto &u : units) {
-        ctx->cur = &ctx->scr[u.branch];
-        const int i = u.prob;
-        if (i >= 0 && (st = poisson_prepare_scratch(ctx, pois[i].plan, probs[i].ncomp * probs[i].nrhs)) != LGF_OK)
-            return st;
-        for (int k : {u.grp, u.dep}) {
-            if (k < 0) continue;
-            const Group &g = groups[k];
-            if ((st = intf_prepare_scratch(ctx, g.plan, g.nf, (int)g.jobs.size())) != LGF_OK) return st;
+        lgf_status e2 = LGF_OK;
+        for (auto &u : units) {
+            ctx->cur = &ctx->scr[u.branch];
+            const int i = u.prob;
+            if (i >= 0 && (e2 = poisson_prepare_scratch(ctx, pois[i].plan, probs[i].ncomp * probs[i].nrhs)) != LGF_OK)
+                break;
+            for (int k : {u.grp, u.dep}) {
+                if (k < 0 || e2 != LGF_OK) continue;
+                const Group &g = groups[k];
+                e2 = intf_prepare_scratch(ctx, g.plan, g.nf, (int)g.jobs.size());
+            }
+            if (e2 != LGF_OK) break;
         }
-    }
-    ctx->cur = &ctx->scr[0];
-    for (int k : post)
-        if ((st = intf_prepare_scratch(ctx, groups[k].plan, groups[k].nf, (int)groups[k].jobs.size())) != LGF_OK)
-            return st;
-    if (nb > 1) {
-        if (!ctx->ev_fork) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-        for (int b = 0; b < nb; ++b) {
-            if (!ctx->br[b]) LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->br[b], cudaStreamNonBlocking));
-            if (!ctx->ev_join[b]) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming));
+        ctx->cur = &ctx->scr[0];
+        if (e2 != LGF_OK) return e2;
+        for (int k : post)
+            if ((e2 = intf_prepare_scratch(ctx, groups[k].plan, groups[k].nf, (int)groups[k].jobs.size())) != LGF_OK)
+                return e2;
+        if (nbv > 1) {
+            if (!ctx->ev_fork) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+            for (int b = 0; b < nbv; ++b) {
+                if (!ctx->br[b]) LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->br[b], cudaStreamNonBlocking));
+                if (!ctx->ev_join[b])
+                    LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming));
+            }
         }
-    }
+        return LGF_OK;
+    };
+    if ((st = setup(nb)) != LGF_OK) return st;
     auto enqueue = [&]() -> lgf_status {
         // problems with no source blocks: zero output
         for (int i = 0; i < nprob; ++i) {
@@ -871,7 +894,55 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         }
         return LGF_OK;
     };
-    // 3. the legacy default stream cannot be captured, and per-kernel timing
+    // 4. the branch count of this batch shape: the persisted choice, or (tuning
+    //    on, a new shape) the fastest of 1, 2 and 4 branches timed with direct
+    //    launches on the caller's stream
+    if (ctx->tune_mode != LGF_TUNE_OFF && !ctx->prof && s != nullptr && nb_max > 1) {
+        const std::string tk = tune_batch_key(ctx->prec == LGF_F64, tune_hash(shape.data(), shape.size()));
+        auto it = ctx->tune_db.find(tk);
+        int pick = 0;
+        if (it != ctx->tune_db.end() && std::sscanf(it->second.c_str(), "nb%d", &pick) == 1 && pick >= 1 &&
+            pick <= nb_max) {
+            nb = pick;
+        } else if (ctx->tune_mode == LGF_TUNE_ON) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            LGF_CUDA(ctx, cudaEventCreate(&e0));
+            LGF_CUDA(ctx, cudaEventCreate(&e1));
+            float tbest = 0.f;
+            int best = nb;
+            for (int cand : {4, 2, 1}) {
+                if (cand > nb_max) continue;
+                if ((st = setup(cand)) != LGF_OK) break;
+                nb = cand;
+                std::vector<float> t;
+                for (int r = 0; r < 3 && st == LGF_OK; ++r) {
+                    cudaEventRecord(e0, s);
+                    st = enqueue();
+                    cudaEventRecord(e1, s);
+                    float v = 0.f;
+                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&v, e0, e1) != cudaSuccess)
+                        st = fail(ctx, LGF_ECUDA, "batch: branch timing");
+                    if (r > 0) t.push_back(v);
+                }
+                if (st != LGF_OK) break;
+                const float tm = std::min(t[0], t[1]);
+                ctx->tune_candidates++;
+                if (tbest == 0.f || tm < 0.97f * tbest) {   // fewer branches must win by 3 %
+                    tbest = tm;
+                    best = cand;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (st != LGF_OK) return st;
+            nb = best;
+            ++ctx->tune_batches;
+            tune_record(ctx, tk, "nb" + std::to_string(nb));
+        }
+        if ((st = setup(nb)) != LGF_OK) return st;
+    }
+    ctx->tune_last_branches = nb;
+    // 5. the legacy default stream cannot be captured, and per-kernel timing
     //    needs direct launches: run without a graph
     //    (and so does a context whose graph cache is switched off)
     if (s == nullptr || ctx->prof || ctx->graphs.cap() == 0) return enqueue();
@@ -898,6 +969,49 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch: graph instantiation");
     ctx->graphs.add(std::move(key), exec, ++ctx->graph_clock);
     LGF_CUDA(ctx, cudaGraphLaunch(exec, s));
+    return LGF_OK;
+}
+
+lgf_status lgf_autotune(lgf_ctx *ctx, int32_t mode, const char *cache_path)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (mode != LGF_TUNE_OFF && mode != LGF_TUNE_ON && mode != LGF_TUNE_CACHED)
+        return fail(ctx, LGF_EINVAL, "autotune: mode must be LGF_TUNE_OFF, LGF_TUNE_ON or LGF_TUNE_CACHED");
+    ctx->tune_mode = mode;
+    const char *path = cache_path ? cache_path : std::getenv("LGF_TUNE_CACHE");
+    ctx->tune_path = path ? path : "";
+    if (!ctx->tune_path.empty()) {
+        if (FILE *f = std::fopen(ctx->tune_path.c_str(), "r")) {
+            std::string text;
+            char buf[4096];
+            size_t n;
+            while ((n = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, n);
+            std::fclose(f);
+            tune_parse(text, &ctx->tune_db);
+        }
+    }
+    return LGF_OK;
+}
+
+lgf_status lgf_tune_report(lgf_ctx *ctx, lgf_tune_info *out)
+{
+    if (!ctx || !out) return LGF_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->plans_tuned = ctx->tune_plans;
+    out->plans_from_cache = ctx->tune_plans_cached;
+    out->candidates_timed = ctx->tune_candidates;
+    out->batches_tuned = ctx->tune_batches;
+    out->last_branches = ctx->tune_last_branches;
+    out->tune_ms = ctx->tune_ms;
+    for (auto &p : ctx->pplans.items()) {
+        out->shifted_x += p->choice.shift[0];
+        out->shifted_y += p->choice.shift[1];
+        out->longer_x += p->choice.bump[0] > 0;
+        out->longer_y += p->choice.bump[1] > 0;
+        out->longer_z += p->choice.bump[2] > 0;
+        out->z_variant += p->choice.zvar;
+    }
     return LGF_OK;
 }
 

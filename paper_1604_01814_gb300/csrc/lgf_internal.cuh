@@ -181,7 +181,7 @@ struct lgf_ctx {
     // kernel spectra per transform-box shape and kernel (alpha = 0: G_L,
     // alpha > 0: G_K(alpha)) and the plans, each cache bounded (least
     // recently used evicted; entries of the current call are kept)
-    lgf::LruCache<lgf::Spectrum> spectra{32};
+    lgf::LruCache<lgf::Spectrum> spectra{128};
     lgf::LruCache<lgf::PoissonPlan> pplans{256};
     lgf::LruCache<lgf::IntfPlan> iplans{256};
     std::vector<std::unique_ptr<lgf::IntfWeights>> weights;
@@ -207,6 +207,19 @@ struct lgf_ctx {
     uint64_t graph_clock = 0;
 
     double *red_dev = nullptr;   // small reduction buffer (residual, table mismatch)
+
+    // autotuner: mode (LGF_TUNE_*), persisted choices (key -> value lines of
+    // lgf_tune.h, loaded from and appended to tune_path), counters, the
+    // branch count per batch shape, and the timing runs' input/output buffers
+    int tune_mode = 0;
+    int tune_reps = 5;
+    std::string tune_path;
+    std::map<std::string, std::string> tune_db;
+    int64_t tune_plans = 0, tune_plans_cached = 0, tune_candidates = 0, tune_batches = 0;
+    double tune_ms = 0.0;
+    int tune_last_branches = 0;
+    void *tune_f = nullptr, *tune_u = nullptr;
+    size_t tune_fb = 0, tune_ub = 0;
 
     // optional per-kernel timing with CUDA events on the launch stream
     bool prof = false;
@@ -309,6 +322,17 @@ lgf_status ib_run(lgf_ctx *ctx, const IBPlan *pl, bool spread, int64_t nm, const
 // Residual (lgf_residual.cu)
 lgf_status residual_run(lgf_ctx *ctx, const lgf_blockset *set, const void *u, const void *f, double dx,
                         double *r, double *max_abs, double *max_f, cudaStream_t s);
+
+// Autotuner (lgf_tune.cu): choose the plan's geometry for nf fields (timed
+// candidates, or the persisted choice); no-op when tuning is off or the plan
+// is tuned.
+lgf_status tune_poisson(lgf_ctx *ctx, PoissonPlan *pl, int nf, double kalpha, cudaStream_t s);
+// Time the five passes of `pl` under choice `ch` (median of the context's
+// repetitions, ms); builds the spectrum the choice needs.
+lgf_status poisson_time_choice(lgf_ctx *ctx, PoissonPlan *pl, const PoissonChoice &ch, int nf, double kalpha,
+                               cudaStream_t s, float *ms);
+// Record a tuned item (in memory and appended to the persisted file).
+void tune_record(lgf_ctx *ctx, const std::string &key, const std::string &value);
 
 // Block-set validation shared by the entry points.
 lgf_status check_blockset(lgf_ctx *ctx, const lgf_blockset *bs, const char *name);

@@ -462,4 +462,64 @@ lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const 
                              (const float *)sp->dev, nfields, 0, false, s);
 }
 
+lgf_status poisson_time_choice(lgf_ctx *ctx, PoissonPlan *pl, const PoissonChoice &ch, int nf, double kalpha,
+                               cudaStream_t s, float *ms)
+{
+    PoissonGeom g = pl->g;
+    int64_t A = 0, B = 0;
+    if (!poisson_geometry(*pl, ch, &g, &A, &B)) return LGF_EUNSUPPORTED;
+    Spectrum *sp = nullptr;
+    lgf_status st = poisson_spectrum(ctx, g, kalpha, &sp, s);
+    if (st != LGF_OK) return st;
+    const bool dbl = ctx->prec == LGF_F64;
+    const size_t csz = dbl ? 16 : 8, esz = dbl ? 8 : 4;
+    if ((st = ensure_scratch(ctx, &ctx->cur->A, &ctx->cur->a, (size_t)A * nf * csz)) != LGF_OK) return st;
+    if ((st = ensure_scratch(ctx, &ctx->cur->B, &ctx->cur->b, (size_t)B * nf * csz)) != LGF_OK) return st;
+    // timing inputs and outputs (zeros: the passes' work does not depend on
+    // the values); not captured by any graph, so growth drops none
+    const size_t fb = (size_t)g.fstride * nf * esz, ub = (size_t)g.ustride * nf * esz;
+    const bool fresh = fb > ctx->tune_fb;
+    if ((st = ensure_scratch(nullptr, &ctx->tune_f, &ctx->tune_fb, fb)) != LGF_OK) return st;
+    if ((st = ensure_scratch(nullptr, &ctx->tune_u, &ctx->tune_ub, ub)) != LGF_OK) return st;
+    if (fresh) LGF_CUDA(ctx, cudaMemsetAsync(ctx->tune_f, 0, ctx->tune_fb, s));
+    for (int d = 0; d < 3; ++d) {
+        twiddles(ctx, g.M[d], dbl, &st);
+        if (st != LGF_OK) return st;
+    }
+    g.Astride = A;
+    g.Bstride = B;
+    g.scale = 1.0;
+    auto run = [&]() -> lgf_status {
+        if (dbl)
+            return run_passes<double>(ctx, g, (const double *)ctx->tune_f, (double *)ctx->tune_u,
+                                      (Cx<double> *)ctx->cur->A, (Cx<double> *)ctx->cur->B, (const double *)sp->dev,
+                                      nf, 0, false, s);
+        return run_passes<float>(ctx, g, (const float *)ctx->tune_f, (float *)ctx->tune_u, (Cx<float> *)ctx->cur->A,
+                                 (Cx<float> *)ctx->cur->B, (const float *)sp->dev, nf, 0, false, s);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LGF_CUDA(ctx, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, LGF_ECUDA, "tune: event creation failed");
+    }
+    std::vector<float> t;
+    for (int r = 0; r < 2 + ctx->tune_reps && st == LGF_OK; ++r) {
+        cudaEventRecord(e0, s);
+        st = run();
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float v = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&v, e0, e1);
+        if (e != cudaSuccess && st == LGF_OK) st = cuda_fail(ctx, e, "tune: timing");
+        if (r >= 2) t.push_back(v);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LGF_OK) return st;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return LGF_OK;
+}
+
 }  // namespace lgf

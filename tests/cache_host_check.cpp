@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "lgf_cache.h"
+#include "lgf_tune.h"
 
 using namespace lgf;
 
@@ -112,11 +113,40 @@ static void graph_bound_evicts_least_recent()
     std::printf("ok graph_bound_evicts_least_recent\n");
 }
 
+static void tune_file_round_trip()
+{
+    const int nbs[3] = {4, 2, 4}, nbt[3] = {67, 4, 4}, off[3] = {-1, -1, 0};
+    const std::string k = tune_plan_key(false, 16, nbs, nbt, off, 3);
+    CHECK(k == "P f32 b16 s4,2,4 t67,4,4 o-1,-1,0 nf3");
+    TuneChoiceText c;
+    c.shift[0] = 1;
+    c.shift[1] = 1;
+    c.bump[2] = 1;
+    c.zvar = 1;
+    const std::string v = tune_plan_value(c);
+    CHECK(v == "x1 y1 bx0 by0 bz1 z1");
+    std::map<std::string, std::string> m;
+    std::string text = "# comment\n" + tune_line(k, "x0 y0 bx0 by0 bz0 z0") + "garbage line\n" + tune_line(k, v) +
+                       tune_line(tune_batch_key(true, 0x9f3aull), "nb2") + " -> lonely\n";
+    CHECK(tune_parse(text, &m) == 3);
+    CHECK(m.size() == 2 && m[k] == v);                      // the later line wins
+    CHECK(m[tune_batch_key(true, 0x9f3aull)] == "nb2");
+    TuneChoiceText r;
+    CHECK(tune_parse_plan_value(m[k], &r));
+    CHECK(r.shift[0] == 1 && r.shift[1] == 1 && r.bump[0] == 0 && r.bump[2] == 1 && r.zvar == 1);
+    CHECK(!tune_parse_plan_value("x2 y0 bx0 by0 bz0 z0", &r));   // out of range
+    CHECK(!tune_parse_plan_value("x1 y0", &r));                  // truncated
+    const unsigned char a[3] = {1, 2, 3}, b[3] = {1, 2, 4};
+    CHECK(tune_hash(a, 3) != tune_hash(b, 3) && tune_hash(a, 3) == tune_hash(a, 3));
+    std::printf("ok tune_file_round_trip\n");
+}
+
 int main()
 {
     lru_evicts_least_recent();
     if (!g_failed) running_call_entries_are_pinned();
     if (!g_failed) invalidation_drops_every_graph();
     if (!g_failed) graph_bound_evicts_least_recent();
+    if (!g_failed) tune_file_round_trip();
     return g_failed;
 }

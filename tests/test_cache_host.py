@@ -1,6 +1,7 @@
 """Host logic of the context caches (no GPU): LRU bounds of the plan and
-spectrum caches, pinning of the entries a running call uses, and the rule that
-any scratch growth or eviction drops every captured batch graph.
+spectrum caches, pinning of the entries a running call uses, the rule that
+any scratch growth or eviction drops every captured batch graph, and the text
+format of the autotuner's persisted choices (csrc/lgf_tune.h).
 
 The library's contexts use exactly this header (csrc/lgf_cache.h); the GPU
 test tests/test_gpu_cache.py checks the same behaviour end to end through
@@ -24,4 +25,4 @@ def test_cache_bookkeeping(tmp_path):
                            os.path.join(ROOT, "tests", "cache_host_check.cpp"), "-o", exe])
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.count("ok ") == 4, r.stdout
+    assert r.stdout.count("ok ") == 5, r.stdout

@@ -51,6 +51,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(b.lgf_problem) == 2 * 16 + 2 * 8 + 4 * 4 + 2 * 8
     assert ctypes.sizeof(b.lgf_kernel_stat) == 48 + 8 + 8
     assert ctypes.sizeof(b.lgf_stats) == 16 * 8
+    assert ctypes.sizeof(b.lgf_tune_info) == 11 * 8 + 8 + 4 * 8
     assert ctypes.sizeof(b.lgf_stage) == 16 + 8 + 9 * 8 + 2 * 8 + 4 * 4
 
 
