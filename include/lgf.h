@@ -195,6 +195,7 @@ typedef struct {
    allowed).  The Poisson parts (each with its own integrating factor when no
    other problem shares its group) and the groups that read only batch inputs
    are independent units: they are spread over up to 4 concurrent branches
+   (8 when the autotuner finds that faster)
    (context streams forked from and joined back to the caller's stream, each
    with its own scratch), longest first onto the least loaded branch.
    Groups of several
@@ -385,7 +386,7 @@ LGF_API lgf_status lgf_cache_limits(lgf_ctx *ctx, int32_t max_plans, int32_t max
    L, or the shifted window, M >= Ls + Lt - 1), the transform length along
    each axis (the smallest supported length, or the next one, whose radix
    plan may run faster), and the register cap of the z pass (FP32); a batch
-   also has its branch count (1, 2 or 4 concurrent streams).  With tuning on,
+   also has its branch count (1, 2, 4 or 8 concurrent streams).  With tuning on,
    each new plan's first apply times candidates on the caller's stream
    (coordinate descent from the default: one knob changed at a time, a change
    kept when it cuts the median time of the passes by at least 3 %), and each

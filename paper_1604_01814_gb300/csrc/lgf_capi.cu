@@ -805,14 +805,14 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         }
     }
     const int nb_max = std::min<int>(kBranches, std::max<int>(1, (int)units.size()));
-    int nb = ctx->prof ? 1 : nb_max;
+    int nb = ctx->prof ? 1 : std::min(nb_max, kDefaultBranches);
     // units onto nbv branches (longest first onto the least loaded), each
     // branch's scratch grown for its units, its stream and events made
     auto setup = [&](int nbv) -> lgf_status {
         std::vector<int> order(units.size());
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
         std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return units[a].cost > units[c].cost; });
-        double load[kBranches] = {0, 0, 0, 0};
+        double load[kBranches] = {};
         for (int i : order) {
             int best = 0;
             for (int b = 1; b < nbv; ++b)
@@ -895,8 +895,8 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         return LGF_OK;
     };
     // 4. the branch count of this batch shape: the persisted choice, or (tuning
-    //    on, a new shape) the fastest of 1, 2 and 4 branches timed with direct
-    //    launches on the caller's stream
+    //    on, a new shape) the fastest of 1, 2, 4 and 8 branches timed with
+    //    direct launches on the caller's stream (4 first: the others must win by 3 %)
     if (ctx->tune_mode != LGF_TUNE_OFF && !ctx->prof && s != nullptr && nb_max > 1) {
         const std::string tk = tune_batch_key(ctx->prec == LGF_F64, tune_hash(shape.data(), shape.size()));
         auto it = ctx->tune_db.find(tk);
@@ -910,7 +910,7 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
             LGF_CUDA(ctx, cudaEventCreate(&e1));
             float tbest = 0.f;
             int best = nb;
-            for (int cand : {4, 2, 1}) {
+            for (int cand : {4, 8, 2, 1}) {
                 if (cand > nb_max) continue;
                 if ((st = setup(cand)) != LGF_OK) break;
                 nb = cand;

@@ -155,7 +155,8 @@ struct CurlPlan {
     uint64_t used = 0;
     ~CurlPlan();
 };
-constexpr int kBranches = 4;   // concurrent branches of a batch
+constexpr int kBranches = 8;        // most concurrent branches of a batch
+constexpr int kDefaultBranches = 4; // branches of an untuned batch
 
 }  // namespace lgf
 

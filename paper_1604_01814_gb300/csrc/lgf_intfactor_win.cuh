@@ -250,10 +250,14 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
             *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + (((z << LB) + y) << LB) + x0 + v) = r;
         }
     } else {
-        // thread: NV adjacent x values, kV consecutive outputs along the axis
+        // thread: NV adjacent x values, kV consecutive outputs along the axis.
+        // z pass: the slab row (y) varies before the axis group, so the two
+        // thread quads of a quarter-warp read adjacent rows (128 contiguous
+        // bytes, every bank once) where the axis groups would be 64 floats
+        // apart (the same banks); the output rows stay contiguous.
         const int xv = tid % (b / NV);
-        const int av = (tid / (b / NV)) % (b / kV);
-        const int sl = tid / ((b / NV) * (b / kV));
+        const int av = AX == 2 ? tid / ((b / NV) * NS) : (tid / (b / NV)) % (b / kV);
+        const int sl = AX == 2 ? (tid / (b / NV)) % NS : tid / ((b / NV) * (b / kV));
         const int x = xv * NV, a0 = av * kV;
         // element (axis position p in [-HL, b + HL), slab-local sl, x)
         const int st = AX == 1 ? b : NS * b;
@@ -284,7 +288,11 @@ struct XYCfg {
     // different bank groups.
     static constexpr int P2 = 2 * E + 4;
     static constexpr int RG = sizeof(T) == 4 ? (EY / 2) * P2 : EY * E;   // staged elements per plane
-    static constexpr int per_plane = RG + EY * b;
+    // pitch of the x stencil's output rows: 20 floats for FP32 16^3 blocks, so
+    // that the y stencil's two thread quads (rows 4 apart) fall on the two
+    // halves of the banks; b elsewhere
+    static constexpr int IP = sizeof(T) == 4 && b == 16 ? 20 : b;
+    static constexpr int per_plane = RG + EY * IP;
     static constexpr int NS0 = 12288 / per_plane;
     static constexpr int NS = NS0 >= 8 ? 8 : NS0 >= 4 ? 4 : NS0 >= 2 ? 2 : 1;
     static constexpr int NSB = NS > b ? b : NS;
@@ -306,7 +314,8 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
     constexpr int b = C::b, bm = b - 1, NV = Vec<T>::N, NS = C::NSB, HL = RMAX, E = C::E, EY = C::EY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *rg = reinterpret_cast<T *>(smem_raw);       // [NS][EY][E] (FP32: [NS][EY/2][P2])
-    T *im = rg + NS * C::RG;                        // [NS][EY][b]
+    T *im = rg + NS * C::RG;                        // [NS][EY][IP] (row pitch IP >= b)
+    constexpr int IP = C::IP;
     const int o1 = items[2 * blockIdx.x], o2 = items[2 * blockIdx.x + 1];
     const bool pair = o2 >= 0;                      // uniform over the CTA
     const int ny = pair ? 2 : 1;
@@ -407,8 +416,8 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
                 }
             }
             static_assert(kV == 4, "one float4 per row");
-            *reinterpret_cast<float4 *>(im + row * b + x0) = make_float4(acc[0].x, acc[1].x, acc[2].x, acc[3].x);
-            *reinterpret_cast<float4 *>(im + (row + 1) * b + x0) =
+            *reinterpret_cast<float4 *>(im + row * IP + x0) = make_float4(acc[0].x, acc[1].x, acc[2].x, acc[3].x);
+            *reinterpret_cast<float4 *>(im + (row + 1) * IP + x0) =
                 make_float4(acc[0].y, acc[1].y, acc[2].y, acc[3].y);
         } else {
             T acc[kV];
@@ -434,7 +443,7 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
                 T *qq = reinterpret_cast<T *>(&q);
 #pragma unroll
                 for (int e = 0; e < NV; ++e) qq[e] = acc[v + e];
-                *reinterpret_cast<VT *>(im + row * b + x0 + v) = q;
+                *reinterpret_cast<VT *>(im + row * IP + x0 + v) = q;
             }
         }
     }
@@ -447,9 +456,9 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
         const int yv = (it / (b / NV)) % ypp;
         const int zl = it / ((b / NV) * ypp);
         const int x = xv * NV, y0 = yv * kV;                  // output row among the ny * b
-        const T *col = im + (zl * EY + y0) * b + x;           // y_ext = y0 - HL ...
+        const T *col = im + (zl * EY + y0) * IP + x;          // y_ext = y0 - HL ...
         VT q[kV];
-        col_window<RMAX>(col, b, W, q);
+        col_window<RMAX>(col, IP, W, q);
         const int z = s0 + zl;
         const int o = y0 < b ? o1 : o2;
         const int yl = y0 & bm;

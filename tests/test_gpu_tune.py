@@ -90,7 +90,7 @@ def test_batch_branch_count_tuned_once_per_shape(oracle, tmp_path):
             c.batch_apply(batch, stream=s)
         s.synchronize()
     r = c.tune_report()
-    assert r["batches_tuned"] == 1 and r["last_branches"] in (1, 2, 4) and r["plans_tuned"] == len(probs)
+    assert r["batches_tuned"] == 1 and r["last_branches"] in (1, 2, 4, 8) and r["plans_tuned"] == len(probs)
     assert any(l.startswith("B f32 ") for l in open(path).read().splitlines())
     for p, q in zip(probs, batch):
         assert rel_linf(q["u"].cpu().numpy().reshape(p.ncomp, -1), _oracle(oracle, p)) < TOL["f32"]
