@@ -83,8 +83,15 @@ typedef struct {
                                 far-field expansion beyond; default 48, range 8..96 */
     int32_t stencil_radius;  /* fixed E_alpha truncation radius; 0 = from tol */
     int32_t device;          /* CUDA device ordinal used by this context */
-    int32_t reserved[4];     /* must be zero */
+    int32_t flags;           /* LGF_FLAG_* below; 0 = defaults */
+    int32_t reserved[3];     /* must be zero */
 } lgf_options;
+
+/* Stage the integrating factor's z pass with bulk asynchronous copies (the
+   TMA engine's cp.async.bulk, double-buffered in a persistent kernel, waits
+   bounded) instead of per-thread 16-byte loads.  Off by default: on the
+   measured workloads the per-thread loads were faster. */
+#define LGF_FLAG_BULK_STAGING 1
 
 /* Create a context on opt->device (NULL opt = defaults, device 0).
    Errors: LGF_EINVAL (bad option), LGF_ECUDA, LGF_ENOMEM. */
@@ -379,6 +386,22 @@ LGF_API lgf_status lgf_ctx_stats(lgf_ctx *ctx, lgf_stats *out);
    insertion.  Changing max_graphs drops the cached graphs.
    Errors: LGF_EINVAL. */
 LGF_API lgf_status lgf_cache_limits(lgf_ctx *ctx, int32_t max_plans, int32_t max_spectra, int32_t max_graphs);
+
+/* Device-side status.  Kernels that wait on the GPU (the integrating
+   factor's z pass stages its slab with bulk asynchronous copies completed on
+   an mbarrier) bound every wait to about one second; a wait that runs out
+   sets a bit of the context's device error word and its CTA returns without
+   output, so nothing traps and the context stays usable.  This call
+   synchronises the device, stores the word in *word (may be NULL), clears
+   it, and returns LGF_ETIMEOUT when it was set.  Errors: LGF_ETIMEOUT,
+   LGF_ECUDA. */
+LGF_API lgf_status lgf_device_status(lgf_ctx *ctx, int32_t *word);
+
+/* Exercise the timeout path: one CTA waits on an mbarrier that no copy
+   completes, with a limit of `cycles` SM clock cycles (1 .. 4e9), so the wait
+   runs out and sets the device error word that lgf_device_status reports.
+   Nothing faults; the context stays usable.  Errors: LGF_EINVAL, LGF_ECUDA. */
+LGF_API lgf_status lgf_wait_selftest(lgf_ctx *ctx, int64_t cycles, void *stream);
 
 /* Autotuner.  A Poisson plan's geometry has free choices that the method
    leaves open (Sec. 2.2 fixes only the convolution): the embedding of x and

@@ -20,13 +20,15 @@ LGF_OK, LGF_EINVAL, LGF_ENOMEM, LGF_ECUDA, LGF_ETIMEOUT, LGF_EUNSUPPORTED, LGF_E
 LGF_F32, LGF_F64 = 0, 1
 LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR, LGF_OP_KINV = 0, 1, 2, 3
 LGF_TUNE_OFF, LGF_TUNE_ON, LGF_TUNE_CACHED = 0, 1, 2
+LGF_FLAG_BULK_STAGING = 1
 
 # Every symbol include/lgf.h declares (checked by the symbol test).
 EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
            "lgf_kinv_lookup", "lgf_poisson_apply", "lgf_kinv_apply", "lgf_curl", "lgf_curl_adjoint",
            "lgf_velocity_refresh", "lgf_ib_spread", "lgf_ib_interp", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
            "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_ctx_stats", "lgf_cache_limits",
-           "lgf_nested_projection_stage", "lgf_autotune", "lgf_tune_report",
+           "lgf_nested_projection_stage", "lgf_autotune", "lgf_tune_report", "lgf_device_status",
+           "lgf_wait_selftest",
            "lgf_intfactor_apply_noalloc",
            "lgf_status_string", "lgf_last_error", "lgf_version")
 
@@ -37,7 +39,8 @@ class lgf_blockset(ctypes.Structure):
 
 class lgf_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("prec", ctypes.c_int32), ("table_radius", ctypes.c_int32),
-                ("stencil_radius", ctypes.c_int32), ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("stencil_radius", ctypes.c_int32), ("device", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class lgf_problem(ctypes.Structure):
@@ -118,6 +121,8 @@ def load(path: str = LIB_PATH):
         "lgf_cache_limits": [vp, i32, i32, i32],
         "lgf_nested_projection_stage": [vp, ctypes.POINTER(lgf_stage), vp],
         "lgf_autotune": [vp, i32, ctypes.c_char_p],
+        "lgf_device_status": [vp, ctypes.POINTER(i32)],
+        "lgf_wait_selftest": [vp, i64, vp],
         "lgf_tune_report": [vp, ctypes.POINTER(lgf_tune_info)],
         "lgf_intfactor_apply_noalloc": [i32, dbl, dbl, bsp, bsp, vp, vp, i32, i32, vp, ctypes.c_char_p, i32],
         "lgf_status_string": [i32],
@@ -157,10 +162,10 @@ class Context:
     """One lgf_ctx: precision, tolerance, G_L table, plans, spectra, scratch."""
 
     def __init__(self, prec: str = "f32", tol: float = 0.0, table_radius: int = 0, stencil_radius: int = 0,
-                 device: int = 0):
+                 device: int = 0, flags: int = 0):
         self._L = load()
         self.prec = {"f32": LGF_F32, "f64": LGF_F64}[prec]
-        opt = lgf_options(float(tol), self.prec, int(table_radius), int(stencil_radius), int(device))
+        opt = lgf_options(float(tol), self.prec, int(table_radius), int(stencil_radius), int(device), int(flags))
         h = ctypes.c_void_p()
         st = self._L.lgf_ctx_create(ctypes.byref(h), ctypes.byref(opt))
         if st != LGF_OK:
@@ -406,6 +411,16 @@ class Context:
         return {name: (float(getattr(t, name)) if name == "tune_ms" else int(getattr(t, name)))
                 for name, _ in lgf_tune_info._fields_ if name != "reserved"}
 
+    def device_status(self) -> int:
+        """Synchronise and return (and clear) the device error word; raises
+        LgfError (LGF_ETIMEOUT) when a bounded device-side wait ran out."""
+        w = ctypes.c_int32()
+        self._check(self._L.lgf_device_status(self._h, ctypes.byref(w)), "lgf_device_status")
+        return w.value
+
+    def wait_selftest(self, cycles: int = 2000000, stream=None):
+        self._check(self._L.lgf_wait_selftest(self._h, int(cycles), _stream_ptr(stream)), "lgf_wait_selftest")
+
     def stats(self) -> dict:
         """Cache state (lgf_ctx_stats): graphs, plans, spectra, invalidations, scratch."""
         st = lgf_stats()
@@ -510,6 +525,14 @@ def lgf_ctx_stats(ctx: Context) -> dict:
 
 def lgf_cache_limits(ctx: Context, max_plans: int = -1, max_spectra: int = -1, max_graphs: int = -1):
     return ctx.cache_limits(max_plans, max_spectra, max_graphs)
+
+
+def lgf_device_status(ctx: Context) -> int:
+    return ctx.device_status()
+
+
+def lgf_wait_selftest(ctx: Context, cycles: int = 2000000, stream=None):
+    return ctx.wait_selftest(cycles, stream)
 
 
 def lgf_autotune(ctx: Context, mode: int = LGF_TUNE_ON, cache_path: Optional[str] = None):

@@ -211,8 +211,9 @@ lgf_status lgf_ctx_create(lgf_ctx **out, const lgf_options *opt)
     if (!(o.tol >= 0.0) || !std::isfinite(o.tol) || o.tol >= 1.0) return LGF_EINVAL;
     if (o.table_radius != 0 && (o.table_radius < 8 || o.table_radius > 96)) return LGF_EINVAL;
     if (o.stencil_radius < 0 || o.stencil_radius > 128 || o.device < 0) return LGF_EINVAL;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i] != 0) return LGF_EINVAL;
+    if ((o.flags & ~LGF_FLAG_BULK_STAGING) != 0) return LGF_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device >= ndev) {
         cudaGetLastError();
@@ -222,11 +223,18 @@ lgf_status lgf_ctx_create(lgf_ctx **out, const lgf_options *opt)
     lgf_ctx *ctx = new (std::nothrow) lgf_ctx;
     if (!ctx) return LGF_ENOMEM;
     ctx->opt = o;
+    ctx->opt_bulk = (o.flags & LGF_FLAG_BULK_STAGING) != 0;
     ctx->device = o.device;
     ctx->prec = o.prec;
     ctx->tol = o.tol > 0.0 ? o.tol : (o.prec == LGF_F64 ? 1e-13 : 1e-7);
     if (ctx->opt.table_radius == 0) ctx->opt.table_radius = 48;
     if (cudaMalloc(&ctx->red_dev, 16 * sizeof(double)) != cudaSuccess) {
+        delete ctx;
+        return LGF_ENOMEM;
+    }
+    if (cudaMalloc(&ctx->err_dev, sizeof(int)) != cudaSuccess || cudaMemset(ctx->err_dev, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(ctx->red_dev);
+        cudaFree(ctx->err_dev);
         delete ctx;
         return LGF_ENOMEM;
     }
@@ -268,6 +276,9 @@ lgf_status lgf_ctx_destroy(lgf_ctx *ctx)
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     cudaFree(ctx->red_dev);
+    cudaFree(ctx->err_dev);
+    cudaFree(ctx->tune_f);
+    cudaFree(ctx->tune_u);
     for (auto &r : ctx->prof_pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -970,6 +981,27 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     ctx->graphs.add(std::move(key), exec, ++ctx->graph_clock);
     LGF_CUDA(ctx, cudaGraphLaunch(exec, s));
     return LGF_OK;
+}
+
+lgf_status lgf_device_status(lgf_ctx *ctx, int32_t *word)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    LGF_CUDA(ctx, cudaDeviceSynchronize());
+    int w = 0;
+    LGF_CUDA(ctx, cudaMemcpy(&w, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    LGF_CUDA(ctx, cudaMemset(ctx->err_dev, 0, sizeof(int)));
+    if (word) *word = w;
+    if (w != 0) return fail(ctx, LGF_ETIMEOUT, "a bounded device-side wait ran out (error word " + std::to_string(w) + ")");
+    return LGF_OK;
+}
+
+lgf_status lgf_wait_selftest(lgf_ctx *ctx, int64_t cycles, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (cycles < 1 || cycles > 4000000000LL) return fail(ctx, LGF_EINVAL, "wait_selftest: cycles in [1, 4e9]");
+    return wait_selftest(ctx, cycles, (cudaStream_t)stream);
 }
 
 lgf_status lgf_autotune(lgf_ctx *ctx, int32_t mode, const char *cache_path)

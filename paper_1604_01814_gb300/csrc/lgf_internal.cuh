@@ -208,6 +208,8 @@ struct lgf_ctx {
     uint64_t graph_clock = 0;
 
     double *red_dev = nullptr;   // small reduction buffer (residual, table mismatch)
+    int *err_dev = nullptr;      // device error word: bits set by bounded waits that ran out
+    bool opt_bulk = false;       // stage the E z pass with bulk asynchronous copies (LGF_FLAG_BULK_STAGING)
 
     // autotuner: mode (LGF_TUNE_*), persisted choices (key -> value lines of
     // lgf_tune.h, loaded from and appended to tune_path), counters, the
@@ -334,6 +336,10 @@ lgf_status poisson_time_choice(lgf_ctx *ctx, PoissonPlan *pl, const PoissonChoic
                                cudaStream_t s, float *ms);
 // Record a tuned item (in memory and appended to the persisted file).
 void tune_record(lgf_ctx *ctx, const std::string &key, const std::string &value);
+
+// A single CTA waiting on an mbarrier that no copy completes, with a limit of
+// `cycles`: the wait runs out and sets the device error word (lgf_stage.cu).
+lgf_status wait_selftest(lgf_ctx *ctx, long long cycles, cudaStream_t s);
 
 // Block-set validation shared by the entry points.
 lgf_status check_blockset(lgf_ctx *ctx, const lgf_blockset *bs, const char *name);

@@ -536,6 +536,11 @@ static lgf_status run_sep_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, 
 
 lgf_status intf_run_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, int njobs, int nfields, cudaStream_t s)
 {
+    // the stencil kernels move 16-byte vectors (block and field strides keep
+    // the alignment of the base pointers)
+    for (int j = 0; j < njobs; ++j)
+        if ((reinterpret_cast<uintptr_t>(jobs[j].f) | reinterpret_cast<uintptr_t>(jobs[j].u)) % 16 != 0)
+            return fail(ctx, LGF_EINVAL, "integrating factor: f and u must be 16-byte aligned");
     lgf_status st = intf_prepare_scratch(ctx, pl, nfields, njobs);
     if (st != LGF_OK) return st;
     const int ntgt = (int)(pl->tgt.size() / 3);
@@ -625,6 +630,8 @@ extern "C" LGF_API lgf_status lgf_intfactor_apply_noalloc(int32_t prec, double t
         return err(LGF_EUNSUPPORTED, "more than 1024 blocks in the source or target set");
     if (tgt->nblocks > 0 && !u_dev) return err(LGF_EINVAL, "null output pointer");
     if (src->nblocks > 0 && tgt->nblocks > 0 && !f_dev) return err(LGF_EINVAL, "null input pointer");
+    if ((reinterpret_cast<uintptr_t>(f_dev) | reinterpret_cast<uintptr_t>(u_dev)) % 16 != 0)
+        return err(LGF_EINVAL, "f and u must be 16-byte aligned");
     const int b = src->b, nf = ncomp * nrhs;
     const size_t esz = prec == LGF_F64 ? 8 : 4;
     const size_t b3 = (size_t)b * b * b;

@@ -13,8 +13,10 @@
 // values in the y and z passes, adjacent y rows in the x pass of the fused
 // x+y kernel.
 #pragma once
+#include <algorithm>
 #include <type_traits>
 
+#include "lgf_async.cuh"
 #include "lgf_internal.cuh"
 
 namespace lgf {
@@ -273,6 +275,104 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
     }
 }
 
+// The z pass as a persistent kernel that stages with bulk asynchronous
+// copies.  In the block layout every staged z-plane of a slab (NS rows of b)
+// is one contiguous run, so a slab plus its halo is at most E bulk copies
+// (cp.async.bulk, completed on an mbarrier); planes of absent blocks are
+// zero-filled.  Each CTA walks the items (output block, slab, job, field)
+// with a stride of the grid and keeps two slab buffers: the copies of item
+// t + 1 are in flight while the stencil runs on item t.  Every wait is
+// bounded; one that runs out sets a bit of *err, drains the other buffer's
+// copies (again bounded) and ends the CTA (lgf_async.cuh).  Results equal
+// those of k_sep_win<T, LB, 2, RMAX> bit for bit.
+template <typename T, int LB, int RMAX>
+__global__ void __launch_bounds__(Cfg<T, LB, 2>::THREADS)
+    k_sep_z_bulk(const SepJobs<T> jobs, const int *__restrict__ nbr, int nr, int nout, int *err)
+{
+    using C = Cfg<T, LB, 2>;
+    using VT = typename Vec<T>::V;
+    constexpr int b = C::b, bm = b - 1, NV = C::NV, NS = C::NS, HL = RMAX, E = b + 2 * HL;
+    constexpr int PV = NS * b;      // values per staged plane
+    constexpr int NSL = b / NS;     // slabs per block
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sbuf = reinterpret_cast<T *>(smem_raw);   // [2][E][NS][b]
+    __shared__ __align__(8) uint64_t bar[2];
+    const int nd = 2 * nr + 1;
+    const int nitems = nout * NSL * jobs.n * jobs.nf;
+    if (threadIdx.x == 0) {
+        async::mbar_init(&bar[0]);
+        async::mbar_init(&bar[1]);
+    }
+    __syncthreads();
+    // item -> output block o (fastest, for neighbour reuse in L2), slab, field, job
+    auto decode = [&](int i, int &o, int &s0, int &fd, int &jb) {
+        o = i % nout;
+        int r = i / nout;
+        s0 = (r % NSL) * NS;
+        r /= NSL;
+        fd = r % jobs.nf;
+        jb = r / jobs.nf;
+    };
+    // stage item i into buffer k: zero the planes of absent blocks, then the
+    // first warp announces the bytes and issues one bulk copy per present plane
+    auto issue = [&](int i, int k) {
+        int o, s0, fd, jb;
+        decode(i, o, s0, fd, jb);
+        const int *nb = nbr + (int64_t)o * nd;
+        const T *inf = jobs.j[jb].in + fd * jobs.j[jb].in_stride;
+        T *sb = sbuf + k * E * PV;
+        for (int it = threadIdx.x; it < E * (PV / NV); it += C::THREADS)
+            if (nb[(it / (PV / NV) - HL + nr * b) >> LB] < 0) *reinterpret_cast<VT *>(sb + it * NV) = VT{};
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            if (lane == 0) {
+                uint32_t bytes = 0;
+                for (int p = 0; p < E; ++p) bytes += nb[(p - HL + nr * b) >> LB] >= 0 ? PV * sizeof(T) : 0;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                async::mbar_arrive_expect(&bar[k], bytes);
+            }
+            __syncwarp();
+            for (int p = lane; p < E; p += 32) {
+                const int e = p - HL;
+                const int bi = nb[(e + nr * b) >> LB];
+                if (bi >= 0)
+                    async::bulk_copy(sb + p * PV, inf + ((int64_t)bi << (3 * LB)) + (((e & bm) << LB) + s0) * b,
+                                     PV * sizeof(T), &bar[k]);
+            }
+        }
+    };
+    const int tid = threadIdx.x;
+    const int xv = tid % (b / NV);
+    const int sl = (tid / (b / NV)) % NS;
+    const int av = tid / ((b / NV) * NS);
+    const int x = xv * NV, a0 = av * kV;
+    int t = 0;
+    if ((int)blockIdx.x < nitems) issue(blockIdx.x, 0);
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x, ++t) {
+        const int k = t & 1;
+        const int inext = i + gridDim.x;
+        if (inext < nitems) issue(inext, k ^ 1);
+        const bool ok = async::mbar_wait(&bar[k], (t >> 1) & 1, err);
+        if (!__syncthreads_and(ok)) {
+            if (inext < nitems) async::mbar_wait(&bar[k ^ 1], ((t + 1) >> 1) & 1, nullptr);
+            return;
+        }
+        int o, s0, fd, jb;
+        decode(i, o, s0, fd, jb);
+        const SepJob<T> &J = jobs.j[jb];
+        WinW<T, RMAX> W;
+        load_weights(W, J.w, J.R);
+        const T *col = sbuf + k * E * PV + (a0 * NS + sl) * b + x;
+        VT r[kV];
+        col_window<RMAX>(col, NS * b, W, r);
+        T *outf = J.out + fd * J.out_stride;
+#pragma unroll
+        for (int v = 0; v < kV; ++v)
+            *reinterpret_cast<VT *>(outf + ((int64_t)o << (3 * LB)) + ((((a0 + v) << LB) + s0 + sl) << LB) + x) = r[v];
+        __syncthreads();   // buffer k is read; the next iteration may refill it
+    }
+}
+
 // Fused x and y passes.  A CTA owns one output block, or two that are
 // neighbours in y (a pair shares the y halo between them: 2b + 2 RMAX staged
 // rows for 2b outputs instead of 2 (b + 2 RMAX)), and NS z-planes.  It stages
@@ -502,6 +602,29 @@ lgf_status launch_m(lgf_ctx *ctx, int nout, const SepJobs<T> &jobs, cudaStream_t
     constexpr int b = 1 << LB, E = b + 2 * RMAX;
     constexpr size_t smem = sizeof(T) * (size_t)C::NS * b * E;
     auto kern = k_sep_win<T, LB, AX, RMAX>;
+    // the z pass stages with bulk copies when every job's input is 16-byte
+    // aligned (the copies' requirement; block and plane offsets keep it) and
+    // the context has a device error word for the bounded waits
+    bool aligned = AX == 2 && ctx != nullptr && ctx->err_dev != nullptr && ctx->opt_bulk;
+    for (int i = 0; i < jobs.n; ++i)
+        aligned = aligned && (reinterpret_cast<uintptr_t>(jobs.j[i].in) % 16 == 0) &&
+                  ((jobs.j[i].in_stride * (int64_t)sizeof(T)) % 16 == 0);
+    if constexpr (AX == 2) {
+        if (aligned) {
+            auto kb = k_sep_z_bulk<T, LB, RMAX>;
+            const size_t sm2 = 2 * smem;
+            cudaError_t e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+            int per_sm = 0;
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb, C::THREADS, sm2);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "bulk z pass set-up");
+            int nsm = 0;
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+            const int64_t nitems = (int64_t)nout * (b / C::NS) * jobs.n * jobs.nf;
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nitems, (int64_t)std::max(1, per_sm) * nsm));
+            kb<<<grid, C::THREADS, sm2, s>>>(jobs, nbr, nr, nout, ctx->err_dev);
+            return LGF_OK;
+        }
+    }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");

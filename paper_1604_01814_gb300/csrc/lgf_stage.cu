@@ -10,6 +10,7 @@
 // and G^dagger = -Dbar.  Both read the block itself and, where the shift
 // leaves it, the neighbour block of a CurlPlan (dir +1 for Dbar, -1 for G);
 // values outside the input block set are zero.  One thread per output cell.
+#include "lgf_async.cuh"
 #include "lgf_internal.cuh"
 
 namespace lgf {
@@ -176,6 +177,17 @@ lgf_status grad_t(lgf_ctx *ctx, int lb, const T *d, const T *a, const T *c, T *o
     return LGF_OK;
 }
 
+// The timeout path of the bounded waits: an mbarrier expecting one arrival
+// that never comes (no thread arrives, no copy is issued), so the wait runs
+// out after `cycles` and sets the error word.
+__global__ void k_wait_selftest(int *err, long long cycles)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) async::mbar_init(&bar);
+    __syncthreads();
+    async::mbar_wait(&bar, 0, err, cycles);
+}
+
 int lb_of(int b)
 {
     int l = 0;
@@ -213,6 +225,13 @@ lgf_status stage_grad(lgf_ctx *ctx, const CurlPlan *pl, const void *d, const voi
                               (double *)out, pl->nbr_dev, ncell, 1.0 / dx, s);
     return grad_t<float>(ctx, lb_of(pl->b), (const float *)d, (const float *)a, (const float *)c, (float *)out,
                          pl->nbr_dev, ncell, (float)(1.0 / dx), s);
+}
+
+lgf_status wait_selftest(lgf_ctx *ctx, long long cycles, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(ctx->err_dev, cycles);
+    LGF_CHECK_LAUNCH(ctx, "wait self-test");
+    return LGF_OK;
 }
 
 // rhs = U - ub; y = W1 rhs; fh = W2 y (W2 null: W1^T y).  Vectors of n values.
