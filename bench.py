@@ -542,6 +542,12 @@ def run_ours(args, rank, world, dist):
             errs.append((np.abs(got - ref).max(), np.abs(ref).max()))
         # per field: max |err| over its samples / max |ref| over its samples
         rel_err = float(max(a / b for a, b in errs if b > 0))
+        # the library's own a-posteriori estimate (FP64 direct sums on the GPU)
+        lib_est = 0.0
+        for e, q in zip([e for e in w.entries if e["op"] in (0, 2)], bp):
+            p = e["p"]
+            lib_est = max(lib_est, ctx.poisson_error_estimate(p.b, p.src, p.tgt, q["f"], q["u"], ncomp=p.ncomp,
+                                                              nrhs=p.nrhs, nsample=16))
         del fsp, bp, outp
         npts = sum(len(x[2]) for x in samples)
 
@@ -674,6 +680,7 @@ def run_ours(args, rank, world, dist):
         line["rel_err_vs_oracle"] = rel_err
         line["rel_err_how"] = ("Poisson apply of the same inputs in the same context, at the cpu_baseline "
                                "sample: per field max |gpu - oracle| / max |oracle|")
+        line["rel_err_estimate_lib"] = lib_est
     ctx.close()
     return line
 

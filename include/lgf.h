@@ -387,6 +387,30 @@ LGF_API lgf_status lgf_ctx_stats(lgf_ctx *ctx, lgf_stats *out);
    Errors: LGF_EINVAL. */
 LGF_API lgf_status lgf_cache_limits(lgf_ctx *ctx, int32_t max_plans, int32_t max_spectra, int32_t max_graphs);
 
+/* A-posteriori error estimate of a Poisson result (the diagnostic of the
+   scope table's boundary): at `nsample` target points spread evenly over the
+   target blocks, the exact sum dx^2 sum_m G_L(n - m) f(m) of Sec. 2.2,
+   Eq. dpoisson_conv, is formed in FP64 on the GPU (one CTA per point over
+   every source point, G_L from the context's table and expansion), and
+   *max_rel_err (host) receives the largest over the fields of
+   max |u - exact| / max |exact| at those points.  f_dev and u_dev are as in
+   lgf_poisson_apply (u its result).  Cost: nsample x sources FP64 terms per
+   field.  Synchronous.  Errors: as lgf_poisson_apply; LGF_EINVAL (nsample
+   outside 1..65536). */
+LGF_API lgf_status lgf_poisson_error_estimate(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt,
+                                              const void *f_dev, const void *u_dev, int32_t ncomp, int32_t nrhs,
+                                              double dx, int32_t nsample, double *max_rel_err, void *stream);
+
+/* Save the context's FP64 G_L table (the App. A pre-processing) to a file,
+   and load one back into a context (skipping the quadrature): a versioned
+   header ("LGFTAB01", radius, entry count, near/far shell mismatch), the
+   values, and a 64-bit hash of them.  A load replaces the table and drops the
+   spectra, G_K tables and graphs built from the old one; a file that fails
+   any check is refused.  Errors: LGF_EINVAL (path, file), LGF_ENOTABLE
+   (save before a build), LGF_ENOMEM, LGF_ECUDA. */
+LGF_API lgf_status lgf_table_save(lgf_ctx *ctx, const char *path);
+LGF_API lgf_status lgf_table_load(lgf_ctx *ctx, const char *path);
+
 /* Device-side status.  Kernels that wait on the GPU (the integrating
    factor's z pass stages its slab with bulk asynchronous copies completed on
    an mbarrier) bound every wait to about one second; a wait that runs out

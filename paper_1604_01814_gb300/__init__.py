@@ -12,7 +12,7 @@ from ._binding import (EXPORTS, LGF_F32, LGF_F64, LGF_TUNE_CACHED, LGF_TUNE_OFF,
                        LGF_OP_POISSON_THEN_INTFACTOR, LIB_PATH, Context, LgfError, lgf_batch_apply,
                        lgf_cache_limits, lgf_ctx_create, lgf_ctx_destroy, lgf_ctx_stats, lgf_device_status, lgf_wait_selftest, lgf_curl, lgf_curl_adjoint, lgf_intfactor_apply,
                        lgf_intfactor_apply_noalloc, lgf_velocity_refresh, lgf_ib_spread, lgf_ib_interp,
-                       lgf_intfactor_weights, lgf_kinv_apply, lgf_nested_projection_stage, lgf_kinv_lookup, lgf_poisson_apply, lgf_profile_enable,
+                       lgf_intfactor_weights, lgf_kinv_apply, lgf_nested_projection_stage, lgf_kinv_lookup, lgf_poisson_apply, lgf_poisson_error_estimate, lgf_table_load, lgf_table_save, lgf_profile_enable,
                        lgf_profile_read, lgf_residual, lgf_status_string, lgf_table_build, lgf_table_info,
                        lgf_table_lookup, lgf_version, load)
 

@@ -28,7 +28,7 @@ EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_in
            "lgf_velocity_refresh", "lgf_ib_spread", "lgf_ib_interp", "lgf_intfactor_apply", "lgf_intfactor_weights", "lgf_batch_apply",
            "lgf_residual", "lgf_profile_enable", "lgf_profile_read", "lgf_ctx_stats", "lgf_cache_limits",
            "lgf_nested_projection_stage", "lgf_autotune", "lgf_tune_report", "lgf_device_status",
-           "lgf_wait_selftest",
+           "lgf_wait_selftest", "lgf_poisson_error_estimate", "lgf_table_save", "lgf_table_load",
            "lgf_intfactor_apply_noalloc",
            "lgf_status_string", "lgf_last_error", "lgf_version")
 
@@ -122,6 +122,9 @@ def load(path: str = LIB_PATH):
         "lgf_nested_projection_stage": [vp, ctypes.POINTER(lgf_stage), vp],
         "lgf_autotune": [vp, i32, ctypes.c_char_p],
         "lgf_device_status": [vp, ctypes.POINTER(i32)],
+        "lgf_poisson_error_estimate": [vp, bsp, bsp, vp, vp, i32, i32, dbl, i32, ctypes.POINTER(dbl), vp],
+        "lgf_table_save": [vp, ctypes.c_char_p],
+        "lgf_table_load": [vp, ctypes.c_char_p],
         "lgf_wait_selftest": [vp, i64, vp],
         "lgf_tune_report": [vp, ctypes.POINTER(lgf_tune_info)],
         "lgf_intfactor_apply_noalloc": [i32, dbl, dbl, bsp, bsp, vp, vp, i32, i32, vp, ctypes.c_char_p, i32],
@@ -411,6 +414,27 @@ class Context:
         return {name: (float(getattr(t, name)) if name == "tune_ms" else int(getattr(t, name)))
                 for name, _ in lgf_tune_info._fields_ if name != "reserved"}
 
+    def poisson_error_estimate(self, b: int, src, tgt, f, u, ncomp: int = 1, nrhs: int = 1, dx: float = 1.0,
+                               nsample: int = 64, stream=None) -> float:
+        """Largest relative error of u against the FP64 direct sum at nsample targets."""
+        s_, sa = _blockset(b, src)
+        t_, ta = _blockset(b, tgt)
+        nf = ncomp * nrhs
+        if s_.nblocks and t_.nblocks:
+            self._field(f, s_.nblocks, b, nf, "f")
+            self._field(u, t_.nblocks, b, nf, "u")
+        e = ctypes.c_double()
+        self._check(self._L.lgf_poisson_error_estimate(self._h, ctypes.byref(s_), ctypes.byref(t_), _ptr(f), _ptr(u),
+                                                       ncomp, nrhs, float(dx), int(nsample), ctypes.byref(e),
+                                                       _stream_ptr(stream)), "lgf_poisson_error_estimate")
+        return e.value
+
+    def table_save(self, path: str):
+        self._check(self._L.lgf_table_save(self._h, path.encode()), "lgf_table_save")
+
+    def table_load(self, path: str):
+        self._check(self._L.lgf_table_load(self._h, path.encode()), "lgf_table_load")
+
     def device_status(self) -> int:
         """Synchronise and return (and clear) the device error word; raises
         LgfError (LGF_ETIMEOUT) when a bounded device-side wait ran out."""
@@ -525,6 +549,18 @@ def lgf_ctx_stats(ctx: Context) -> dict:
 
 def lgf_cache_limits(ctx: Context, max_plans: int = -1, max_spectra: int = -1, max_graphs: int = -1):
     return ctx.cache_limits(max_plans, max_spectra, max_graphs)
+
+
+def lgf_poisson_error_estimate(ctx: Context, *a, **kw) -> float:
+    return ctx.poisson_error_estimate(*a, **kw)
+
+
+def lgf_table_save(ctx: Context, path: str):
+    return ctx.table_save(path)
+
+
+def lgf_table_load(ctx: Context, path: str):
+    return ctx.table_load(path)
 
 
 def lgf_device_status(ctx: Context) -> int:

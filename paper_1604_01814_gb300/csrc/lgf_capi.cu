@@ -983,6 +983,79 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     return LGF_OK;
 }
 
+lgf_status lgf_poisson_error_estimate(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt,
+                                      const void *f_dev, const void *u_dev, int32_t ncomp, int32_t nrhs, double dx,
+                                      int32_t nsample, double *max_rel_err, void *stream)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if ((st = check_blockset(ctx, src, "source")) != LGF_OK) return st;
+    if ((st = check_blockset(ctx, tgt, "target")) != LGF_OK) return st;
+    if (src->b != tgt->b) return fail(ctx, LGF_EINVAL, "source and target block edges differ");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(ctx, LGF_EINVAL, "dx must be positive and finite");
+    if ((st = check_fields(ctx, f_dev, const_cast<void *>(u_dev), ncomp, nrhs, src->nblocks, tgt->nblocks)) !=
+        LGF_OK)
+        return st;
+    if (nsample < 1 || nsample > 65536 || !max_rel_err) return fail(ctx, LGF_EINVAL, "error estimate: nsample 1..65536");
+    if (!ctx->table_dev) return fail(ctx, LGF_ENOTABLE, "lgf_table_build has not been called");
+    *max_rel_err = 0.0;
+    if (tgt->nblocks == 0 || src->nblocks == 0) return LGF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int b = tgt->b;
+    const int64_t b3 = (int64_t)b * b * b, ntot = (int64_t)tgt->nblocks * b3;
+    const int n = (int)std::min<int64_t>(nsample, ntot);
+    // evenly spread target points, in the field's element order
+    std::vector<int64_t> idx(n);
+    std::vector<int32_t> pts(3 * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+        const int64_t i = std::min<int64_t>(ntot - 1, (int64_t)(((double)k + 0.5) * (double)ntot / n));
+        idx[k] = i;
+        const int64_t blk = i / b3, loc = i % b3;
+        pts[3 * k] = tgt->coords[3 * blk] * b + (int)(loc % b);
+        pts[3 * k + 1] = tgt->coords[3 * blk + 1] * b + (int)((loc / b) % b);
+        pts[3 * k + 2] = tgt->coords[3 * blk + 2] * b + (int)(loc / ((int64_t)b * b));
+    }
+    const size_t esz = elem_size(ctx);
+    std::vector<double> ref(n), got(n);
+    double worst = 0.0;
+    for (int fld = 0; fld < ncomp * nrhs; ++fld) {
+        const void *ff = (const unsigned char *)f_dev + (size_t)fld * src->nblocks * b3 * esz;
+        const void *uf = (const unsigned char *)u_dev + (size_t)fld * ntot * esz;
+        if ((st = direct_samples(ctx, src, ff, pts.data(), n, dx, ref.data(), s)) != LGF_OK) return st;
+        if ((st = gather_values(ctx, uf, idx.data(), n, got.data(), s)) != LGF_OK) return st;
+        double num = 0.0, den = 0.0;
+        for (int k = 0; k < n; ++k) {
+            num = std::max(num, std::fabs(got[k] - ref[k]));
+            den = std::max(den, std::fabs(ref[k]));
+        }
+        if (den > 0.0) worst = std::max(worst, num / den);
+    }
+    *max_rel_err = worst;
+    return LGF_OK;
+}
+
+lgf_status lgf_table_save(lgf_ctx *ctx, const char *path)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (!path) return fail(ctx, LGF_EINVAL, "table_save: null path");
+    if (!ctx->table_dev) return fail(ctx, LGF_ENOTABLE, "table not built");
+    return table_save(ctx, path);
+}
+
+lgf_status lgf_table_load(lgf_ctx *ctx, const char *path)
+{
+    lgf_status st = enter(ctx);
+    if (st != LGF_OK) return st;
+    if (!path) return fail(ctx, LGF_EINVAL, "table_load: null path");
+    before_evict(ctx);   // spectra, G_K tables and graphs built from the old table go
+    if ((st = table_load(ctx, path)) != LGF_OK) return st;
+    ctx->spectra.clear();
+    for (auto &kv : ctx->gk_tables) cudaFree(kv.second);
+    ctx->gk_tables.clear();
+    return LGF_OK;
+}
+
 lgf_status lgf_device_status(lgf_ctx *ctx, int32_t *word)
 {
     lgf_status st = enter(ctx);

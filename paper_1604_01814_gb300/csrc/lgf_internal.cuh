@@ -274,6 +274,15 @@ lgf_status table_lookup(lgf_ctx *ctx, const double *table, const int32_t *off, i
 lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], int xc, int xP, int yc, int yP,
                          double *box, cudaStream_t s);
 lgf_status bessel_weights(lgf_ctx *ctx, double z, int nmax, double *out_dev, cudaStream_t s);
+// FP64 direct sums dx^2 sum_m G_L(t - m) f(m) of one source field at npts
+// lattice points (host [npts][3]); values to host out.  Synchronous.
+lgf_status direct_samples(lgf_ctx *ctx, const lgf_blockset *src, const void *f_field, const int32_t *pts_host,
+                          int npts, double dx, double *out_host, cudaStream_t s);
+// Values of a field at element indices (host), to host doubles.  Synchronous.
+lgf_status gather_values(lgf_ctx *ctx, const void *field, const int64_t *idx_host, int n, double *out_host,
+                         cudaStream_t s);
+lgf_status table_save(lgf_ctx *ctx, const char *path);
+lgf_status table_load(lgf_ctx *ctx, const char *path);
 
 // Poisson (lgf_poisson.cu)
 lgf_status poisson_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, PoissonPlan **out);

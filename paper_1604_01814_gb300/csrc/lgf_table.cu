@@ -391,6 +391,64 @@ lgf_status gk_table(lgf_ctx *ctx, double alpha, const double **out, cudaStream_t
     return LGF_OK;
 }
 
+// File form of the G_L table: magic "LGFTAB01", int32 radius, int64 count,
+// double shell mismatch, the count FP64 values, then their 64-bit FNV-1a
+// hash (little-endian host; the file is rejected unless all of it checks).
+lgf_status table_save(lgf_ctx *ctx, const char *path)
+{
+    const int64_t n = (int64_t)(ctx->table_radius + 1) * (ctx->table_radius + 2) * (ctx->table_radius + 3) / 6;
+    std::vector<double> h((size_t)n);
+    LGF_CUDA(ctx, cudaMemcpy(h.data(), ctx->table_dev, n * sizeof(double), cudaMemcpyDeviceToHost));
+    unsigned long long hash = 1469598103934665603ull;
+    const unsigned char *bytes = (const unsigned char *)h.data();
+    for (size_t i = 0; i < h.size() * sizeof(double); ++i) hash = (hash ^ bytes[i]) * 1099511628211ull;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, LGF_EINVAL, std::string("table_save: cannot open ") + path);
+    const char magic[8] = {'L', 'G', 'F', 'T', 'A', 'B', '0', '1'};
+    const int32_t R = ctx->table_radius;
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(&R, 4, 1, f) == 1 && std::fwrite(&n, 8, 1, f) == 1 &&
+              std::fwrite(&ctx->shell_mismatch, 8, 1, f) == 1 &&
+              std::fwrite(h.data(), sizeof(double), h.size(), f) == h.size() && std::fwrite(&hash, 8, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? LGF_OK : fail(ctx, LGF_EINVAL, std::string("table_save: write failed: ") + path);
+}
+
+lgf_status table_load(lgf_ctx *ctx, const char *path)
+{
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, LGF_EINVAL, std::string("table_load: cannot open ") + path);
+    char magic[8];
+    int32_t R = 0;
+    int64_t n = 0;
+    double mm = 0.0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "LGFTAB01", 8) == 0 &&
+              std::fread(&R, 4, 1, f) == 1 && std::fread(&n, 8, 1, f) == 1 && std::fread(&mm, 8, 1, f) == 1 &&
+              R >= 8 && R <= 96 && n == (int64_t)(R + 1) * (R + 2) * (R + 3) / 6;
+    std::vector<double> h(ok ? (size_t)n : 0);
+    unsigned long long hash = 0, want = 1469598103934665603ull;
+    if (ok) ok = std::fread(h.data(), sizeof(double), h.size(), f) == h.size() && std::fread(&hash, 8, 1, f) == 1;
+    std::fclose(f);
+    if (ok) {
+        const unsigned char *bytes = (const unsigned char *)h.data();
+        for (size_t i = 0; i < h.size() * sizeof(double); ++i) want = (want ^ bytes[i]) * 1099511628211ull;
+        ok = hash == want;
+    }
+    if (!ok) return fail(ctx, LGF_EINVAL, std::string("table_load: not a valid G_L table file: ") + path);
+    double *dev = nullptr;
+    if (cudaMalloc(&dev, n * sizeof(double)) != cudaSuccess)
+        return fail(ctx, LGF_ENOMEM, "table_load: allocation failed");
+    cudaError_t e = cudaMemcpy(dev, h.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return cuda_fail(ctx, e, "table_load: copy");
+    }
+    cudaFree(ctx->table_dev);
+    ctx->table_dev = dev;
+    ctx->table_radius = R;
+    ctx->shell_mismatch = mm;
+    return LGF_OK;
+}
+
 lgf_status table_lookup(lgf_ctx *ctx, const double *table, const int32_t *off, int64_t n, double *out,
                         cudaStream_t s)
 {
@@ -398,6 +456,110 @@ lgf_status table_lookup(lgf_ctx *ctx, const double *table, const int32_t *off, i
     k_lookup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(table, ctx->table_radius, off, n, out);
     LGF_CHECK_LAUNCH(ctx, "lookup kernel");
     return LGF_OK;
+}
+
+namespace {
+// The exact sum u(t) = dx^2 sum_m G_L(t - m) f(m) at one sampled target per
+// CTA, in FP64 (G_L from the table and its expansion, as the apply uses it):
+// the reference values of the a-posteriori error estimate.
+template <typename T>
+__global__ void __launch_bounds__(256) k_direct_sample(const double *table, int R, const int *src, int nsrc, int lb,
+                                                       const T *f, const int *pts, double dx2, double *out)
+{
+    const int *tp = pts + 3 * blockIdx.x;
+    const int tx = tp[0], ty = tp[1], tz = tp[2];
+    const int b = 1 << lb, b3 = b * b * b;
+    const int64_t n = (int64_t)nsrc * b3;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const T v = f[i];
+        if (v == T(0)) continue;
+        const int blk = (int)(i >> (3 * lb)), loc = (int)(i & (b3 - 1));
+        const int mx = src[3 * blk] * b + (loc & (b - 1));
+        const int my = src[3 * blk + 1] * b + ((loc >> lb) & (b - 1));
+        const int mz = src[3 * blk + 2] * b + (loc >> (2 * lb));
+        acc += lgf_value(table, R, tx - mx, ty - my, tz - mz) * (double)v;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = dx2 * red[0];
+}
+}  // namespace
+
+namespace {
+template <typename T>
+__global__ void k_gather(const T *field, const int64_t *idx, int n, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)field[idx[i]];
+}
+}  // namespace
+
+lgf_status gather_values(lgf_ctx *ctx, const void *field, const int64_t *idx_host, int n, double *out_host,
+                         cudaStream_t s)
+{
+    if (n <= 0) return LGF_OK;
+    int64_t *didx = nullptr;
+    double *dout = nullptr;
+    if (cudaMalloc(&didx, sizeof(int64_t) * n) != cudaSuccess || cudaMalloc(&dout, sizeof(double) * n) != cudaSuccess) {
+        cudaFree(didx);
+        return fail(ctx, LGF_ENOMEM, "error estimate: allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(didx, idx_host, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        if (ctx->prec == LGF_F64)
+            k_gather<double><<<(n + 255) / 256, 256, 0, s>>>((const double *)field, didx, n, dout);
+        else
+            k_gather<float><<<(n + 255) / 256, 256, 0, s>>>((const float *)field, didx, n, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dout, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(didx);
+    cudaFree(dout);
+    return e == cudaSuccess ? LGF_OK : cuda_fail(ctx, e, "error estimate: gather");
+}
+
+lgf_status direct_samples(lgf_ctx *ctx, const lgf_blockset *src, const void *f_field, const int32_t *pts_host,
+                          int npts, double dx, double *out_host, cudaStream_t s)
+{
+    if (npts <= 0) return LGF_OK;
+    int lb = 0;
+    while ((1 << lb) < src->b) ++lb;
+    int *dsrc = nullptr, *dpts = nullptr;
+    double *dout = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(dsrc);
+        cudaFree(dpts);
+        cudaFree(dout);
+    };
+    if (cudaMalloc(&dsrc, 3 * sizeof(int) * (size_t)std::max(1, src->nblocks)) != cudaSuccess ||
+        cudaMalloc(&dpts, 3 * sizeof(int) * (size_t)npts) != cudaSuccess ||
+        cudaMalloc(&dout, sizeof(double) * (size_t)npts) != cudaSuccess) {
+        cleanup();
+        return fail(ctx, LGF_ENOMEM, "error estimate: allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(dsrc, src->coords, 3 * sizeof(int) * (size_t)src->nblocks,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dpts, pts_host, 3 * sizeof(int) * (size_t)npts, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        if (ctx->prec == LGF_F64)
+            k_direct_sample<double><<<npts, 256, 0, s>>>(ctx->table_dev, ctx->table_radius, dsrc, src->nblocks, lb,
+                                                         (const double *)f_field, dpts, dx * dx, dout);
+        else
+            k_direct_sample<float><<<npts, 256, 0, s>>>(ctx->table_dev, ctx->table_radius, dsrc, src->nblocks, lb,
+                                                        (const float *)f_field, dpts, dx * dx, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dout, sizeof(double) * (size_t)npts, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    return e == cudaSuccess ? LGF_OK : cuda_fail(ctx, e, "error estimate: direct samples");
 }
 
 lgf_status kernel_window(lgf_ctx *ctx, const double *table, const int M[3], int xc, int xP, int yc, int yP,
