@@ -28,6 +28,31 @@
 #include "lgf_poisson_kernels.cuh"
 
 namespace lgf {
+// The pass launchers are instantiated in lgf_poisson_{f32,f64}_{rows,cols,
+// conv,conv_x,conv_y}.cu, which compile in parallel; this unit only calls them.
+#define LGF_EXTERN_PASSES(T)                                                                                      \
+    extern template lgf_status launch_row_forward<T>(lgf_ctx *, const PoissonGeom &, const T *, Cx<T> *,        \
+                                                     const Cx<T> *, int, int, int, cudaStream_t);                \
+    extern template lgf_status launch_row_inverse<T>(lgf_ctx *, const PoissonGeom &, const Cx<T> *, T *,        \
+                                                     const Cx<T> *, int, int, cudaStream_t);                     \
+    extern template lgf_status launch_col_forward<T>(lgf_ctx *, int, int, int, int, const Cx<T> *, Cx<T> *, int, \
+                                                     int, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,   \
+                                                     const Cx<T> *, pk::RowFlags, cudaStream_t, const char *);   \
+    extern template lgf_status launch_col_inverse<T>(lgf_ctx *, int, int, int, int, const Cx<T> *, Cx<T> *, int, \
+                                                     int, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,   \
+                                                     const Cx<T> *, cudaStream_t, const char *);                 \
+    extern template lgf_status launch_col_convolve<T, 0>(lgf_ctx *, const PoissonGeom &, Cx<T> *, const T *,   \
+                                                         const Cx<T> *, int, cudaStream_t);                      \
+    extern template lgf_status launch_col_convolve<T, 1>(lgf_ctx *, const PoissonGeom &, Cx<T> *, const T *,   \
+                                                         const Cx<T> *, int, cudaStream_t);                      \
+    extern template lgf_status launch_col_convolve<T, 2>(lgf_ctx *, const PoissonGeom &, Cx<T> *, const T *,   \
+                                                         const Cx<T> *, int, cudaStream_t);
+LGF_EXTERN_PASSES(float)
+LGF_EXTERN_PASSES(double)
+#undef LGF_EXTERN_PASSES
+}  // namespace lgf
+
+namespace lgf {
 
 namespace {
 // 2^k, 3 * 2^k and 5 * 2^k: the box pays at most 1.34x its extent per axis
