@@ -93,6 +93,15 @@ typedef struct {
    measured workloads the per-thread loads were faster. */
 #define LGF_FLAG_BULK_STAGING 1
 
+/* Execution of lgf_batch_apply where the autotuner has not chosen one for
+   the batch's shape: by default the ragged mode (one launch per pass and
+   transform length across the batch's Poisson parts) when the batch has two
+   or more Poisson parts, per-problem launches otherwise.  BATCH_RAGGED asks
+   for the ragged mode also with one Poisson part; BATCH_PER_PROBLEM for
+   per-problem launches always (not both). */
+#define LGF_FLAG_BATCH_RAGGED 2
+#define LGF_FLAG_BATCH_PER_PROBLEM 4
+
 /* Create a context on opt->device (NULL opt = defaults, device 0).
    Errors: LGF_EINVAL (bad option), LGF_ECUDA, LGF_ENOMEM. */
 LGF_API lgf_status lgf_ctx_create(lgf_ctx **out, const lgf_options *opt);
@@ -201,12 +210,22 @@ typedef struct {
    launch per pass (up to 8 problems per launch, different alphas and buffers
    allowed).  The Poisson parts (each with its own integrating factor when no
    other problem shares its group) and the groups that read only batch inputs
-   are independent units: they are spread over up to 4 concurrent branches
+   are independent units.  With per-problem launches they are spread over up
+   to 4 concurrent branches
    (8 when the autotuner finds that faster)
    (context streams forked from and joined back to the caller's stream, each
    with its own scratch), longest first onto the least loaded branch.
    Groups of several
-   POISSON_THEN_INTFACTOR problems run after the branches join.  On a
+   POISSON_THEN_INTFACTOR problems run after the branches join.  In the
+   ragged mode (see LGF_FLAG_BATCH_RAGGED) the Poisson parts of all
+   problems instead run together: one launch per pass and transform length
+   (each CTA finds its problem in a job table passed with the launch, up to
+   64 problems per launch), the lengths of a pass on concurrent branches,
+   every part with its own slice of one scratch; the integrating-factor
+   groups that read Poisson results follow, their jobs of all block sets
+   together in one launch per pass (and block edge and stencil radius
+   class); the groups that read only batch inputs run likewise on a branch
+   alongside the Poisson passes.  The autotuner times both modes.  On a
    non-default stream the whole batch is captured once into a CUDA graph,
    and later calls with an identical batch (same block lists, pointers,
    alphas, stream) replay it; the context keeps the graphs of the 8 most
@@ -457,7 +476,8 @@ typedef struct {
     int64_t last_branches;      /* branch count of the last batch */
     int64_t shifted_x, shifted_y, longer_x, longer_y, longer_z, z_variant;   /* counts over the context's plans */
     double tune_ms;             /* GPU time spent timing candidates */
-    int64_t reserved[4];
+    int64_t last_ragged;        /* 1: the last batch ran its Poisson parts ragged (one launch per pass and length) */
+    int64_t reserved[3];
 } lgf_tune_info;
 
 /* The tuner's counters and a summary of the choices of the context's plans.

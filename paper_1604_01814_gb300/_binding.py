@@ -21,6 +21,8 @@ LGF_F32, LGF_F64 = 0, 1
 LGF_OP_POISSON, LGF_OP_INTFACTOR, LGF_OP_POISSON_THEN_INTFACTOR, LGF_OP_KINV = 0, 1, 2, 3
 LGF_TUNE_OFF, LGF_TUNE_ON, LGF_TUNE_CACHED = 0, 1, 2
 LGF_FLAG_BULK_STAGING = 1
+LGF_FLAG_BATCH_RAGGED = 2
+LGF_FLAG_BATCH_PER_PROBLEM = 4
 
 # Every symbol include/lgf.h declares (checked by the symbol test).
 EXPORTS = ("lgf_ctx_create", "lgf_ctx_destroy", "lgf_table_build", "lgf_table_info", "lgf_table_lookup",
@@ -74,7 +76,8 @@ class lgf_tune_info(ctypes.Structure):
                 ("candidates_timed", ctypes.c_int64), ("batches_tuned", ctypes.c_int64),
                 ("last_branches", ctypes.c_int64), ("shifted_x", ctypes.c_int64), ("shifted_y", ctypes.c_int64),
                 ("longer_x", ctypes.c_int64), ("longer_y", ctypes.c_int64), ("longer_z", ctypes.c_int64),
-                ("z_variant", ctypes.c_int64), ("tune_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
+                ("z_variant", ctypes.c_int64), ("tune_ms", ctypes.c_double), ("last_ragged", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 3)]
 
 
 class LgfError(RuntimeError):

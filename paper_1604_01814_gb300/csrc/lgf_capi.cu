@@ -213,7 +213,9 @@ lgf_status lgf_ctx_create(lgf_ctx **out, const lgf_options *opt)
     if (o.stencil_radius < 0 || o.stencil_radius > 128 || o.device < 0) return LGF_EINVAL;
     for (int i = 0; i < 3; ++i)
         if (o.reserved[i] != 0) return LGF_EINVAL;
-    if ((o.flags & ~LGF_FLAG_BULK_STAGING) != 0) return LGF_EINVAL;
+    if ((o.flags & ~(LGF_FLAG_BULK_STAGING | LGF_FLAG_BATCH_RAGGED | LGF_FLAG_BATCH_PER_PROBLEM)) != 0 ||
+        ((o.flags & LGF_FLAG_BATCH_RAGGED) && (o.flags & LGF_FLAG_BATCH_PER_PROBLEM)))
+        return LGF_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device >= ndev) {
         cudaGetLastError();
@@ -224,6 +226,8 @@ lgf_status lgf_ctx_create(lgf_ctx **out, const lgf_options *opt)
     if (!ctx) return LGF_ENOMEM;
     ctx->opt = o;
     ctx->opt_bulk = (o.flags & LGF_FLAG_BULK_STAGING) != 0;
+    ctx->opt_rag = (o.flags & LGF_FLAG_BATCH_RAGGED) != 0;
+    ctx->opt_units = (o.flags & LGF_FLAG_BATCH_PER_PROBLEM) != 0;
     ctx->device = o.device;
     ctx->prec = o.prec;
     ctx->tol = o.tol > 0.0 ? o.tol : (o.prec == LGF_F64 ? 1e-13 : 1e-7);
@@ -817,9 +821,48 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     }
     const int nb_max = std::min<int>(kBranches, std::max<int>(1, (int)units.size()));
     int nb = ctx->prof ? 1 : std::min(nb_max, kDefaultBranches);
+    // Ragged mode: all Poisson parts together, one launch per pass and
+    // transform length (poisson_run_ragged), then every integrating-factor
+    // group, the groups spread over the branches.
+    std::vector<RagPart> parts;
+    for (int i = 0; i < nprob; ++i)
+        if (pois[i].plan)
+            parts.push_back(RagPart{pois[i].plan, pois[i].spec, probs[i].f_dev, probs[i].u_dev,
+                                    probs[i].ncomp * probs[i].nrhs, probs[i].dx});
+    // (the default for batches of several Poisson parts, or on request)
+    bool rag = !ctx->opt_units && ((ctx->opt_rag && !parts.empty()) || parts.size() >= 2);
+    if (rag && !ctx->prof) nb = std::min(kDefaultBranches, kBranches);
+    // integrating-factor groups of the ragged mode: those that read the
+    // batch's Poisson results (after the Poisson passes, scratch of branch 0)
+    // and those that read only batch inputs (alongside the Poisson passes on
+    // the last branch, with its scratch)
+    std::vector<IntfGroupRef> grefs_dep, grefs_ind;
+    for (auto &g : groups)
+        (g.after_poisson ? grefs_dep : grefs_ind)
+            .push_back(IntfGroupRef{g.plan, g.jobs.data(), (int)g.jobs.size(), g.nf});
+    Scratch *const scr_ind = &ctx->scr[kBranches - 1];
+    auto make_branches = [&](int nbv) -> lgf_status {
+        if (nbv > 1) {
+            if (!ctx->ev_fork) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+            for (int b = 0; b < nbv; ++b) {
+                if (!ctx->br[b]) LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->br[b], cudaStreamNonBlocking));
+                if (!ctx->ev_join[b])
+                    LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming));
+            }
+        }
+        return LGF_OK;
+    };
+    auto setup_rag = [&](int nbv) -> lgf_status {
+        lgf_status e2 = poisson_ragged_scratch(ctx, parts.data(), (int)parts.size());
+        if (e2 == LGF_OK) e2 = intf_ragged_scratch(ctx, grefs_dep.data(), (int)grefs_dep.size(), &ctx->scr[0]);
+        if (e2 == LGF_OK) e2 = intf_ragged_scratch(ctx, grefs_ind.data(), (int)grefs_ind.size(), scr_ind);
+        if (e2 != LGF_OK) return e2;
+        return make_branches(grefs_ind.empty() ? nbv : kBranches);
+    };
     // units onto nbv branches (longest first onto the least loaded), each
     // branch's scratch grown for its units, its stream and events made
     auto setup = [&](int nbv) -> lgf_status {
+        if (rag) return setup_rag(nbv);
         std::vector<int> order(units.size());
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
         std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return units[a].cost > units[c].cost; });
@@ -849,15 +892,7 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         for (int k : post)
             if ((e2 = intf_prepare_scratch(ctx, groups[k].plan, groups[k].nf, (int)groups[k].jobs.size())) != LGF_OK)
                 return e2;
-        if (nbv > 1) {
-            if (!ctx->ev_fork) LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-            for (int b = 0; b < nbv; ++b) {
-                if (!ctx->br[b]) LGF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->br[b], cudaStreamNonBlocking));
-                if (!ctx->ev_join[b])
-                    LGF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join[b], cudaEventDisableTiming));
-            }
-        }
-        return LGF_OK;
+        return make_branches(nbv);
     };
     if ((st = setup(nb)) != LGF_OK) return st;
     auto enqueue = [&]() -> lgf_status {
@@ -868,6 +903,23 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
             if (p.tgt.nblocks > 0 && p.src.nblocks == 0)
                 LGF_CUDA(ctx, cudaMemsetAsync(p.u_dev, 0,
                                               (size_t)p.tgt.nblocks * b3 * p.ncomp * p.nrhs * elem_size(ctx), s));
+        }
+        if (rag) {
+            const bool side = !grefs_ind.empty() && !parts.empty() && nb > 1;
+            cudaStream_t si = side ? ctx->br[kBranches - 1] : s;
+            if (side) {
+                LGF_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+                LGF_CUDA(ctx, cudaStreamWaitEvent(si, ctx->ev_fork, 0));
+            }
+            lgf_status e2 = intf_run_ragged(ctx, grefs_ind.data(), (int)grefs_ind.size(), si, scr_ind);
+            if (e2 == LGF_OK) e2 = poisson_run_ragged(ctx, parts.data(), (int)parts.size(), s, nb);
+            if (e2 == LGF_OK) e2 = intf_run_ragged(ctx, grefs_dep.data(), (int)grefs_dep.size(), s, &ctx->scr[0]);
+            if (e2 != LGF_OK) return e2;
+            if (side) {
+                LGF_CUDA(ctx, cudaEventRecord(ctx->ev_join[kBranches - 1], si));
+                LGF_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join[kBranches - 1], 0));
+            }
+            return LGF_OK;
         }
         if (nb > 1) {
             LGF_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
@@ -905,9 +957,12 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         }
         return LGF_OK;
     };
-    // 4. the branch count of this batch shape: the persisted choice, or (tuning
-    //    on, a new shape) the fastest of 1, 2, 4 and 8 branches timed with
-    //    direct launches on the caller's stream (4 first: the others must win by 3 %)
+    // 4. the execution of this batch shape: the persisted choice, or (tuning
+    //    on, a new shape) the fastest of 1, 2, 4 and 8 branches of per-problem
+    //    launches and of the ragged mode (on 4 branches), timed with direct
+    //    launches on the caller's stream (the default first: the others must
+    //    win by 3 %)
+    const int nb_rag = std::min(kDefaultBranches, kBranches);
     if (ctx->tune_mode != LGF_TUNE_OFF && !ctx->prof && s != nullptr && nb_max > 1) {
         const std::string tk = tune_batch_key(ctx->prec == LGF_F64, tune_hash(shape.data(), shape.size()));
         auto it = ctx->tune_db.find(tk);
@@ -915,14 +970,26 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         if (it != ctx->tune_db.end() && std::sscanf(it->second.c_str(), "nb%d", &pick) == 1 && pick >= 1 &&
             pick <= nb_max) {
             nb = pick;
+        } else if (it != ctx->tune_db.end() && std::sscanf(it->second.c_str(), "rg%d", &pick) == 1 && pick >= 1 &&
+                   pick <= kBranches) {
+            rag = true;
+            nb = pick;
         } else if (ctx->tune_mode == LGF_TUNE_ON) {
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             LGF_CUDA(ctx, cudaEventCreate(&e0));
             LGF_CUDA(ctx, cudaEventCreate(&e1));
             float tbest = 0.f;
             int best = nb;
-            for (int cand : {4, 8, 2, 1}) {
-                if (cand > nb_max) continue;
+            bool best_rag = false;
+            // the default first: the others must beat it by 3 %
+            static constexpr int kCand[4] = {4, 8, 2, 1};
+            const bool rag0 = rag;
+            for (int ci = 0; ci < 5; ++ci) {
+                const bool crag = rag0 ? ci == 0 : ci == 4;
+                const int cand = crag ? nb_rag : kCand[rag0 ? ci - 1 : ci];
+                if (!crag && cand > nb_max) continue;
+                if (crag && parts.empty()) continue;
+                rag = crag;
                 if ((st = setup(cand)) != LGF_OK) break;
                 nb = cand;
                 std::vector<float> t;
@@ -938,21 +1005,24 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
                 if (st != LGF_OK) break;
                 const float tm = std::min(t[0], t[1]);
                 ctx->tune_candidates++;
-                if (tbest == 0.f || tm < 0.97f * tbest) {   // fewer branches must win by 3 %
+                if (tbest == 0.f || tm < 0.97f * tbest) {   // later candidates must win by 3 %
                     tbest = tm;
                     best = cand;
+                    best_rag = crag;
                 }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             if (st != LGF_OK) return st;
             nb = best;
+            rag = best_rag;
             ++ctx->tune_batches;
-            tune_record(ctx, tk, "nb" + std::to_string(nb));
+            tune_record(ctx, tk, (rag ? "rg" : "nb") + std::to_string(nb));
         }
         if ((st = setup(nb)) != LGF_OK) return st;
     }
     ctx->tune_last_branches = nb;
+    ctx->tune_last_ragged = rag ? 1 : 0;
     // 5. the legacy default stream cannot be captured, and per-kernel timing
     //    needs direct launches: run without a graph
     //    (and so does a context whose graph cache is switched off)
@@ -1108,6 +1178,7 @@ lgf_status lgf_tune_report(lgf_ctx *ctx, lgf_tune_info *out)
     out->candidates_timed = ctx->tune_candidates;
     out->batches_tuned = ctx->tune_batches;
     out->last_branches = ctx->tune_last_branches;
+    out->last_ragged = ctx->tune_last_ragged;
     out->tune_ms = ctx->tune_ms;
     for (auto &p : ctx->pplans.items()) {
         out->shifted_x += p->choice.shift[0];

@@ -210,6 +210,8 @@ struct lgf_ctx {
     double *red_dev = nullptr;   // small reduction buffer (residual, table mismatch)
     int *err_dev = nullptr;      // device error word: bits set by bounded waits that ran out
     bool opt_bulk = false;       // stage the E z pass with bulk asynchronous copies (LGF_FLAG_BULK_STAGING)
+    bool opt_rag = false;        // batches in the ragged mode unless tuned otherwise (LGF_FLAG_BATCH_RAGGED)
+    bool opt_units = false;      // batches in per-problem launches unless tuned otherwise (LGF_FLAG_BATCH_PER_PROBLEM)
 
     // autotuner: mode (LGF_TUNE_*), persisted choices (key -> value lines of
     // lgf_tune.h, loaded from and appended to tune_path), counters, the
@@ -221,6 +223,7 @@ struct lgf_ctx {
     int64_t tune_plans = 0, tune_plans_cached = 0, tune_candidates = 0, tune_batches = 0;
     double tune_ms = 0.0;
     int tune_last_branches = 0;
+    int tune_last_ragged = 0;
     void *tune_f = nullptr, *tune_u = nullptr;
     size_t tune_fb = 0, tune_ub = 0;
 
@@ -298,6 +301,20 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, S
 lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const void *f, void *u, int nfields,
                        double dx, cudaStream_t s);
 lgf_status poisson_prepare_scratch(lgf_ctx *ctx, const PoissonPlan *pl, int nfields);
+// Many Poisson parts at once (lgf_batch_apply): one launch per pass and
+// transform length, the length groups of a pass spread over `nbr` branch
+// streams of the context (nbr <= 1: all on s).  Every part's A and B are
+// slices of the scratch of branch 0, which poisson_ragged_scratch sizes.
+struct RagPart {
+    const PoissonPlan *plan;
+    const Spectrum *sp;
+    const void *f;
+    void *u;
+    int nf;
+    double dx;
+};
+lgf_status poisson_ragged_scratch(lgf_ctx *ctx, const RagPart *parts, int n);
+lgf_status poisson_run_ragged(lgf_ctx *ctx, const RagPart *parts, int n, cudaStream_t s, int nbr);
 
 // Integrating factor (lgf_intfactor.cu)
 lgf_status intf_weights(lgf_ctx *ctx, double alpha, IntfWeights **out, cudaStream_t s);
@@ -311,6 +328,20 @@ struct IntfJob {
 lgf_status intf_run_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, int njobs, int nfields, cudaStream_t s);
 lgf_status intf_run(lgf_ctx *ctx, IntfPlan *pl, const IntfWeights *w, const void *f, void *u, int nfields,
                     cudaStream_t s);
+// Integrating-factor groups of several plans at once (lgf_batch_apply's
+// ragged mode): the fused x+y pass of all their jobs in one launch per block
+// edge and window bound, then the z pass likewise, each job's intermediate a
+// slice of scratch D of `sc` (intf_ragged_scratch sizes it); groups the
+// window kernels do not cover run one after another as intf_run_jobs (with
+// the scratch of `sc`).
+struct IntfGroupRef {
+    IntfPlan *plan;
+    const IntfJob *jobs;
+    int njobs;
+    int nf;
+};
+lgf_status intf_ragged_scratch(lgf_ctx *ctx, const IntfGroupRef *gs, int n, Scratch *sc);
+lgf_status intf_run_ragged(lgf_ctx *ctx, const IntfGroupRef *gs, int n, cudaStream_t s, Scratch *sc);
 
 // Curl and velocity refresh (lgf_curl.cu)
 lgf_status curl_plan(lgf_ctx *ctx, const lgf_blockset *src, const lgf_blockset *tgt, int dir, CurlPlan **out);

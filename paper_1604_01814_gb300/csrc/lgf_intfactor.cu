@@ -34,6 +34,8 @@ extern template lgf_status launch_sep_xy<float>(lgf_ctx *, int, int, const SepJo
                                                 const int *, int, bool *);
 extern template lgf_status launch_sep_xy<double>(lgf_ctx *, int, int, const SepJobs<double> &, cudaStream_t,
                                                  const int *, const int *, int, bool *);
+extern template lgf_status launch_sep_rag<float>(lgf_ctx *, bool, int, int, SepRagJob<float> *, int, cudaStream_t);
+extern template lgf_status launch_sep_rag<double>(lgf_ctx *, bool, int, int, SepRagJob<double> *, int, cudaStream_t);
 
 IntfPlan::~IntfPlan()
 {
@@ -554,6 +556,129 @@ lgf_status intf_run_jobs(lgf_ctx *ctx, IntfPlan *pl, const IntfJob *jobs, int nj
     }
     if (ctx->prec == LGF_F64) return run_sep_jobs<double>(ctx, pl, jobs, njobs, nfields, s);
     return run_sep_jobs<float>(ctx, pl, jobs, njobs, nfields, s);
+}
+
+namespace {
+
+// Window bound of a job on a plan, 0 where the window kernels do not cover it.
+int rag_rmax(const IntfPlan *pl, const IntfJob &j)
+{
+    const int c = window_class(j.w->R);
+    if (c == 0 || c > pl->nr * pl->b || (pl->b != 8 && pl->b != 16 && pl->b != 32)) return 0;
+    return c;
+}
+
+// Groups of the ragged launches: every job of a group has a window bound and
+// the plan a z pass with sources.
+bool rag_group(const IntfGroupRef &g)
+{
+    if (g.plan->n2 == 0 || g.plan->pass[2].nout == 0) return false;
+    for (int j = 0; j < g.njobs; ++j)
+        if (rag_rmax(g.plan, g.jobs[j]) == 0) return false;
+    return true;
+}
+
+template <typename T>
+lgf_status run_ragged_t(lgf_ctx *ctx, const IntfGroupRef *gs, int n, cudaStream_t s)
+{
+    const size_t esz = sizeof(T);
+    T *Y2all = (T *)ctx->cur->D;
+    int64_t y2off = 0;
+    // (block edge, window bound) -> the jobs of the x+y pass and of the z pass
+    std::vector<std::array<int, 2>> keys;
+    std::vector<std::vector<SepRagJob<T>>> xy, zz;
+    for (int gi = 0; gi < n; ++gi) {
+        const IntfGroupRef &g = gs[gi];
+        if (!rag_group(g)) continue;
+        const IntfPlan *pl = g.plan;
+        const int64_t b3 = (int64_t)pl->b * pl->b * pl->b;
+        const int64_t y2f = (int64_t)pl->n2 * b3;
+        const int nsrc = (int)(pl->src.size() / 3), ntgt = (int)(pl->tgt.size() / 3);
+        for (int j = 0; j < g.njobs; ++j) {
+            const IntfJob &J = g.jobs[j];
+            if ((reinterpret_cast<uintptr_t>(J.f) | reinterpret_cast<uintptr_t>(J.u)) % 16 != 0)
+                return fail(ctx, LGF_EINVAL, "integrating factor: f and u must be 16-byte aligned");
+            const T *w = sizeof(T) == 8 ? (const T *)(const void *)J.w->w64 : (const T *)(const void *)J.w->w32;
+            T *y2 = Y2all + y2off;
+            y2off += y2f * g.nf;
+            const std::array<int, 2> key{pl->b, rag_rmax(pl, J)};
+            size_t k = 0;
+            while (k < keys.size() && keys[k] != key) ++k;
+            if (k == keys.size()) {
+                keys.push_back(key);
+                xy.emplace_back();
+                zz.emplace_back();
+            }
+            SepRagJob<T> a{};
+            a.job = SepJob<T>{(const T *)J.f, y2, w, J.w->R, 0, nsrc * b3, y2f};
+            a.nbr = pl->nbr_xy_dev;
+            a.items = pl->xy_items_dev;
+            a.nr = pl->nr;
+            a.nitems = pl->n_xy_items;
+            a.nf = g.nf;
+            xy[k].push_back(a);
+            SepRagJob<T> z{};
+            z.job = SepJob<T>{y2, (T *)J.u, w, J.w->R, 0, y2f, ntgt * b3};
+            z.nbr = pl->pass[2].nbr_dev;
+            z.items = nullptr;
+            z.nr = pl->nr;
+            z.nitems = ntgt;
+            z.nf = g.nf;
+            zz[k].push_back(z);
+        }
+    }
+    if ((size_t)y2off * esz > ctx->cur->d) return fail(ctx, LGF_EINVAL, "ragged integrating factor: scratch not prepared");
+    for (size_t k = 0; k < keys.size(); ++k) {
+        const int ph = prof_begin(ctx, s, "intfactor_pass_xy");
+        lgf_status st = launch_sep_rag<T>(ctx, true, keys[k][0], keys[k][1], xy[k].data(), (int)xy[k].size(), s);
+        if (st != LGF_OK) return st;
+        LGF_CHECK_LAUNCH(ctx, "intfactor xy pass");
+        prof_end(ctx, s, ph);
+        const int pz = prof_begin(ctx, s, "intfactor_pass_z");
+        if ((st = launch_sep_rag<T>(ctx, false, keys[k][0], keys[k][1], zz[k].data(), (int)zz[k].size(), s)) !=
+            LGF_OK)
+            return st;
+        LGF_CHECK_LAUNCH(ctx, "intfactor z pass");
+        prof_end(ctx, s, pz);
+    }
+    // the rest, group by group
+    for (int gi = 0; gi < n; ++gi)
+        if (!rag_group(gs[gi])) {
+            lgf_status st = intf_run_jobs(ctx, gs[gi].plan, gs[gi].jobs, gs[gi].njobs, gs[gi].nf, s);
+            if (st != LGF_OK) return st;
+        }
+    return LGF_OK;
+}
+
+}  // namespace
+
+lgf_status intf_ragged_scratch(lgf_ctx *ctx, const IntfGroupRef *gs, int n, Scratch *sc)
+{
+    const size_t esz = ctx->prec == LGF_F64 ? 8 : 4;
+    size_t d = 0;
+    Scratch *keep = ctx->cur;
+    ctx->cur = sc;
+    lgf_status st = LGF_OK;
+    for (int gi = 0; gi < n && st == LGF_OK; ++gi) {
+        const IntfPlan *pl = gs[gi].plan;
+        if (rag_group(gs[gi]))
+            d += (size_t)pl->n2 * pl->b * pl->b * pl->b * gs[gi].nf * esz * gs[gi].njobs;
+        else
+            st = intf_prepare_scratch(ctx, pl, gs[gi].nf, gs[gi].njobs);
+    }
+    if (st == LGF_OK) st = ensure_scratch(ctx, &sc->D, &sc->d, std::max<size_t>(d, 1));
+    ctx->cur = keep;
+    return st;
+}
+
+lgf_status intf_run_ragged(lgf_ctx *ctx, const IntfGroupRef *gs, int n, cudaStream_t s, Scratch *sc)
+{
+    Scratch *keep = ctx->cur;
+    ctx->cur = sc;
+    const lgf_status st =
+        ctx->prec == LGF_F64 ? run_ragged_t<double>(ctx, gs, n, s) : run_ragged_t<float>(ctx, gs, n, s);
+    ctx->cur = keep;
+    return st;
 }
 
 lgf_status intf_run(lgf_ctx *ctx, IntfPlan *pl, const IntfWeights *w, const void *f, void *u, int nfields,

@@ -136,6 +136,53 @@ struct SepJobs {
     int nf;   // fields per job (grid.z = n * nf)
 };
 
+// Ragged launches (lgf_batch_apply's ragged mode): jobs of different plans
+// (block sets) in one launch.  Job i carries its plan's tables and owns the
+// CTAs [cta0_i, cta0_i + nitems_i * nf_i) along x (field-major); every CTA
+// finds its job by a binary search over cta0.
+constexpr int kSepRagJobs = 64;
+template <typename T>
+struct SepRagJob {
+    SepJob<T> job;
+    const int *nbr;     // the pass's neighbour table of the job's plan
+    const int *items;   // fused x+y pass: the plan's output items
+    int nr, nitems, nf, cta0;
+};
+template <typename T>
+struct SepRag {
+    SepRagJob<T> j[kSepRagJobs];
+    int n;
+};
+
+// Where a CTA's work lies: its job, field and output item, and the plan
+// tables to use.
+template <typename T>
+struct SepAt {
+    const SepJob<T> *J;
+    int field, item;
+    const int *nbr, *items;
+    int nr;
+};
+template <typename T>
+__device__ __forceinline__ SepAt<T> sep_at(const SepJobs<T> &t, const int *nbr, const int *items, int nr)
+{
+    return {&t.j[blockIdx.z / t.nf], (int)blockIdx.z % t.nf, (int)blockIdx.x, nbr, items, nr};
+}
+template <typename T>
+__device__ __forceinline__ SepAt<T> sep_at(const SepRag<T> &t, const int *, const int *, int)
+{
+    int lo = 0, hi = t.n - 1;
+    const int c = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.j[mid].cta0 <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    const SepRagJob<T> &r = t.j[lo];
+    const int k = c - r.cta0;
+    return {&r.job, k / r.nitems, k % r.nitems, r.nbr, r.items, r.nr};
+}
+
 namespace win {
 
 // Threads per CTA and slab extent for block edge b = 2^LB.
@@ -150,12 +197,15 @@ struct Cfg {
     static constexpr int THREADS = NS * per_plane;
 };
 
-template <typename T, int LB, int AX, int RMAX>
+template <typename T, int LB, int AX, int RMAX, class Tab = SepJobs<T>>
 __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
-    k_sep_win(const SepJobs<T> jobs, const int *__restrict__ nbr, int nr)
+    k_sep_win(const __grid_constant__ Tab jobs, const int *__restrict__ nbr_arg, int nr_arg)
 {
-    const SepJob<T> &J = jobs.j[blockIdx.z / jobs.nf];
-    const int field = blockIdx.z % jobs.nf;
+    const SepAt<T> at = sep_at(jobs, nbr_arg, nullptr, nr_arg);
+    const SepJob<T> &J = *at.J;
+    const int field = at.field;
+    const int *__restrict__ nbr = at.nbr;
+    const int nr = at.nr;
     const T *__restrict__ wg = J.w;
     const int R = J.R;
     using C = Cfg<T, LB, AX>;
@@ -163,7 +213,7 @@ __global__ void __launch_bounds__(Cfg<T, LB, AX>::THREADS)
     constexpr int b = C::b, bm = b - 1, NV = C::NV, NS = C::NS, HL = RMAX, E = b + 2 * HL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
-    const int o = blockIdx.x;
+    const int o = at.item;
     const int s0 = blockIdx.y * NS;
     const int nd = 2 * nr + 1;
     const int *nb = nbr + (int64_t)o * nd;
@@ -401,12 +451,16 @@ struct XYCfg {
 
 // items: [n][2] output blocks (second -1 for a single block); nbr: for every
 // output block its (2nr+1)^2 xy neighbourhood of source blocks.
-template <typename T, int LB, int RMAX>
-__global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int *__restrict__ nbr,
-                                                const int *__restrict__ items, int nr)
+template <typename T, int LB, int RMAX, class Tab = SepJobs<T>>
+__global__ void __launch_bounds__(256) k_sep_xy(const __grid_constant__ Tab jobs, const int *__restrict__ nbr_arg,
+                                                const int *__restrict__ items_arg, int nr_arg)
 {
-    const SepJob<T> &J = jobs.j[blockIdx.z / jobs.nf];
-    const int field = blockIdx.z % jobs.nf;
+    const SepAt<T> at = sep_at(jobs, nbr_arg, items_arg, nr_arg);
+    const SepJob<T> &J = *at.J;
+    const int field = at.field;
+    const int *__restrict__ nbr = at.nbr;
+    const int *__restrict__ items = at.items;
+    const int nr = at.nr;
     const T *__restrict__ wg = J.w;
     const int R = J.R;
     using C = XYCfg<T, LB, RMAX>;
@@ -416,7 +470,7 @@ __global__ void __launch_bounds__(256) k_sep_xy(const SepJobs<T> jobs, const int
     T *rg = reinterpret_cast<T *>(smem_raw);       // [NS][EY][E] (FP32: [NS][EY/2][P2])
     T *im = rg + NS * C::RG;                        // [NS][EY][IP] (row pitch IP >= b)
     constexpr int IP = C::IP;
-    const int o1 = items[2 * blockIdx.x], o2 = items[2 * blockIdx.x + 1];
+    const int o1 = items[2 * at.item], o2 = items[2 * at.item + 1];
     const bool pair = o2 >= 0;                      // uniform over the CTA
     const int ny = pair ? 2 : 1;
     const int rows = pair ? C::EY : C::EY1;         // staged rows per plane
@@ -634,6 +688,61 @@ lgf_status launch_m(lgf_ctx *ctx, int nout, const SepJobs<T> &jobs, cudaStream_t
     return LGF_OK;
 }
 
+// Ragged launches: every job field but cta0 set; sent in tables of
+// kSepRagJobs, each table by launch(grid.x, table).
+template <typename T, class Launch>
+lgf_status rag_send_sep(lgf_ctx *ctx, SepRagJob<T> *jobs, int n, Launch launch)
+{
+    static_assert(sizeof(SepRag<T>) <= 32000, "job table beyond the kernel parameter space");
+    for (int c0 = 0; c0 < n;) {
+        SepRag<T> t;
+        t.n = 0;
+        int64_t ctas = 0;
+        for (; c0 < n && t.n < kSepRagJobs; ++c0) {
+            SepRagJob<T> &j = jobs[c0];
+            const int64_t nc = (int64_t)j.nitems * j.nf;
+            if (nc <= 0) continue;
+            j.cta0 = (int)ctas;
+            t.j[t.n++] = j;
+            ctas += nc;
+        }
+        if (t.n == 0) continue;
+        if (ctas > 0x7fffffff) return fail(ctx, LGF_EUNSUPPORTED, "ragged integrating factor: too many CTAs");
+        launch((unsigned)ctas, t);
+    }
+    return LGF_OK;
+}
+
+template <typename T, int LB, int RMAX>
+lgf_status launch_xy_rag_m(lgf_ctx *ctx, SepRagJob<T> *jobs, int n, cudaStream_t s)
+{
+    using C = XYCfg<T, LB, RMAX>;
+    auto kern = k_sep_xy<T, LB, RMAX, SepRag<T>>;
+    if (C::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    }
+    return rag_send_sep<T>(ctx, jobs, n, [&](unsigned gx, const SepRag<T> &t) {
+        kern<<<dim3(gx, C::b / C::NSB, 1), 256, C::SMEM, s>>>(t, nullptr, nullptr, 0);
+    });
+}
+
+template <typename T, int LB, int RMAX>
+lgf_status launch_z_rag_m(lgf_ctx *ctx, SepRagJob<T> *jobs, int n, cudaStream_t s)
+{
+    using C = Cfg<T, LB, 2>;
+    constexpr int b = 1 << LB, E = b + 2 * RMAX;
+    constexpr size_t smem = sizeof(T) * (size_t)C::NS * b * E;
+    auto kern = k_sep_win<T, LB, 2, RMAX, SepRag<T>>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    }
+    return rag_send_sep<T>(ctx, jobs, n, [&](unsigned gx, const SepRag<T> &t) {
+        kern<<<dim3(gx, b / C::NS, 1), C::THREADS, smem, s>>>(t, nullptr, 0);
+    });
+}
+
 template <typename T, int LB, int AX>
 lgf_status launch_r(lgf_ctx *ctx, int rmax, int nout, const SepJobs<T> &jobs, cudaStream_t s, const int *nbr, int nr)
 {
@@ -703,6 +812,27 @@ lgf_status launch_sep_window(lgf_ctx *ctx, int ax, int b, int nout, const SepJob
         LGF_WIN_AX(2)
     }
 #undef LGF_WIN_AX
+}
+
+// Ragged fused x+y pass (xy = true) or z pass over jobs of several plans
+// that share the block edge b and the window bound rmax (4, 8, 12, 16, at
+// most nr * b of every job's plan).
+template <typename T>
+lgf_status launch_sep_rag(lgf_ctx *ctx, bool xy, int b, int rmax, SepRagJob<T> *jobs, int n, cudaStream_t s)
+{
+#define LGF_RAG_R(LBV)                                                                                   \
+    switch (rmax) {                                                                                      \
+    case 4: return xy ? win::launch_xy_rag_m<T, LBV, 4>(ctx, jobs, n, s) : win::launch_z_rag_m<T, LBV, 4>(ctx, jobs, n, s);     \
+    case 8: return xy ? win::launch_xy_rag_m<T, LBV, 8>(ctx, jobs, n, s) : win::launch_z_rag_m<T, LBV, 8>(ctx, jobs, n, s);     \
+    case 12: return xy ? win::launch_xy_rag_m<T, LBV, 12>(ctx, jobs, n, s) : win::launch_z_rag_m<T, LBV, 12>(ctx, jobs, n, s);  \
+    default: return xy ? win::launch_xy_rag_m<T, LBV, 16>(ctx, jobs, n, s) : win::launch_z_rag_m<T, LBV, 16>(ctx, jobs, n, s);  \
+    }
+    switch (b) {
+    case 8: LGF_RAG_R(3)
+    case 16: LGF_RAG_R(4)
+    default: LGF_RAG_R(5)
+    }
+#undef LGF_RAG_R
 }
 
 }  // namespace lgf

@@ -46,7 +46,19 @@ namespace lgf {
     extern template lgf_status launch_col_convolve<T, 1>(lgf_ctx *, const PoissonGeom &, Cx<T> *, const T *,   \
                                                          const Cx<T> *, int, cudaStream_t);                      \
     extern template lgf_status launch_col_convolve<T, 2>(lgf_ctx *, const PoissonGeom &, Cx<T> *, const T *,   \
-                                                         const Cx<T> *, int, cudaStream_t);
+                                                         const Cx<T> *, int, cudaStream_t);                      \
+    extern template lgf_status launch_row_forward_rag<T>(lgf_ctx *, int, pk::RowJob<T> *, int, cudaStream_t);    \
+    extern template lgf_status launch_row_inverse_rag<T>(lgf_ctx *, int, bool, pk::RowJob<T> *, int,             \
+                                                         cudaStream_t);                                          \
+    extern template lgf_status launch_col_forward_rag<T>(lgf_ctx *, int, pk::ColJob<T> *, int, cudaStream_t);    \
+    extern template lgf_status launch_col_inverse_rag<T>(lgf_ctx *, int, bool, pk::ColJob<T> *, int,             \
+                                                         cudaStream_t);                                          \
+    extern template lgf_status launch_col_convolve_rag<T, 0>(lgf_ctx *, int, int, pk::ConvJob<T> *, int,         \
+                                                             cudaStream_t);                                      \
+    extern template lgf_status launch_col_convolve_rag<T, 1>(lgf_ctx *, int, int, pk::ConvJob<T> *, int,         \
+                                                             cudaStream_t);                                      \
+    extern template lgf_status launch_col_convolve_rag<T, 2>(lgf_ctx *, int, int, pk::ConvJob<T> *, int,         \
+                                                             cudaStream_t);
 LGF_EXTERN_PASSES(float)
 LGF_EXTERN_PASSES(double)
 #undef LGF_EXTERN_PASSES
@@ -485,6 +497,212 @@ lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const 
                                   (Cx<double> *)ctx->cur->B, (const double *)sp->dev, nfields, 0, false, s);
     return run_passes<float>(ctx, g, (const float *)f, (float *)u, (Cx<float> *)ctx->cur->A, (Cx<float> *)ctx->cur->B,
                              (const float *)sp->dev, nfields, 0, false, s);
+}
+
+namespace {
+
+// Scratch slices of the ragged run: part i's A at a[i], B at b[i] (complex
+// elements), each rounded up to 32 elements (256-byte aligned for FP32).
+void ragged_offsets(const RagPart *parts, int n, std::vector<int64_t> *a, std::vector<int64_t> *b, int64_t *atot,
+                    int64_t *btot)
+{
+    a->assign(n, 0);
+    b->assign(n, 0);
+    int64_t ta = 0, tb = 0;
+    for (int i = 0; i < n; ++i) {
+        (*a)[i] = ta;
+        (*b)[i] = tb;
+        ta += (parts[i].plan->A_elems * parts[i].nf + 31) / 32 * 32;
+        tb += (parts[i].plan->B_elems * parts[i].nf + 31) / 32 * 32;
+    }
+    *atot = ta;
+    *btot = tb;
+}
+
+// Launches of one pass: the groups (one transform length and variant each)
+// go round-robin to the branch streams, which fork from s and join it again.
+template <class Launch>
+lgf_status ragged_pass(lgf_ctx *ctx, cudaStream_t s, int nbr, int ngroups, Launch launch)
+{
+    const int nb = std::min(nbr, ngroups);
+    if (nb <= 1) {
+        for (int k = 0; k < ngroups; ++k) {
+            lgf_status st = launch(k, s);
+            if (st != LGF_OK) return st;
+        }
+        return LGF_OK;
+    }
+    LGF_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+    for (int b = 0; b < nb; ++b) LGF_CUDA(ctx, cudaStreamWaitEvent(ctx->br[b], ctx->ev_fork, 0));
+    for (int k = 0; k < ngroups; ++k) {
+        lgf_status st = launch(k, ctx->br[k % nb]);
+        if (st != LGF_OK) return st;
+    }
+    for (int b = 0; b < nb; ++b) {
+        LGF_CUDA(ctx, cudaEventRecord(ctx->ev_join[b], ctx->br[b]));
+        LGF_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join[b], 0));
+    }
+    return LGF_OK;
+}
+
+// Jobs grouped by a key (the transform length and the compile-time variant),
+// groups in order of first appearance.
+template <class Job>
+struct JobGroups {
+    std::vector<std::array<int, 3>> keys;
+    std::vector<std::vector<Job>> jobs;
+    void add(const std::array<int, 3> &k, const Job &j)
+    {
+        for (size_t i = 0; i < keys.size(); ++i)
+            if (keys[i] == k) {
+                jobs[i].push_back(j);
+                return;
+            }
+        keys.push_back(k);
+        jobs.push_back({j});
+    }
+};
+
+template <typename T>
+lgf_status run_ragged(lgf_ctx *ctx, const RagPart *parts, int n, cudaStream_t s, int nbr)
+{
+    const bool dbl = sizeof(T) == 8;
+    std::vector<int64_t> ao, bo;
+    int64_t at = 0, bt = 0;
+    ragged_offsets(parts, n, &ao, &bo, &at, &bt);
+    const size_t csz = sizeof(Cx<T>);
+    if ((size_t)at * csz > ctx->scr[0].a || (size_t)bt * csz > ctx->scr[0].b)
+        return fail(ctx, LGF_EINVAL, "ragged Poisson run: scratch not prepared");
+    Cx<T> *A0 = (Cx<T> *)ctx->scr[0].A, *B0 = (Cx<T> *)ctx->scr[0].B;
+    JobGroups<pk::RowJob<T>> xf, xi;
+    JobGroups<pk::ColJob<T>> yf, yi;
+    JobGroups<pk::ConvJob<T>> zc;
+    lgf_status st = LGF_OK;
+    for (int i = 0; i < n; ++i) {
+        const RagPart &q = parts[i];
+        PoissonGeom g = q.plan->g;
+        g.Astride = q.plan->A_elems;
+        g.Bstride = q.plan->B_elems;
+        g.scale = q.dx * q.dx;
+        const Cx<T> *tw[3];
+        for (int d = 0; d < 3; ++d) {
+            tw[d] = (const Cx<T> *)twiddles(ctx, g.M[d], dbl, &st);
+            if (st != LGF_OK) return st;
+        }
+        const int lb = log2i(g.b);
+        const int K = g.Kx, My = g.M[1];
+        const int64_t planeA = (int64_t)g.ldA_y * K, planeB = (int64_t)My * K;
+        Cx<T> *A = A0 + ao[i], *B = B0 + bo[i];
+        pk::RowJob<T> r{};
+        r.g = g;
+        r.in = q.f;
+        r.out = A;
+        r.tw = tw[0];
+        r.npairs = (g.Ls[1] / 2) * g.Ls[2];
+        r.lb = lb;
+        r.nf = q.nf;
+        xf.add({g.M[0], 0, 0}, r);
+        pk::ColJob<T> c{};
+        c.in = A;
+        c.out = B;
+        c.tw = tw[1];
+        c.rf = pk::RowFlags{g.srcrow, lb};
+        c.rs = c.os = K;
+        c.in_plane = planeA;
+        c.out_plane = planeB;
+        c.in_field = g.Astride;
+        c.out_field = g.Bstride;
+        c.K = K;
+        c.nplanes = g.Ls[2];
+        c.lo = g.s0[1];
+        c.n = g.Ls[1];
+        c.nf = q.nf;
+        yf.add({My, 0, 0}, c);
+        pk::ConvJob<T> z{};
+        z.B = B;
+        z.spec = q.sp->dev;
+        z.tw = tw[2];
+        z.field = g.Bstride;
+        z.K = K;
+        z.My = My;
+        z.s0 = g.s0[2];
+        z.ns = g.Ls[2];
+        z.t0 = g.t0[2];
+        z.nt = g.Lt[2];
+        z.nf = q.nf;
+        const int spec = g.yasym ? 2 : g.xasym ? 1 : 0;
+        zc.add({g.M[2], spec, sizeof(T) == 4 ? g.zvar : 0}, z);
+        pk::ColJob<T> c2{};
+        c2.in = B;
+        c2.out = A;
+        c2.tw = tw[1];
+        c2.rs = c2.os = K;
+        c2.in_plane = planeB;
+        c2.out_plane = planeA;
+        c2.in_field = g.Bstride;
+        c2.out_field = g.Astride;
+        c2.K = K;
+        c2.nplanes = g.Lt[2];
+        c2.lo = g.t0[1];
+        c2.n = g.Lt[1];
+        c2.nf = q.nf;
+        yi.add({My, g.t0[1] + g.Lt[1] <= My / 2 ? 1 : 0, 0}, c2);
+        pk::RowJob<T> r2{};
+        r2.g = g;
+        r2.in = A;
+        r2.out = q.u;
+        r2.tw = tw[0];
+        r2.npairs = (g.Lt[1] / 2) * g.Lt[2];
+        r2.lb = lb;
+        r2.nf = q.nf;
+        xi.add({g.M[0], 2 * (g.t0[0] + g.Lt[0]) <= g.M[0] ? 1 : 0, 0}, r2);
+    }
+    if ((st = ragged_pass(ctx, s, nbr, (int)xf.keys.size(), [&](int k, cudaStream_t bs) {
+             return launch_row_forward_rag<T>(ctx, xf.keys[k][0], xf.jobs[k].data(), (int)xf.jobs[k].size(), bs);
+         })) != LGF_OK)
+        return st;
+    if ((st = ragged_pass(ctx, s, nbr, (int)yf.keys.size(), [&](int k, cudaStream_t bs) {
+             return launch_col_forward_rag<T>(ctx, yf.keys[k][0], yf.jobs[k].data(), (int)yf.jobs[k].size(), bs);
+         })) != LGF_OK)
+        return st;
+    if ((st = ragged_pass(ctx, s, nbr, (int)zc.keys.size(), [&](int k, cudaStream_t bs) {
+             const auto &key = zc.keys[k];
+             pk::ConvJob<T> *j = zc.jobs[k].data();
+             const int nj = (int)zc.jobs[k].size();
+             return key[1] == 2   ? launch_col_convolve_rag<T, 2>(ctx, key[0], key[2], j, nj, bs)
+                    : key[1] == 1 ? launch_col_convolve_rag<T, 1>(ctx, key[0], key[2], j, nj, bs)
+                                  : launch_col_convolve_rag<T, 0>(ctx, key[0], key[2], j, nj, bs);
+         })) != LGF_OK)
+        return st;
+    if ((st = ragged_pass(ctx, s, nbr, (int)yi.keys.size(), [&](int k, cudaStream_t bs) {
+             return launch_col_inverse_rag<T>(ctx, yi.keys[k][0], yi.keys[k][1] != 0, yi.jobs[k].data(),
+                                              (int)yi.jobs[k].size(), bs);
+         })) != LGF_OK)
+        return st;
+    return ragged_pass(ctx, s, nbr, (int)xi.keys.size(), [&](int k, cudaStream_t bs) {
+        return launch_row_inverse_rag<T>(ctx, xi.keys[k][0], xi.keys[k][1] != 0, xi.jobs[k].data(),
+                                         (int)xi.jobs[k].size(), bs);
+    });
+}
+
+}  // namespace
+
+lgf_status poisson_ragged_scratch(lgf_ctx *ctx, const RagPart *parts, int n)
+{
+    std::vector<int64_t> ao, bo;
+    int64_t at = 0, bt = 0;
+    ragged_offsets(parts, n, &ao, &bo, &at, &bt);
+    const size_t csz = ctx->prec == LGF_F64 ? 16 : 8;
+    lgf_status st = ensure_scratch(ctx, &ctx->scr[0].A, &ctx->scr[0].a, (size_t)at * csz);
+    if (st != LGF_OK) return st;
+    return ensure_scratch(ctx, &ctx->scr[0].B, &ctx->scr[0].b, (size_t)bt * csz);
+}
+
+lgf_status poisson_run_ragged(lgf_ctx *ctx, const RagPart *parts, int n, cudaStream_t s, int nbr)
+{
+    if (n == 0) return LGF_OK;
+    if (ctx->prec == LGF_F64) return run_ragged<double>(ctx, parts, n, s, nbr);
+    return run_ragged<float>(ctx, parts, n, s, nbr);
 }
 
 lgf_status poisson_time_choice(lgf_ctx *ctx, PoissonPlan *pl, const PoissonChoice &ch, int nf, double kalpha,

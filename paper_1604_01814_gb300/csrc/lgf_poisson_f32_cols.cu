@@ -9,4 +9,6 @@ template lgf_status launch_col_forward<float>(lgf_ctx *, int, int, int, int, con
 template lgf_status launch_col_inverse<float>(lgf_ctx *, int, int, int, int, const Cx<float> *, Cx<float> *, int, int,
                                            int64_t, int64_t, int64_t, int64_t, int64_t, int64_t, const Cx<float> *,
                                            cudaStream_t, const char *);
+template lgf_status launch_col_forward_rag<float>(lgf_ctx *, int, pk::ColJob<float> *, int, cudaStream_t);
+template lgf_status launch_col_inverse_rag<float>(lgf_ctx *, int, bool, pk::ColJob<float> *, int, cudaStream_t);
 }  // namespace lgf

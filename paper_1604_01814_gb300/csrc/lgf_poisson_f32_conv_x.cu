@@ -6,4 +6,5 @@
 namespace lgf {
 template lgf_status launch_col_convolve<float, 1>(lgf_ctx *, const PoissonGeom &, Cx<float> *, const float *,
                                               const Cx<float> *, int, cudaStream_t);
+template lgf_status launch_col_convolve_rag<float, 1>(lgf_ctx *, int, int, pk::ConvJob<float> *, int, cudaStream_t);
 }  // namespace lgf

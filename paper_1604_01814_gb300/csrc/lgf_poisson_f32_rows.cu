@@ -7,4 +7,6 @@ template lgf_status launch_row_forward<float>(lgf_ctx *, const PoissonGeom &, co
                                            int, int, int, cudaStream_t);
 template lgf_status launch_row_inverse<float>(lgf_ctx *, const PoissonGeom &, const Cx<float> *, float *, const Cx<float> *,
                                            int, int, cudaStream_t);
+template lgf_status launch_row_forward_rag<float>(lgf_ctx *, int, pk::RowJob<float> *, int, cudaStream_t);
+template lgf_status launch_row_inverse_rag<float>(lgf_ctx *, int, bool, pk::RowJob<float> *, int, cudaStream_t);
 }  // namespace lgf

@@ -6,4 +6,5 @@
 namespace lgf {
 template lgf_status launch_col_convolve<double, 0>(lgf_ctx *, const PoissonGeom &, Cx<double> *, const double *,
                                               const Cx<double> *, int, cudaStream_t);
+template lgf_status launch_col_convolve_rag<double, 0>(lgf_ctx *, int, int, pk::ConvJob<double> *, int, cudaStream_t);
 }  // namespace lgf

@@ -7,4 +7,6 @@ template lgf_status launch_row_forward<double>(lgf_ctx *, const PoissonGeom &, c
                                            int, int, int, cudaStream_t);
 template lgf_status launch_row_inverse<double>(lgf_ctx *, const PoissonGeom &, const Cx<double> *, double *, const Cx<double> *,
                                            int, int, cudaStream_t);
+template lgf_status launch_row_forward_rag<double>(lgf_ctx *, int, pk::RowJob<double> *, int, cudaStream_t);
+template lgf_status launch_row_inverse_rag<double>(lgf_ctx *, int, bool, pk::RowJob<double> *, int, cudaStream_t);
 }  // namespace lgf

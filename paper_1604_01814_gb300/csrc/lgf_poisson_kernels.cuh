@@ -244,12 +244,14 @@ __device__ __forceinline__ bool column_of(int cta, int w, int K, int nplanes, in
 // stage's upper inputs are zero at compile time and its first butterfly
 // layer is skipped.  Row addresses advance by a fixed stride per radix digit
 // (the last stage's digit is the top digit of the frequency).
+// (The body of every pass kernel takes its CTA coordinates as arguments: the
+// kernels below run it at their own blockIdx, the ragged kernels at the
+// coordinates of a CTA inside one job of a job table.)
 template <typename T, int ML, int W, bool HALF>
-__global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_forward(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
-                                                                     int K, int nplanes, int lo, int n, int64_t rs,
-                                                                     int64_t os, int64_t in_plane, int64_t out_plane,
-                                                                     int64_t in_field, int64_t out_field,
-                                                                     const Cx<T> *__restrict__ twg, RowFlags rf)
+__device__ __forceinline__ void col_forward_body(int bx, int by, const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
+                                                 int K, int nplanes, int lo, int n, int64_t rs, int64_t os,
+                                                 int64_t in_plane, int64_t out_plane, int64_t in_field,
+                                                 int64_t out_field, const Cx<T> *__restrict__ twg, RowFlags rf)
 {
     using P = Plan<ML>;
     constexpr int M = P::M;
@@ -259,9 +261,9 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_forward(const Cx<T> *
     load_twiddles(tw, twg, M);
     const int w = threadIdx.x % W, t = threadIdx.x / W;
     int kx, pl;
-    const bool live = column_of<W>(blockIdx.x, w, K, nplanes, kx, pl);
-    const Cx<T> *ib = in + blockIdx.y * in_field + pl * in_plane + kx;
-    Cx<T> *ob = out + blockIdx.y * out_field + pl * out_plane + kx;
+    const bool live = column_of<W>(bx, w, K, nplanes, kx, pl);
+    const Cx<T> *ib = in + by * in_field + pl * in_plane + kx;
+    Cx<T> *ob = out + by * out_field + pl * out_plane + kx;
     const ColAddrW ad{W};
     constexpr int R0 = P::R0;
     constexpr int NG0 = P::G0 / P::TPC;
@@ -327,17 +329,27 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_forward(const Cx<T> *
     }
 }
 
+template <typename T, int ML, int W, bool HALF>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_forward(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
+                                                                     int K, int nplanes, int lo, int n, int64_t rs,
+                                                                     int64_t os, int64_t in_plane, int64_t out_plane,
+                                                                     int64_t in_field, int64_t out_field,
+                                                                     const Cx<T> *__restrict__ twg, RowFlags rf)
+{
+    col_forward_body<T, ML, W, HALF>(blockIdx.x, blockIdx.y, in, out, K, nplanes, lo, n, rs, os, in_plane, out_plane,
+                                     in_field, out_field, twg, rf);
+}
+
 // Inverse along the column: spectrum rows (natural order, row k at
 // in + k * rs) in; rows [lo, lo + n) of the result written to
 // out + (m - lo) * os.  HALF_OUT: the written rows lie in [0, M/2), so the
 // last stage forms only the lower half of its outputs (otherwise, the
 // shifted y window with targets past M/2, all of them).
 template <typename T, int ML, int W, bool HALF_OUT>
-__global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
-                                                                     int K, int nplanes, int lo, int n, int64_t rs,
-                                                                     int64_t os, int64_t in_plane, int64_t out_plane,
-                                                                     int64_t in_field, int64_t out_field,
-                                                                     const Cx<T> *__restrict__ twg)
+__device__ __forceinline__ void col_inverse_body(int bx, int by, const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
+                                                 int K, int nplanes, int lo, int n, int64_t rs, int64_t os,
+                                                 int64_t in_plane, int64_t out_plane, int64_t in_field,
+                                                 int64_t out_field, const Cx<T> *__restrict__ twg)
 {
     using P = Plan<ML>;
     constexpr int M = P::M;
@@ -347,9 +359,9 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
     load_twiddles(tw, twg, M);
     const int w = threadIdx.x % W, t = threadIdx.x / W;
     int kx, pl;
-    const bool live = column_of<W>(blockIdx.x, w, K, nplanes, kx, pl);
-    const Cx<T> *ib = in + blockIdx.y * in_field + pl * in_plane + kx;
-    Cx<T> *ob = out + blockIdx.y * out_field + pl * out_plane + kx;
+    const bool live = column_of<W>(bx, w, K, nplanes, kx, pl);
+    const Cx<T> *ib = in + by * in_field + pl * in_plane + kx;
+    Cx<T> *ob = out + by * out_field + pl * out_plane + kx;
     const ColAddrW ad{W};
     constexpr int RL = P::RL;
     constexpr int NGL = P::GL / P::TPC;
@@ -398,6 +410,17 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
     }
 }
 
+template <typename T, int ML, int W, bool HALF_OUT>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *__restrict__ in, Cx<T> *__restrict__ out,
+                                                                     int K, int nplanes, int lo, int n, int64_t rs,
+                                                                     int64_t os, int64_t in_plane, int64_t out_plane,
+                                                                     int64_t in_field, int64_t out_field,
+                                                                     const Cx<T> *__restrict__ twg)
+{
+    col_inverse_body<T, ML, W, HALF_OUT>(blockIdx.x, blockIdx.y, in, out, K, nplanes, lo, n, rs, os, in_plane,
+                                         out_plane, in_field, out_field, twg);
+}
+
 // z pass: forward along z over the source planes, times the real even kernel
 // spectrum, inverse along z, target planes written back in place.  The field
 // is the fastest part of the CTA index, so the CTAs of every field of one
@@ -420,10 +443,10 @@ struct ConvOcc {
 // SPEC: 0 the real spectrum of the even embedding ([kz][ky <= My/2][kx]);
 // 1 the complex spectrum of the shifted x window (same layout); 2 the complex
 // spectrum of the shifted y window ([kz][ky < My][kx], no mirror in ky).
-template <typename T, int ML, int W, int SPEC, int ZV>
-__global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML, ZV>::value) k_col_convolve(Cx<T> *__restrict__ B, const void *__restrict__ specv,
-                                                                      int K, int My, int s0, int ns, int t0, int nt,
-                                                                      int64_t field, const Cx<T> *__restrict__ twg)
+template <typename T, int ML, int W, int SPEC>
+__device__ __forceinline__ void col_convolve_body(int bx, int nf, Cx<T> *__restrict__ B, const void *__restrict__ specv,
+                                                  int K, int My, int s0, int ns, int t0, int nt, int64_t field,
+                                                  const Cx<T> *__restrict__ twg)
 {
     constexpr bool CPLX = SPEC > 0;
     using SpecT = typename std::conditional<CPLX, Cx<T>, T>::type;
@@ -436,9 +459,8 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML, ZV>::value) 
     load_twiddles(tw, twg, M);
     const int w = threadIdx.x % W, t = threadIdx.x / W;
     int kx, ky;
-    const int nf = gridDim.x / col_ctas<W>(K, My);
-    const int field_i = blockIdx.x % nf;
-    const bool live = column_of<W>(blockIdx.x / nf, w, K, My, kx, ky);
+    const int field_i = bx % nf;
+    const bool live = column_of<W>(bx / nf, w, K, My, kx, ky);
     const int64_t plane = (int64_t)My * K;
     Cx<T> *bb = B + field_i * field + (int64_t)ky * K + kx;
     const ColAddrW ad{W};
@@ -529,6 +551,15 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML, ZV>::value) 
     }
 }
 
+template <typename T, int ML, int W, int SPEC, int ZV>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML, ZV>::value) k_col_convolve(Cx<T> *__restrict__ B, const void *__restrict__ specv,
+                                                                      int K, int My, int s0, int ns, int t0, int nt,
+                                                                      int64_t field, const Cx<T> *__restrict__ twg)
+{
+    col_convolve_body<T, ML, W, SPEC>(blockIdx.x, gridDim.x / col_ctas<W>(K, My), B, specv, K, My, s0, ns, t0, nt,
+                                      field, twg);
+}
+
 // ---------------------------------------------------------------------------
 // Row passes along x (real <-> half complex), two real rows per complex line.
 // ---------------------------------------------------------------------------
@@ -537,9 +568,9 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML, ZV>::value) 
 // stage's upper inputs are zero at compile time) or from a dense box with row
 // length dense_ld (the spectrum build, full rows).
 template <typename T, int ML, int LPC, bool HALF>
-__global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward(const T *__restrict__ f, Cx<T> *__restrict__ A,
-                                                                       PoissonGeom g, const Cx<T> *__restrict__ twg,
-                                                                       int npairs, int lb, int dense_ld)
+__device__ __forceinline__ void row_forward_body(int bx, int by, const T *__restrict__ f, Cx<T> *__restrict__ A,
+                                                 const PoissonGeom &g, const Cx<T> *__restrict__ twg, int npairs,
+                                                 int lb, int dense_ld)
 {
     using P = Plan<ML>;
     constexpr int M = P::M;
@@ -548,14 +579,14 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward(const T *__
     Cx<T> *s = tw + M;
     load_twiddles(tw, twg, M);
     const int t = threadIdx.x % P::TPC, l = threadIdx.x / P::TPC;
-    const int pr = blockIdx.x * LPC + l;
+    const int pr = bx * LPC + l;
     const bool live = pr < npairs;
     const int hp = g.Ls[1] >> 1;
     const int zi = live ? pr / hp : 0, yi = live ? 2 * (pr - zi * hp) : 0;
     // a CTA whose lines all lie in row blocks without source blocks has
     // nothing to transform (the y pass does not read those rows)
     if (g.srcrow && !__syncthreads_or(live && ((g.srcrow[zi >> lb] >> (yi >> lb)) & 1ull))) return;
-    const T *ff = f + blockIdx.y * g.fstride;
+    const T *ff = f + by * g.fstride;
     const RowAddr<ML> ad{};
     constexpr int R0 = P::R0;
     constexpr int NG0 = P::G0 / P::TPC;
@@ -633,7 +664,7 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward(const T *__
     __syncthreads();
     if (!live) return;
     const int K = g.Kx;
-    Cx<T> *row = A + blockIdx.y * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
+    Cx<T> *row = A + by * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
     for (int k = t; k < K; k += P::TPC) {
         const Cx<T> zk = s[ad(l, pos_of<ML>(k))];
         const Cx<T> zm = s[ad(l, pos_of<ML>(k == 0 ? 0 : M - k))];
@@ -642,15 +673,23 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward(const T *__
     }
 }
 
+template <typename T, int ML, int LPC, bool HALF>
+__global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward(const T *__restrict__ f, Cx<T> *__restrict__ A,
+                                                                       PoissonGeom g, const Cx<T> *__restrict__ twg,
+                                                                       int npairs, int lb, int dense_ld)
+{
+    row_forward_body<T, ML, LPC, HALF>(blockIdx.x, blockIdx.y, f, A, g, twg, npairs, lb, dense_ld);
+}
+
 // Inverse: rows (y, y+1) of target plane z from their half spectra; x in
 // [t0x, t0x + Ltx) scaled by dx^2 and scattered to the target block layout.
 // HALF_OUT: the target x lies in [0, M/2) (even embedding), so only the
 // lower half of the last stage's outputs is formed; otherwise (the shifted x
 // window, targets up to M) every output is.
 template <typename T, int ML, int LPC, bool HALF_OUT>
-__global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T> *__restrict__ A, T *__restrict__ u,
-                                                                       PoissonGeom g, const Cx<T> *__restrict__ twg,
-                                                                       int npairs, int lb)
+__device__ __forceinline__ void row_inverse_body(int bx, int by, const Cx<T> *__restrict__ A, T *__restrict__ u,
+                                                 const PoissonGeom &g, const Cx<T> *__restrict__ twg, int npairs,
+                                                 int lb)
 {
     using P = Plan<ML>;
     constexpr int M = P::M;
@@ -659,7 +698,7 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T>
     Cx<T> *s = tw + M;
     load_twiddles(tw, twg, M);
     const int t = threadIdx.x % P::TPC, l = threadIdx.x / P::TPC;
-    const int pr = blockIdx.x * LPC + l;
+    const int pr = bx * LPC + l;
     const bool live = pr < npairs;
     const int hp = g.Lt[1] >> 1;
     const int zi = live ? pr / hp : 0, yi = live ? 2 * (pr - zi * hp) : 0;
@@ -667,7 +706,7 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T>
     // nothing to write
     if (g.tgtrow && !__syncthreads_or(live && ((g.tgtrow[zi >> lb] >> (yi >> lb)) & 1ull))) return;
     const int K = g.Kx;
-    const Cx<T> *row = A + blockIdx.y * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
+    const Cx<T> *row = A + by * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
     const RowAddr<ML> ad{};
     // Hermitian extension of the two half spectra, packed as Z = G1 + i G2,
     // stored at the digit-reversed positions the inverse sweep expects.
@@ -713,7 +752,7 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T>
     }
     if (!live) return;
     const T sc = T(g.scale);
-    T *uu = u + blockIdx.y * g.ustride;
+    T *uu = u + by * g.ustride;
     const int bm = g.b - 1;
     const int *mrow = g.tgtmap + ((zi >> lb) * g.nbt[1] + (yi >> lb)) * g.nbt[0];
     const int inner = (((zi & bm) << lb) + (yi & bm)) << lb;
@@ -737,6 +776,121 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T>
             q[1 << lb] = sc * a[p].y;   // row y + 1 of the same block (y is even, b >= 2)
         }
     }
+}
+
+template <typename T, int ML, int LPC, bool HALF_OUT>
+__global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse(const Cx<T> *__restrict__ A, T *__restrict__ u,
+                                                                       PoissonGeom g, const Cx<T> *__restrict__ twg,
+                                                                       int npairs, int lb)
+{
+    row_inverse_body<T, ML, LPC, HALF_OUT>(blockIdx.x, blockIdx.y, A, u, g, twg, npairs, lb);
+}
+
+// ---------------------------------------------------------------------------
+// Ragged launches: one pass of many independent problems that share the
+// transform length (and the kernel's compile-time variant) in one launch.
+// The job table travels in the kernel's parameter space; job j owns the CTAs
+// [cta0_j, cta0_{j+1}) of the one-dimensional grid, and every CTA finds its
+// job by a binary search over cta0 (the same for all threads of a CTA), then
+// runs the pass body at its coordinates inside that job.  No CTA waits on
+// another, so problems of any size mix in one launch.
+// ---------------------------------------------------------------------------
+constexpr int kRagJobs = 64;   // jobs per launch (longer lists go in several launches)
+
+template <class J>
+struct RagTable {
+    J j[kRagJobs];
+    int n;
+};
+
+template <class J>
+__device__ __forceinline__ const J &rag_job(const RagTable<J> &t)
+{
+    int lo = 0, hi = t.n - 1;
+    const int c = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.j[mid].cta0 <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return t.j[lo];
+}
+
+// x passes: in = f (forward) or A (inverse), out = A or u; CTAs (gx, nf).
+template <typename T>
+struct RowJob {
+    PoissonGeom g;
+    const void *in;
+    void *out;
+    const Cx<T> *tw;
+    int npairs, lb, nf;
+    int cta0, gx;
+};
+// y passes: the argument list of k_col_forward / k_col_inverse; CTAs (gx, nf).
+template <typename T>
+struct ColJob {
+    const Cx<T> *in;
+    Cx<T> *out;
+    const Cx<T> *tw;
+    RowFlags rf;
+    int64_t rs, os, in_plane, out_plane, in_field, out_field;
+    int K, nplanes, lo, n, nf;
+    int cta0, gx;
+};
+// z pass: the argument list of k_col_convolve; CTAs nf * col_ctas.
+template <typename T>
+struct ConvJob {
+    Cx<T> *B;
+    const void *spec;
+    const Cx<T> *tw;
+    int64_t field;
+    int K, My, s0, ns, t0, nt, nf;
+    int cta0, gx;
+};
+
+template <typename T, int ML, int LPC, bool HALF>
+__global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward_rag(const __grid_constant__ RagTable<RowJob<T>> t)
+{
+    const RowJob<T> &J = rag_job(t);
+    const int c = (int)blockIdx.x - J.cta0;
+    row_forward_body<T, ML, LPC, HALF>(c % J.gx, c / J.gx, (const T *)J.in, (Cx<T> *)J.out, J.g, J.tw, J.npairs, J.lb,
+                                       0);
+}
+
+template <typename T, int ML, int LPC, bool HALF_OUT>
+__global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_inverse_rag(const __grid_constant__ RagTable<RowJob<T>> t)
+{
+    const RowJob<T> &J = rag_job(t);
+    const int c = (int)blockIdx.x - J.cta0;
+    row_inverse_body<T, ML, LPC, HALF_OUT>(c % J.gx, c / J.gx, (const Cx<T> *)J.in, (T *)J.out, J.g, J.tw, J.npairs,
+                                           J.lb);
+}
+
+template <typename T, int ML, int W>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_forward_rag(const __grid_constant__ RagTable<ColJob<T>> t)
+{
+    const ColJob<T> &J = rag_job(t);
+    const int c = (int)blockIdx.x - J.cta0;
+    col_forward_body<T, ML, W, true>(c % J.gx, c / J.gx, J.in, J.out, J.K, J.nplanes, J.lo, J.n, J.rs, J.os,
+                                     J.in_plane, J.out_plane, J.in_field, J.out_field, J.tw, J.rf);
+}
+
+template <typename T, int ML, int W, bool HALF_OUT>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse_rag(const __grid_constant__ RagTable<ColJob<T>> t)
+{
+    const ColJob<T> &J = rag_job(t);
+    const int c = (int)blockIdx.x - J.cta0;
+    col_inverse_body<T, ML, W, HALF_OUT>(c % J.gx, c / J.gx, J.in, J.out, J.K, J.nplanes, J.lo, J.n, J.rs, J.os,
+                                         J.in_plane, J.out_plane, J.in_field, J.out_field, J.tw);
+}
+
+template <typename T, int ML, int W, int SPEC, int ZV>
+__global__ void __launch_bounds__(W * Plan<ML>::TPC, ConvOcc<T, ML, ZV>::value) k_col_convolve_rag(
+    const __grid_constant__ RagTable<ConvJob<T>> t)
+{
+    const ConvJob<T> &J = rag_job(t);
+    col_convolve_body<T, ML, W, SPEC>((int)blockIdx.x - J.cta0, J.nf, J.B, J.spec, J.K, J.My, J.s0, J.ns, J.t0, J.nt,
+                                      J.field, J.tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -783,6 +937,19 @@ lgf_status launch_col_inverse(lgf_ctx *ctx, int M, int K, int nplanes, int nfiel
 template <typename T, int SPEC>
 lgf_status launch_col_convolve(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T *spec, const Cx<T> *tw,
                                int nfields, cudaStream_t s);
+// Ragged launches of one pass over jobs that share the transform length M
+// (and the variant named by the other arguments); every job field but cta0
+// and gx is set by the caller.
+template <typename T>
+lgf_status launch_row_forward_rag(lgf_ctx *ctx, int M, pk::RowJob<T> *jobs, int n, cudaStream_t s);
+template <typename T>
+lgf_status launch_row_inverse_rag(lgf_ctx *ctx, int M, bool half_out, pk::RowJob<T> *jobs, int n, cudaStream_t s);
+template <typename T>
+lgf_status launch_col_forward_rag(lgf_ctx *ctx, int M, pk::ColJob<T> *jobs, int n, cudaStream_t s);
+template <typename T>
+lgf_status launch_col_inverse_rag(lgf_ctx *ctx, int M, bool half_out, pk::ColJob<T> *jobs, int n, cudaStream_t s);
+template <typename T, int SPEC>
+lgf_status launch_col_convolve_rag(lgf_ctx *ctx, int M, int zvar, pk::ConvJob<T> *jobs, int n, cudaStream_t s);
 
 }  // namespace lgf
 
@@ -911,6 +1078,115 @@ lgf_status col_convolve_m(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, const T 
     return LGF_OK;
 }
 
+// Send jobs in tables of kRagJobs, CTA ranges assigned in order; jobs with
+// no CTAs are skipped.
+template <class J, class Kern>
+lgf_status rag_send(lgf_ctx *ctx, Kern kern, int threads, size_t smem, J *jobs, int n, cudaStream_t s,
+                    const char *name)
+{
+    static_assert(sizeof(RagTable<J>) <= 32000, "job table beyond the kernel parameter space");
+    for (int c0 = 0; c0 < n;) {
+        RagTable<J> t;
+        t.n = 0;
+        int64_t ctas = 0;
+        for (; c0 < n && t.n < kRagJobs; ++c0) {
+            J &j = jobs[c0];
+            const int64_t nc = (int64_t)j.gx * j.nf;
+            if (nc <= 0) continue;
+            j.cta0 = (int)ctas;
+            t.j[t.n++] = j;
+            ctas += nc;
+        }
+        if (t.n == 0) continue;
+        if (ctas > 0x7fffffff) return fail(ctx, LGF_EUNSUPPORTED, "ragged launch: too many CTAs");
+        const int ph = prof_begin(ctx, s, name);
+        kern<<<(unsigned)ctas, threads, smem, s>>>(t);
+        LGF_CHECK_LAUNCH(ctx, name);
+        prof_end(ctx, s, ph);
+    }
+    return LGF_OK;
+}
+
+template <typename T, int ML>
+lgf_status row_forward_rag_m(lgf_ctx *ctx, RowJob<T> *jobs, int n, cudaStream_t s)
+{
+    using C = RowCfg<T, ML>;
+    auto kern = k_row_forward_rag<T, ML, C::LPC, true>;
+    for (int i = 0; i < n; ++i) {
+        const PoissonGeom &g = jobs[i].g;
+        if (g.M[0] != ML || g.s0[0] < 0 || 2 * (g.s0[0] + g.Ls[0]) > g.M[0])
+            return fail(ctx, LGF_EINVAL, "ragged row forward: source beyond half the transform length");
+        jobs[i].gx = (jobs[i].npairs + C::LPC - 1) / C::LPC;
+    }
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    return rag_send(ctx, kern, C::LPC * C::TPC, C::SMEM, jobs, n, s, "poisson_x_forward");
+}
+
+template <typename T, int ML>
+lgf_status row_inverse_rag_m(lgf_ctx *ctx, bool half_out, RowJob<T> *jobs, int n, cudaStream_t s)
+{
+    using C = RowCfg<T, ML>;
+    auto kern = half_out ? k_row_inverse_rag<T, ML, C::LPC, true> : k_row_inverse_rag<T, ML, C::LPC, false>;
+    for (int i = 0; i < n; ++i) {
+        const PoissonGeom &g = jobs[i].g;
+        if (g.M[0] != ML || g.t0[0] < 0 || g.t0[0] + g.Lt[0] > g.M[0] ||
+            (half_out && 2 * (g.t0[0] + g.Lt[0]) > g.M[0]))
+            return fail(ctx, LGF_EINVAL, "ragged row inverse: target beyond the transform length");
+        jobs[i].gx = (jobs[i].npairs + C::LPC - 1) / C::LPC;
+    }
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    return rag_send(ctx, kern, C::LPC * C::TPC, C::SMEM, jobs, n, s, "poisson_x_inverse");
+}
+
+template <typename T, int ML>
+lgf_status col_forward_rag_m(lgf_ctx *ctx, ColJob<T> *jobs, int n, cudaStream_t s)
+{
+    using C = ColCfg<T, ML>;
+    auto kern = k_col_forward_rag<T, ML, C::W>;
+    for (int i = 0; i < n; ++i) {
+        if (jobs[i].lo < 0 || jobs[i].lo + jobs[i].n > ML / 2)
+            return fail(ctx, LGF_EINVAL, "ragged column forward: input beyond half the transform length");
+        jobs[i].gx = col_ctas<C::W>(jobs[i].K, jobs[i].nplanes);
+    }
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    return rag_send(ctx, kern, C::W * C::TPC, C::SMEM, jobs, n, s, "poisson_y_forward");
+}
+
+template <typename T, int ML>
+lgf_status col_inverse_rag_m(lgf_ctx *ctx, bool half_out, ColJob<T> *jobs, int n, cudaStream_t s)
+{
+    using C = ColCfg<T, ML>;
+    auto kern = half_out ? k_col_inverse_rag<T, ML, C::W, true> : k_col_inverse_rag<T, ML, C::W, false>;
+    for (int i = 0; i < n; ++i) {
+        if (jobs[i].lo < 0 || jobs[i].lo + jobs[i].n > (half_out ? ML / 2 : ML))
+            return fail(ctx, LGF_EINVAL, "ragged column inverse: rows beyond the length");
+        jobs[i].gx = col_ctas<C::W>(jobs[i].K, jobs[i].nplanes);
+    }
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    return rag_send(ctx, kern, C::W * C::TPC, C::SMEM, jobs, n, s, "poisson_y_inverse");
+}
+
+template <typename T, int ML, int SPEC>
+lgf_status col_convolve_rag_m(lgf_ctx *ctx, int zvar, ConvJob<T> *jobs, int n, cudaStream_t s)
+{
+    using C = ColCfg<T, ML>;
+    auto kern = (sizeof(T) == 4 && zvar) ? k_col_convolve_rag<T, ML, C::W, SPEC, sizeof(T) == 4 ? 1 : 0>
+                                         : k_col_convolve_rag<T, ML, C::W, SPEC, 0>;
+    for (int i = 0; i < n; ++i) {
+        const ConvJob<T> &j = jobs[i];
+        if (j.s0 < 0 || j.t0 < 0 || 2 * (j.s0 + j.ns) > ML || 2 * (j.t0 + j.nt) > ML)
+            return fail(ctx, LGF_EINVAL, "ragged z pass: planes beyond half the transform length");
+        jobs[i].gx = col_ctas<C::W>(j.K, j.My);
+    }
+    lgf_status st = set_smem(ctx, kern, C::SMEM);
+    if (st != LGF_OK) return st;
+    return rag_send(ctx, kern, C::W * C::TPC, C::SMEM, jobs, n, s, "poisson_z_convolve");
+}
+
 #define LGF_DISPATCH_ML(M_RT, CALL)                                             \
     switch (M_RT) {                                                             \
     case 32: { constexpr int LM = 32; return CALL; }                            \
@@ -978,6 +1254,36 @@ lgf_status launch_col_convolve(lgf_ctx *ctx, const PoissonGeom &g, Cx<T> *B, con
                                int nfields, cudaStream_t s)
 {
     LGF_DISPATCH_ML(g.M[2], (pk::col_convolve_m<T, LM, SPEC>(ctx, g, B, spec, tw, nfields, s)));
+}
+
+template <typename T>
+lgf_status launch_row_forward_rag(lgf_ctx *ctx, int M, pk::RowJob<T> *jobs, int n, cudaStream_t s)
+{
+    LGF_DISPATCH_ML(M, (pk::row_forward_rag_m<T, LM>(ctx, jobs, n, s)));
+}
+
+template <typename T>
+lgf_status launch_row_inverse_rag(lgf_ctx *ctx, int M, bool half_out, pk::RowJob<T> *jobs, int n, cudaStream_t s)
+{
+    LGF_DISPATCH_ML(M, (pk::row_inverse_rag_m<T, LM>(ctx, half_out, jobs, n, s)));
+}
+
+template <typename T>
+lgf_status launch_col_forward_rag(lgf_ctx *ctx, int M, pk::ColJob<T> *jobs, int n, cudaStream_t s)
+{
+    LGF_DISPATCH_ML(M, (pk::col_forward_rag_m<T, LM>(ctx, jobs, n, s)));
+}
+
+template <typename T>
+lgf_status launch_col_inverse_rag(lgf_ctx *ctx, int M, bool half_out, pk::ColJob<T> *jobs, int n, cudaStream_t s)
+{
+    LGF_DISPATCH_ML(M, (pk::col_inverse_rag_m<T, LM>(ctx, half_out, jobs, n, s)));
+}
+
+template <typename T, int SPEC>
+lgf_status launch_col_convolve_rag(lgf_ctx *ctx, int M, int zvar, pk::ConvJob<T> *jobs, int n, cudaStream_t s)
+{
+    LGF_DISPATCH_ML(M, (pk::col_convolve_rag_m<T, LM, SPEC>(ctx, zvar, jobs, n, s)));
 }
 
 }  // namespace lgf
