@@ -432,12 +432,12 @@ __global__ void __launch_bounds__(W * Plan<ML>::TPC) k_col_inverse(const Cx<T> *
 // lengths 256 (32 warps), 320, 384 and 512 (24 warps) and the long mixed
 // lengths (2 CTAs); no spills).
 // ZV = 1 (the tuner's alternative, FP32 only) asks for one more resident CTA
-// per SM than the default, i.e. a tighter register cap (3 where the default
-// leaves the choice to the compiler).
+// per SM than the default, i.e. a tighter register cap (where the default
+// leaves the choice to the compiler: 4 up to length 192, 3 above).
 template <typename T, int ML, int ZV = 0>
 struct ConvOcc {
     static constexpr int base = sizeof(T) == 4 ? (ML == 256 ? 4 : ML == 320 || ML == 384 || ML == 512 ? 3 : ML == 640 || ML == 1536 || ML == 2560 || ML == 3072 ? 2 : 1) : 1;
-    static constexpr int value = ZV == 0 ? base : (base == 1 ? 3 : base + 1);
+    static constexpr int value = ZV == 0 ? base : (base == 1 ? (ML <= 192 ? 4 : 3) : base + 1);
 };
 
 // SPEC: 0 the real spectrum of the even embedding ([kz][ky <= My/2][kx]);
