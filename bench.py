@@ -274,6 +274,8 @@ def pass_io_bytes(p, nfields: int) -> dict:
         "poisson_z_convolve": nfields * (Ls[2] * M[1] * K * c8 + Lt[2] * M[1] * K * c8) + spec,
         "poisson_y_inverse": nfields * (Lt[2] * M[1] * K * c8 + Lt[2] * Lt[1] * K * c8),
         "poisson_x_inverse": nfields * (Lt[2] * Lt[1] * K * c8 + ntgt * b3 * 4),
+        # the y and x inverses fused (one cluster per target plane): B in, u out
+        "poisson_yx_inverse": nfields * (Lt[2] * M[1] * K * c8 + ntgt * b3 * 4),
     }
 
 
@@ -288,7 +290,7 @@ def z_pass_flops(p, nfields: int) -> float:
 
 
 POISSON_PASSES = ("poisson_x_forward", "poisson_y_forward", "poisson_z_convolve", "poisson_y_inverse",
-                  "poisson_x_inverse")
+                  "poisson_x_inverse", "poisson_yx_inverse")
 INTF_PASSES = ("intfactor_pass_xy", "intfactor_pass_z", "intfactor_pass_x", "intfactor_pass_y")
 
 

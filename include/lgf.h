@@ -451,7 +451,7 @@ LGF_API lgf_status lgf_wait_selftest(lgf_ctx *ctx, int64_t cycles, void *stream)
    of y (the even circular embedding of G_L, M >= 2L - 1 on the union extent
    L, or the shifted window, M >= Ls + Lt - 1), the transform length along
    each axis (the smallest supported length, or the next one, whose radix
-   plan may run faster), and the register cap of the z pass (FP32); a batch
+   plan may run faster) and the register cap of the z pass (FP32); a batch
    also has its branch count (1, 2, 4 or 8 concurrent streams).  With tuning on,
    each new plan's first apply times candidates on the caller's stream
    (coordinate descent from the default: one knob changed at a time, a change
@@ -459,7 +459,11 @@ LGF_API lgf_status lgf_wait_selftest(lgf_ctx *ctx, int64_t cycles, void *stream)
    new batch shape times its branch counts; the choices are kept in the
    context and, when `cache_path` names a file (NULL: the LGF_TUNE_CACHE
    environment variable, if set), appended to it as "key -> value" lines and
-   read back by later contexts.  LGF_TUNE_CACHED uses the file's choices and
+   read back by later contexts.  A plan value ends in "f0" or "f1": with
+   "f1" (FP32, lengths 64, 80, 96 and 128 along y) the y and x inverses run
+   fused, one thread-block cluster per target plane holding the plane's rows
+   in distributed shared memory; the tuner keeps "f0", which measured faster
+   inside batches.  LGF_TUNE_CACHED uses the file's choices and
    the defaults elsewhere, timing nothing.  Results do not depend on the
    choices beyond floating-point rounding.  Tuning runs synchronously in the
    call that first meets a plan, so tune before capturing a stream into a
@@ -477,7 +481,8 @@ typedef struct {
     int64_t shifted_x, shifted_y, longer_x, longer_y, longer_z, z_variant;   /* counts over the context's plans */
     double tune_ms;             /* GPU time spent timing candidates */
     int64_t last_ragged;        /* 1: the last batch ran its Poisson parts ragged (one launch per pass and length) */
-    int64_t reserved[3];
+    int64_t fused_inverse;      /* plans whose y and x inverses run as one cluster kernel */
+    int64_t reserved[2];
 } lgf_tune_info;
 
 /* The tuner's counters and a summary of the choices of the context's plans.

@@ -77,7 +77,7 @@ class lgf_tune_info(ctypes.Structure):
                 ("last_branches", ctypes.c_int64), ("shifted_x", ctypes.c_int64), ("shifted_y", ctypes.c_int64),
                 ("longer_x", ctypes.c_int64), ("longer_y", ctypes.c_int64), ("longer_z", ctypes.c_int64),
                 ("z_variant", ctypes.c_int64), ("tune_ms", ctypes.c_double), ("last_ragged", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("fused_inverse", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2)]
 
 
 class LgfError(RuntimeError):

@@ -1187,6 +1187,8 @@ lgf_status lgf_tune_report(lgf_ctx *ctx, lgf_tune_info *out)
         out->longer_y += p->choice.bump[1] > 0;
         out->longer_z += p->choice.bump[2] > 0;
         out->z_variant += p->choice.zvar;
+        int rpb = 0;
+        out->fused_inverse += ctx->prec == LGF_F32 && poisson_fused_ncl(p->g, &rpb) > 0;
     }
     return LGF_OK;
 }

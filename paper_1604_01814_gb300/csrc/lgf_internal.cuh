@@ -54,6 +54,7 @@ struct PoissonGeom {
     int xasym, xc, xP;
     int yasym, yc, yP;
     int zvar;           // z-pass variant: 0 default, 1 one more CTA per SM (tighter register cap)
+    int fuse;           // FP32: the y and x inverses as one cluster kernel where available
     double scale;       // dx^2
 };
 
@@ -62,10 +63,11 @@ struct PoissonChoice {
     int shift[2] = {0, 0};   // x, y: shifted window instead of the even embedding
     int bump[3] = {0, 0, 0}; // transform length: the bump-th supported length above the smallest valid one
     int zvar = 0;
+    int fuse = 0;            // fused y+x inverse (FP32, where instantiated; the tuner's alternative)
     bool operator==(const PoissonChoice &o) const
     {
         return shift[0] == o.shift[0] && shift[1] == o.shift[1] && bump[0] == o.bump[0] && bump[1] == o.bump[1] &&
-               bump[2] == o.bump[2] && zvar == o.zvar;
+               bump[2] == o.bump[2] && zvar == o.zvar && fuse == o.fuse;
     }
 };
 
@@ -301,6 +303,10 @@ lgf_status poisson_spectrum(lgf_ctx *ctx, const PoissonGeom &pg, double alpha, S
 lgf_status poisson_run(lgf_ctx *ctx, PoissonPlan *pl, const Spectrum *sp, const void *f, void *u, int nfields,
                        double dx, cudaStream_t s);
 lgf_status poisson_prepare_scratch(lgf_ctx *ctx, const PoissonPlan *pl, int nfields);
+// Cluster size of the fused y+x inverse for a geometry (0: not available:
+// FP64, a length pair not instantiated, or rows that do not fit), and the
+// rows per CTA.
+int poisson_fused_ncl(const PoissonGeom &g, int *rpb);
 // Many Poisson parts at once (lgf_batch_apply): one launch per pass and
 // transform length, the length groups of a pass spread over `nbr` branch
 // streams of the context (nbr <= 1: all on s).  Every part's A and B are

@@ -25,7 +25,7 @@
 #include <cstring>
 #include <unordered_map>
 
-#include "lgf_poisson_kernels.cuh"
+#include "lgf_poisson_fused.cuh"
 
 namespace lgf {
 // The pass launchers are instantiated in lgf_poisson_{f32,f64}_{rows,cols,
@@ -62,6 +62,17 @@ namespace lgf {
 LGF_EXTERN_PASSES(float)
 LGF_EXTERN_PASSES(double)
 #undef LGF_EXTERN_PASSES
+// the fused y+x inverse: lgf_poisson_f32_fused_<My>.cu
+namespace pk {
+#define LGF_EXTERN_YX(MYV)                                                                                     \
+    extern template lgf_status yx_launch_my<MYV>(lgf_ctx *, int, int, YXJob *, int, cudaStream_t);            \
+    extern template bool yx_info_my<MYV>(int, size_t *, int *);
+LGF_EXTERN_YX(64)
+LGF_EXTERN_YX(80)
+LGF_EXTERN_YX(96)
+LGF_EXTERN_YX(128)
+#undef LGF_EXTERN_YX
+}  // namespace pk
 }  // namespace lgf
 
 namespace lgf {
@@ -119,6 +130,7 @@ bool poisson_geometry(const PoissonPlan &pl, const PoissonChoice &ch, PoissonGeo
     g.yc = ch.shift[1] ? (pl.tlo[1] - pl.slo[1]) * b : 0;
     g.yP = ch.shift[1] ? g.Lt[1] + (g.M[1] - g.Ls[1] + 1 - g.Lt[1]) / 2 : g.M[1] / 2;
     g.zvar = ch.zvar;
+    g.fuse = ch.fuse;
     g.Kx = g.M[0] / 2 + 1;
     g.ldA_y = std::max(g.Ls[1], g.Lt[1]);
     *A = (int64_t)std::max(g.Ls[2], g.Lt[2]) * g.ldA_y * g.Kx;
@@ -222,6 +234,45 @@ int log2i(int v)
     return l;
 }
 
+constexpr size_t kFusedSmemMax = 200 * 1024;   // shared memory of one fused CTA, at most
+
+bool yx_info(int My, int Mx, size_t *work, int *lpc)
+{
+    switch (My) {
+    case 64: return pk::yx_info_my<64>(Mx, work, lpc);
+    case 80: return pk::yx_info_my<80>(Mx, work, lpc);
+    case 96: return pk::yx_info_my<96>(Mx, work, lpc);
+    case 128: return pk::yx_info_my<128>(Mx, work, lpc);
+    default: return false;
+    }
+}
+
+lgf_status yx_launch(lgf_ctx *ctx, int My, int Mx, int ncl, pk::YXJob *jobs, int n, cudaStream_t s)
+{
+    switch (My) {
+    case 64: return pk::yx_launch_my<64>(ctx, Mx, ncl, jobs, n, s);
+    case 80: return pk::yx_launch_my<80>(ctx, Mx, ncl, jobs, n, s);
+    case 96: return pk::yx_launch_my<96>(ctx, Mx, ncl, jobs, n, s);
+    case 128: return pk::yx_launch_my<128>(ctx, Mx, ncl, jobs, n, s);
+    default: return fail(ctx, LGF_EUNSUPPORTED, "fused inverse: length along y not instantiated");
+    }
+}
+
+pk::YXJob yx_job(const PoissonGeom &g, const Cx<float> *B, float *u, const Cx<float> *twy, const Cx<float> *twx,
+                 int nf, int rpb)
+{
+    pk::YXJob j{};
+    j.g = g;
+    j.B = B;
+    j.u = u;
+    j.twy = twy;
+    j.twx = twx;
+    j.nf = nf;
+    j.lb = log2i(g.b);
+    j.rpb = rpb;
+    return j;
+}
+
 // The five passes of one problem (all fields in each launch); in spectrum
 // mode only the forward transform of a dense box (x, y, then z in place).
 template <typename T>
@@ -253,6 +304,14 @@ lgf_status run_passes(lgf_ctx *ctx, const PoissonGeom &g, const T *f, T *u, Cx<T
        : g.xasym ? launch_col_convolve<T, 1>(ctx, g, B, spec, twz, nf, s)
                  : launch_col_convolve<T, 0>(ctx, g, B, spec, twz, nf, s);
     if (st != LGF_OK) return st;
+    if constexpr (sizeof(T) == 4) {
+        int rpb = 0;
+        const int ncl = poisson_fused_ncl(g, &rpb);
+        if (ncl > 0) {
+            pk::YXJob j = yx_job(g, B, u, twy, twx, nf, rpb);
+            return yx_launch(ctx, My, g.M[0], ncl, &j, 1, s);
+        }
+    }
     if ((st = launch_col_inverse<T>(ctx, My, K, g.Lt[2], nf, B, A, g.t0[1], g.Lt[1], K, K, planeB, planeA, g.Bstride,
                                     g.Astride, twy, s, "poisson_y_inverse")) != LGF_OK)
         return st;
@@ -260,6 +319,24 @@ lgf_status run_passes(lgf_ctx *ctx, const PoissonGeom &g, const T *f, T *u, Cx<T
 }
 
 }  // namespace
+
+int poisson_fused_ncl(const PoissonGeom &g, int *rpb)
+{
+    size_t work = 0;
+    int lpc = 0;
+    if (!g.fuse || !yx_info(g.M[1], g.M[0], &work, &lpc) || g.Lt[1] < 2) return 0;
+    // the smallest cluster whose CTAs hold their rows in one batch of line
+    // pairs and in shared memory
+    for (int ncl : {1, 2, 4}) {
+        int r = (g.Lt[1] + ncl - 1) / ncl;
+        r += r & 1;
+        if (r <= 2 * lpc && (size_t)r * g.Kx * sizeof(Cx<float>) + work <= kFusedSmemMax) {
+            *rpb = r;
+            return ncl;
+        }
+    }
+    return 0;
+}
 
 const void *twiddles(lgf_ctx *ctx, int M, bool dbl, lgf_status *st)
 {
@@ -577,6 +654,7 @@ lgf_status run_ragged(lgf_ctx *ctx, const RagPart *parts, int n, cudaStream_t s,
     JobGroups<pk::RowJob<T>> xf, xi;
     JobGroups<pk::ColJob<T>> yf, yi;
     JobGroups<pk::ConvJob<T>> zc;
+    JobGroups<pk::YXJob> yx;
     lgf_status st = LGF_OK;
     for (int i = 0; i < n; ++i) {
         const RagPart &q = parts[i];
@@ -632,6 +710,14 @@ lgf_status run_ragged(lgf_ctx *ctx, const RagPart *parts, int n, cudaStream_t s,
         z.nf = q.nf;
         const int spec = g.yasym ? 2 : g.xasym ? 1 : 0;
         zc.add({g.M[2], spec, sizeof(T) == 4 ? g.zvar : 0}, z);
+        if constexpr (sizeof(T) == 4) {   // the fused y+x inverse where it applies
+            int rpb = 0;
+            const int ncl = poisson_fused_ncl(g, &rpb);
+            if (ncl > 0) {
+                yx.add({My, g.M[0], ncl}, yx_job(g, B, (float *)q.u, tw[1], tw[0], q.nf, rpb));
+                continue;
+            }
+        }
         pk::ColJob<T> c2{};
         c2.in = B;
         c2.out = A;
@@ -674,7 +760,14 @@ lgf_status run_ragged(lgf_ctx *ctx, const RagPart *parts, int n, cudaStream_t s,
                                   : launch_col_convolve_rag<T, 0>(ctx, key[0], key[2], j, nj, bs);
          })) != LGF_OK)
         return st;
-    if ((st = ragged_pass(ctx, s, nbr, (int)yi.keys.size(), [&](int k, cudaStream_t bs) {
+    // the fused inverses go with the y inverses (both read B)
+    const int nyi = (int)yi.keys.size();
+    if ((st = ragged_pass(ctx, s, nbr, nyi + (int)yx.keys.size(), [&](int k, cudaStream_t bs) {
+             if (k >= nyi) {
+                 const auto &key = yx.keys[k - nyi];
+                 auto &j = yx.jobs[k - nyi];
+                 return yx_launch(ctx, key[0], key[1], key[2], j.data(), (int)j.size(), bs);
+             }
              return launch_col_inverse_rag<T>(ctx, yi.keys[k][0], yi.keys[k][1] != 0, yi.jobs[k].data(),
                                               (int)yi.jobs[k].size(), bs);
          })) != LGF_OK)

@@ -686,73 +686,90 @@ __global__ void __launch_bounds__(LPC * Plan<ML>::TPC) k_row_forward(const T *__
 // HALF_OUT: the target x lies in [0, M/2) (even embedding), so only the
 // lower half of the last stage's outputs is formed; otherwise (the shifted x
 // window, targets up to M) every output is.
-template <typename T, int ML, int LPC, bool HALF_OUT>
-__device__ __forceinline__ void row_inverse_body(int bx, int by, const Cx<T> *__restrict__ A, T *__restrict__ u,
-                                                 const PoissonGeom &g, const Cx<T> *__restrict__ twg, int npairs,
-                                                 int lb)
+// One line pair per slot l < LPC (thread t of TPC in it): rows (yi, yi+1)
+// of target plane zi, their half spectra at row[0..K) and row[K..2K), in any
+// memory; the Hermitian extension goes to s, the inverse sweep runs, and x in
+// [t0x, t0x + Ltx) scaled by dx^2 is scattered to the target blocks of uu.
+// tw holds the M twiddles in shared memory.  GUARD (the fused inverse, rows
+// in shared memory): the CTA may have threads beyond the LPC slots, which
+// take part in the barriers only.
+template <typename T, int ML, int LPC, bool HALF_OUT, bool GUARD = false>
+__device__ __forceinline__ void row_inverse_line(int t, int l, bool live, int zi, int yi,
+                                                 const Cx<T> *__restrict__ row, T *__restrict__ uu,
+                                                 const PoissonGeom &g, const Cx<T> *__restrict__ tw,
+                                                 Cx<T> *__restrict__ s, int lb)
 {
     using P = Plan<ML>;
     constexpr int M = P::M;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *s = tw + M;
-    load_twiddles(tw, twg, M);
-    const int t = threadIdx.x % P::TPC, l = threadIdx.x / P::TPC;
-    const int pr = bx * LPC + l;
-    const bool live = pr < npairs;
-    const int hp = g.Lt[1] >> 1;
-    const int zi = live ? pr / hp : 0, yi = live ? 2 * (pr - zi * hp) : 0;
-    // a CTA whose lines all lie in row blocks without target blocks has
-    // nothing to write
-    if (g.tgtrow && !__syncthreads_or(live && ((g.tgtrow[zi >> lb] >> (yi >> lb)) & 1ull))) return;
+    const bool act = !GUARD || l < LPC;
+    if (GUARD) live = live && act;
     const int K = g.Kx;
-    const Cx<T> *row = A + by * g.Astride + ((int64_t)zi * g.ldA_y + yi) * K;
     const RowAddr<ML> ad{};
     // Hermitian extension of the two half spectra, packed as Z = G1 + i G2,
     // stored at the digit-reversed positions the inverse sweep expects.
     constexpr int NPT = M / P::TPC;
-    Cx<T> g1[NPT], g2[NPT];
+    if constexpr (GUARD) {
+        // (row may lie in shared memory: each value is stored right after its
+        // load, so no long run of loads is held in registers)
+        if (act) {
 #pragma unroll
-    for (int i = 0; i < NPT; ++i) {
-        const int k = t + i * P::TPC;
-        const int kk = k <= M / 2 ? k : M - k;
-        g1[i] = live ? row[kk] : Cx<T>{T(0), T(0)};
-        g2[i] = live ? row[K + kk] : Cx<T>{T(0), T(0)};
-    }
-#pragma unroll
-    for (int i = 0; i < NPT; ++i) {
-        const int k = t + i * P::TPC;
-        Cx<T> v;
-        if (k <= M / 2) {
-            if (k == 0 || k == M / 2) {
-                g1[i].y = T(0);
-                g2[i].y = T(0);
+            for (int i = 0; i < NPT; ++i) {
+                const int k = t + i * P::TPC;
+                const int kk = k <= M / 2 ? k : M - k;
+                Cx<T> g1 = live ? row[kk] : Cx<T>{T(0), T(0)};
+                Cx<T> g2 = live ? row[K + kk] : Cx<T>{T(0), T(0)};
+                if (k == 0 || k == M / 2) {
+                    g1.y = T(0);
+                    g2.y = T(0);
+                }
+                s[ad(l, pos_of<ML>(k))] = k <= M / 2 ? Cx<T>{g1.x - g2.y, g1.y + g2.x} : Cx<T>{g1.x + g2.y, g2.x - g1.y};
             }
-            v = {g1[i].x - g2[i].y, g1[i].y + g2[i].x};
-        } else {
-            v = {g1[i].x + g2[i].y, g2[i].x - g1[i].y};
         }
-        s[ad(l, pos_of<ML>(k))] = v;
+    } else {
+        Cx<T> g1[NPT], g2[NPT];
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+            const int k = t + i * P::TPC;
+            const int kk = k <= M / 2 ? k : M - k;
+            g1[i] = live ? row[kk] : Cx<T>{T(0), T(0)};
+            g2[i] = live ? row[K + kk] : Cx<T>{T(0), T(0)};
+        }
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+            const int k = t + i * P::TPC;
+            Cx<T> v;
+            if (k <= M / 2) {
+                if (k == 0 || k == M / 2) {
+                    g1[i].y = T(0);
+                    g2[i].y = T(0);
+                }
+                v = {g1[i].x - g2[i].y, g1[i].y + g2[i].x};
+            } else {
+                v = {g1[i].x + g2[i].y, g2[i].x - g1[i].y};
+            }
+            s[ad(l, pos_of<ML>(k))] = v;
+        }
     }
     __syncthreads();
     constexpr int RL = P::RL;
+    if (act) {
 #pragma unroll
-    for (int gg = t; gg < P::GL; gg += P::TPC) {
-        Cx<T> c[RL];
+        for (int gg = t; gg < P::GL; gg += P::TPC) {
+            Cx<T> c[RL];
 #pragma unroll
-        for (int q = 0; q < RL; ++q) c[q] = s[ad(l, (gg * P::RL) + q)];
-        Dft<RL, 1, T>::run(c);
+            for (int q = 0; q < RL; ++q) c[q] = s[ad(l, (gg * P::RL) + q)];
+            Dft<RL, 1, T>::run(c);
 #pragma unroll
-        for (int q = 0; q < RL; ++q) s[ad(l, (gg * P::RL) + q)] = c[q];
+            for (int q = 0; q < RL; ++q) s[ad(l, (gg * P::RL) + q)] = c[q];
+        }
     }
     __syncthreads();
     if constexpr (P::NST == 3) {
-        middle_stage<ML, 1>(s, ad, l, t, tw);
+        if (act) middle_stage<ML, 1>(s, ad, l, t, tw);
         __syncthreads();
     }
     if (!live) return;
     const T sc = T(g.scale);
-    T *uu = u + by * g.ustride;
     const int bm = g.b - 1;
     const int *mrow = g.tgtmap + ((zi >> lb) * g.nbt[1] + (yi >> lb)) * g.nbt[0];
     const int inner = (((zi & bm) << lb) + (yi & bm)) << lb;
@@ -776,6 +793,29 @@ __device__ __forceinline__ void row_inverse_body(int bx, int by, const Cx<T> *__
             q[1 << lb] = sc * a[p].y;   // row y + 1 of the same block (y is even, b >= 2)
         }
     }
+}
+
+template <typename T, int ML, int LPC, bool HALF_OUT>
+__device__ __forceinline__ void row_inverse_body(int bx, int by, const Cx<T> *__restrict__ A, T *__restrict__ u,
+                                                 const PoissonGeom &g, const Cx<T> *__restrict__ twg, int npairs,
+                                                 int lb)
+{
+    using P = Plan<ML>;
+    constexpr int M = P::M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *tw = reinterpret_cast<Cx<T> *>(smem_raw);
+    Cx<T> *s = tw + M;
+    load_twiddles(tw, twg, M);
+    const int t = threadIdx.x % P::TPC, l = threadIdx.x / P::TPC;
+    const int pr = bx * LPC + l;
+    const bool live = pr < npairs;
+    const int hp = g.Lt[1] >> 1;
+    const int zi = live ? pr / hp : 0, yi = live ? 2 * (pr - zi * hp) : 0;
+    // a CTA whose lines all lie in row blocks without target blocks has
+    // nothing to write
+    if (g.tgtrow && !__syncthreads_or(live && ((g.tgtrow[zi >> lb] >> (yi >> lb)) & 1ull))) return;
+    const Cx<T> *row = A + by * g.Astride + ((int64_t)zi * g.ldA_y + yi) * g.Kx;
+    row_inverse_line<T, ML, LPC, HALF_OUT>(t, l, live, zi, yi, row, u + by * g.ustride, g, tw, s, lb);
 }
 
 template <typename T, int ML, int LPC, bool HALF_OUT>

@@ -5,7 +5,8 @@
 // embedding along x and along y (the even circular embedding or the shifted
 // window), the transform length along each axis (the smallest supported
 // length that holds the convolution, or the next one, whose radix plan may
-// run faster), and the register variant of the z pass.  On a plan's first
+// run faster), and the register variant of the z pass.  (Whether the y and x
+// inverses run as one cluster kernel is a persisted choice only.)  On a plan's first
 // use with tuning on, the tuner times candidates by coordinate descent from
 // the default choice: it changes one knob at a time, keeps a change that
 // cuts the median of the timed repetitions by at least 3 %, and stops after
@@ -54,6 +55,7 @@ TuneChoiceText to_text(const PoissonChoice &c)
     for (int d = 0; d < 2; ++d) t.shift[d] = c.shift[d];
     for (int d = 0; d < 3; ++d) t.bump[d] = c.bump[d];
     t.zvar = c.zvar;
+    t.fuse = c.fuse;
     return t;
 }
 
@@ -63,6 +65,7 @@ PoissonChoice from_text(const TuneChoiceText &t)
     for (int d = 0; d < 2; ++d) c.shift[d] = t.shift[d];
     for (int d = 0; d < 3; ++d) c.bump[d] = t.bump[d];
     c.zvar = t.zvar;
+    c.fuse = t.fuse;
     return c;
 }
 
@@ -107,6 +110,9 @@ lgf_status tune_poisson(lgf_ctx *ctx, PoissonPlan *pl, int nf, double kalpha, cu
     if (st != LGF_OK) return st;
     ++ctx->tune_candidates;
     const bool f32 = ctx->prec == LGF_F32;
+    // (the fused y+x inverse is not searched: timed alone it won on some plate
+    // plans by a few per cent, inside the batch it lost; a persisted choice
+    // "f1" selects it)
     for (int knob = 0; knob < 6; ++knob) {
         PoissonChoice c = best;
         if (knob < 2) c.shift[knob] ^= 1;                 // the other embedding along x, y

@@ -23,6 +23,7 @@ struct TuneChoiceText {
     int shift[2] = {0, 0};
     int bump[3] = {0, 0, 0};
     int zvar = 0;
+    int fuse = 0;
 };
 
 inline std::string tune_plan_key(bool f64, int b, const int nbs[3], const int nbt[3], const int off[3], int nf)
@@ -37,7 +38,7 @@ inline std::string tune_plan_value(const TuneChoiceText &c)
 {
     std::ostringstream o;
     o << "x" << c.shift[0] << " y" << c.shift[1] << " bx" << c.bump[0] << " by" << c.bump[1] << " bz" << c.bump[2]
-      << " z" << c.zvar;
+      << " z" << c.zvar << " f" << c.fuse;
     return o.str();
 }
 
@@ -45,9 +46,12 @@ inline std::string tune_plan_value(const TuneChoiceText &c)
 inline bool tune_parse_plan_value(const std::string &v, TuneChoiceText *c)
 {
     TuneChoiceText t;
-    if (std::sscanf(v.c_str(), "x%d y%d bx%d by%d bz%d z%d", &t.shift[0], &t.shift[1], &t.bump[0], &t.bump[1],
-                    &t.bump[2], &t.zvar) != 6)
-        return false;
+    // (files written before the fused inverse existed end after the z field:
+    // the inverse then stays apart, the default)
+    const int nread = std::sscanf(v.c_str(), "x%d y%d bx%d by%d bz%d z%d f%d", &t.shift[0], &t.shift[1], &t.bump[0],
+                                  &t.bump[1], &t.bump[2], &t.zvar, &t.fuse);
+    if (nread != 6 && nread != 7) return false;
+    if (t.fuse < 0 || t.fuse > 1) return false;
     for (int d = 0; d < 2; ++d)
         if (t.shift[d] < 0 || t.shift[d] > 1) return false;
     for (int d = 0; d < 3; ++d)

@@ -123,8 +123,9 @@ static void tune_file_round_trip()
     c.shift[1] = 1;
     c.bump[2] = 1;
     c.zvar = 1;
+    c.fuse = 1;
     const std::string v = tune_plan_value(c);
-    CHECK(v == "x1 y1 bx0 by0 bz1 z1");
+    CHECK(v == "x1 y1 bx0 by0 bz1 z1 f1");
     std::map<std::string, std::string> m;
     std::string text = "# comment\n" + tune_line(k, "x0 y0 bx0 by0 bz0 z0") + "garbage line\n" + tune_line(k, v) +
                        tune_line(tune_batch_key(true, 0x9f3aull), "nb2") + " -> lonely\n";
@@ -133,7 +134,9 @@ static void tune_file_round_trip()
     CHECK(m[tune_batch_key(true, 0x9f3aull)] == "nb2");
     TuneChoiceText r;
     CHECK(tune_parse_plan_value(m[k], &r));
-    CHECK(r.shift[0] == 1 && r.shift[1] == 1 && r.bump[0] == 0 && r.bump[2] == 1 && r.zvar == 1);
+    CHECK(r.shift[0] == 1 && r.shift[1] == 1 && r.bump[0] == 0 && r.bump[2] == 1 && r.zvar == 1 && r.fuse == 1);
+    CHECK(tune_parse_plan_value("x0 y1 bx0 by0 bz0 z1", &r) && r.fuse == 0);   // older file: apart, the default
+    CHECK(!tune_parse_plan_value("x0 y0 bx0 by0 bz0 z0 f2", &r));             // out of range
     CHECK(!tune_parse_plan_value("x2 y0 bx0 by0 bz0 z0", &r));   // out of range
     CHECK(!tune_parse_plan_value("x1 y0", &r));                  // truncated
     const unsigned char a[3] = {1, 2, 3}, b[3] = {1, 2, 4};
