@@ -62,11 +62,11 @@ namespace lgf {
 LGF_EXTERN_PASSES(float)
 LGF_EXTERN_PASSES(double)
 #undef LGF_EXTERN_PASSES
-// the fused y+x inverse: lgf_poisson_f32_fused_<My>.cu
+// the fused y+x inverse: lgf_poisson_f32_fused_<My>_<part>.cu
 namespace pk {
 #define LGF_EXTERN_YX(MYV)                                                                                     \
-    extern template lgf_status yx_launch_my<MYV>(lgf_ctx *, int, int, YXJob *, int, cudaStream_t);            \
-    extern template bool yx_info_my<MYV>(int, size_t *, int *);
+    extern template lgf_status yx_launch_my<MYV, 0>(lgf_ctx *, int, int, YXJob *, int, cudaStream_t);         \
+    extern template lgf_status yx_launch_my<MYV, 1>(lgf_ctx *, int, int, YXJob *, int, cudaStream_t);
 LGF_EXTERN_YX(64)
 LGF_EXTERN_YX(80)
 LGF_EXTERN_YX(96)
@@ -250,10 +250,14 @@ bool yx_info(int My, int Mx, size_t *work, int *lpc)
 lgf_status yx_launch(lgf_ctx *ctx, int My, int Mx, int ncl, pk::YXJob *jobs, int n, cudaStream_t s)
 {
     switch (My) {
-    case 64: return pk::yx_launch_my<64>(ctx, Mx, ncl, jobs, n, s);
-    case 80: return pk::yx_launch_my<80>(ctx, Mx, ncl, jobs, n, s);
-    case 96: return pk::yx_launch_my<96>(ctx, Mx, ncl, jobs, n, s);
-    case 128: return pk::yx_launch_my<128>(ctx, Mx, ncl, jobs, n, s);
+    case 64: return pk::yx_part(Mx) ? pk::yx_launch_my<64, 1>(ctx, Mx, ncl, jobs, n, s)
+                                    : pk::yx_launch_my<64, 0>(ctx, Mx, ncl, jobs, n, s);
+    case 80: return pk::yx_part(Mx) ? pk::yx_launch_my<80, 1>(ctx, Mx, ncl, jobs, n, s)
+                                    : pk::yx_launch_my<80, 0>(ctx, Mx, ncl, jobs, n, s);
+    case 96: return pk::yx_part(Mx) ? pk::yx_launch_my<96, 1>(ctx, Mx, ncl, jobs, n, s)
+                                    : pk::yx_launch_my<96, 0>(ctx, Mx, ncl, jobs, n, s);
+    case 128: return pk::yx_part(Mx) ? pk::yx_launch_my<128, 1>(ctx, Mx, ncl, jobs, n, s)
+                                     : pk::yx_launch_my<128, 0>(ctx, Mx, ncl, jobs, n, s);
     default: return fail(ctx, LGF_EUNSUPPORTED, "fused inverse: length along y not instantiated");
     }
 }

@@ -210,19 +210,53 @@ lgf_status yx_m(lgf_ctx *ctx, YXJob *jobs, int n, cudaStream_t s)
     return rag_send(ctx, kern, YXCfg<MY, MX>::THREADS, smem, jobs, n, s, "poisson_yx_inverse");
 }
 
-template <int MY, int NCL>
+// The lengths along x in two parts (PART 0: up to 384, PART 1: above), each
+// part of each length along y its own translation unit.
+template <int MY, int PART, int NCL>
 lgf_status yx_mx(lgf_ctx *ctx, int Mx, YXJob *jobs, int n, cudaStream_t s)
 {
-    LGF_DISPATCH_ML(Mx, (yx_m<MY, LM, NCL>(ctx, jobs, n, s)));
+    if constexpr (PART == 0) {
+        switch (Mx) {
+        case 32: return yx_m<MY, 32, NCL>(ctx, jobs, n, s);
+        case 64: return yx_m<MY, 64, NCL>(ctx, jobs, n, s);
+        case 80: return yx_m<MY, 80, NCL>(ctx, jobs, n, s);
+        case 96: return yx_m<MY, 96, NCL>(ctx, jobs, n, s);
+        case 128: return yx_m<MY, 128, NCL>(ctx, jobs, n, s);
+        case 160: return yx_m<MY, 160, NCL>(ctx, jobs, n, s);
+        case 192: return yx_m<MY, 192, NCL>(ctx, jobs, n, s);
+        case 256: return yx_m<MY, 256, NCL>(ctx, jobs, n, s);
+        case 320: return yx_m<MY, 320, NCL>(ctx, jobs, n, s);
+        case 384: return yx_m<MY, 384, NCL>(ctx, jobs, n, s);
+        default: break;
+        }
+    } else {
+        switch (Mx) {
+        case 512: return yx_m<MY, 512, NCL>(ctx, jobs, n, s);
+        case 640: return yx_m<MY, 640, NCL>(ctx, jobs, n, s);
+        case 768: return yx_m<MY, 768, NCL>(ctx, jobs, n, s);
+        case 1024: return yx_m<MY, 1024, NCL>(ctx, jobs, n, s);
+        case 1280: return yx_m<MY, 1280, NCL>(ctx, jobs, n, s);
+        case 1536: return yx_m<MY, 1536, NCL>(ctx, jobs, n, s);
+        case 2048: return yx_m<MY, 2048, NCL>(ctx, jobs, n, s);
+        case 2560: return yx_m<MY, 2560, NCL>(ctx, jobs, n, s);
+        case 3072: return yx_m<MY, 3072, NCL>(ctx, jobs, n, s);
+        case 4096: return yx_m<MY, 4096, NCL>(ctx, jobs, n, s);
+        default: break;
+        }
+    }
+    return fail(ctx, LGF_EUNSUPPORTED, "fused inverse: length along x not in this part");
 }
 
-template <int MY>
+// Part of a length along x.
+inline int yx_part(int Mx) { return Mx <= 384 ? 0 : 1; }
+
+template <int MY, int PART>
 lgf_status yx_launch_my(lgf_ctx *ctx, int Mx, int ncl, YXJob *jobs, int n, cudaStream_t s)
 {
     switch (ncl) {
-    case 1: return yx_mx<MY, 1>(ctx, Mx, jobs, n, s);
-    case 2: return yx_mx<MY, 2>(ctx, Mx, jobs, n, s);
-    case 4: return yx_mx<MY, 4>(ctx, Mx, jobs, n, s);
+    case 1: return yx_mx<MY, PART, 1>(ctx, Mx, jobs, n, s);
+    case 2: return yx_mx<MY, PART, 2>(ctx, Mx, jobs, n, s);
+    case 4: return yx_mx<MY, PART, 4>(ctx, Mx, jobs, n, s);
     default: return fail(ctx, LGF_EINVAL, "fused inverse: cluster size 1, 2 or 4");
     }
 }
