@@ -505,7 +505,7 @@ def run_ours(args, rank, world, dist):
                    "pass_io_GBps": (io[k] / (t / nprof * 1e-3) / 1e9) if k in io else None}
                for k, (n, t) in stats.items()}
     peak, peak_kind = measured_peaks()
-    # roofline of the Poisson apply (SURVEY 8(d)(ii)): 8 B per target point
+    # roofline of the Poisson apply: 8 B per target point
     # (4 B read of f + 4 B write of u, FP32) over the summed time of its five
     # pass kernels per step
     pois_ms = sum(stats[k][1] for k in POISSON_PASSES if k in stats) / nprof
