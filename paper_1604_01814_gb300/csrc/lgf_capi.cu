@@ -970,6 +970,7 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
         if (it != ctx->tune_db.end() && std::sscanf(it->second.c_str(), "nb%d", &pick) == 1 && pick >= 1 &&
             pick <= nb_max) {
             nb = pick;
+            rag = false;
         } else if (it != ctx->tune_db.end() && std::sscanf(it->second.c_str(), "rg%d", &pick) == 1 && pick >= 1 &&
                    pick <= kBranches) {
             rag = true;

@@ -95,3 +95,42 @@ def test_batch_branch_count_tuned_once_per_shape(oracle, tmp_path):
     for p, q in zip(probs, batch):
         assert rel_linf(q["u"].cpu().numpy().reshape(p.ncomp, -1), _oracle(oracle, p)) < TOL["f32"]
     c.close()
+
+
+@pytest.mark.parametrize("mode", ["rg4", "nb2"])
+def test_batch_execution_read_back_from_file(mode, oracle, tmp_path):
+    """A batch shape's persisted execution (the ragged mode on 4 branches, or
+    per-problem launches on 2) is taken from the file by a new context, which
+    times nothing, reports the mode and matches the oracle."""
+    path = tmp_path / "tune.txt"
+    probs = [li.random_sparse(60 + k, b=8, nsrc=2, ntgt=3 + k, extent=(3, 3, 2), ncomp=1) for k in range(4)]
+
+    def run(ctx):
+        batch = []
+        for p in probs:
+            f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
+            u = torch.full((p.tgt.shape[0] * p.b ** 3,), float("nan"), device="cuda")
+            batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=1, op=lgf.LGF_OP_POISSON))
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            ctx.batch_apply(batch, stream=s)
+        s.synchronize()
+        return batch
+
+    # a tuned context writes the batch key; its value is then replaced by `mode`
+    c1 = _fresh("f32")
+    c1.autotune(lgf.LGF_TUNE_ON, str(path))
+    run(c1)
+    c1.close()
+    lines = path.read_text().splitlines()
+    key = next(l.split(" -> ")[0] for l in lines if l.startswith("B f32 "))
+    path.write_text("\n".join(lines) + f"\n{key} -> {mode}\n")
+    c2 = _fresh("f32")
+    c2.autotune(lgf.LGF_TUNE_CACHED, str(path))
+    batch = run(c2)
+    r = c2.tune_report()
+    assert r["candidates_timed"] == 0 and r["batches_tuned"] == 0
+    assert r["last_ragged"] == (mode == "rg4") and r["last_branches"] == int(mode[2:])
+    for p, q in zip(probs, batch):
+        assert rel_linf(q["u"].cpu().numpy(), _oracle(oracle, p).reshape(-1)) < TOL["f32"]
+    c2.close()
