@@ -178,3 +178,42 @@ def test_ragged_batch_against_oracle(prec, rag_ctx, oracle):
         if op == lgf.LGF_OP_POISSON_THEN_INTFACTOR:
             ref = oracle.intfactor_blocks(alpha, p.b, p.tgt, ref.reshape(-1, p.b ** 3), p.tgt).reshape(-1)
         assert rel_linf(q["u"].cpu().numpy(), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_ragged_random_batches_equal_per_problem(seed, rag_ctx):
+    """Seeded random batches (block edges 8 and 16, uneven sets, every
+    operation, several fields and right-hand sides): the ragged mode equals
+    per-problem launches bit for bit."""
+    rng = np.random.default_rng(seed)
+    probs, ops, alphas, nrhs = [], [], [], []
+    for i in range(24):
+        b = int(rng.choice([8, 16]))
+        ext = tuple(int(v) for v in rng.integers(1, 5, size=3))
+        nsrc = int(rng.integers(1, 1 + min(6, ext[0] * ext[1] * ext[2])))
+        ntgt = int(rng.integers(1, 1 + min(7, ext[0] * ext[1] * ext[2])))
+        r = int(rng.integers(1, 3))
+        p = li.random_sparse(seed * 1000 + i, b=b, nsrc=nsrc, ntgt=ntgt, extent=ext, nrhs=r,
+                             ncomp=int(rng.choice([1, 3])))
+        probs.append(p)
+        nrhs.append(r)
+        ops.append(int(rng.choice([lgf.LGF_OP_POISSON, lgf.LGF_OP_POISSON_THEN_INTFACTOR, lgf.LGF_OP_KINV,
+                                   lgf.LGF_OP_INTFACTOR])))
+        alphas.append(float(rng.choice([0.05, 0.25, 1.0])))
+    outs = {}
+    for mode in ("ragged", "per_problem"):
+        ctx = rag_ctx["f32", mode]
+        batch = []
+        for p, op, a in zip(probs, ops, alphas):
+            f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
+            u = torch.full((p.nrhs * p.ncomp * p.tgt.shape[0] * p.b ** 3,), float("nan"), device="cuda")
+            batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, nrhs=p.nrhs, op=op, alpha=a,
+                              dx=1.0))
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            ctx.batch_apply(batch, stream=s)
+        s.synchronize()
+        outs[mode] = [q["u"].cpu() for q in batch]
+    for a, b in zip(outs["ragged"], outs["per_problem"]):
+        assert torch.equal(a, b)
+        assert not torch.isnan(a).any()
