@@ -90,3 +90,36 @@ def test_fused_inverse_equals_separate_passes(name, xy, p, built, tmp_path, orac
     for c in range(nf):
         ref = oracle.poisson_direct(p.b, p.src, p.f[0, c], pts_all[idx], R=64)
         assert rel_linf(got[c, idx], ref) < 1e-5
+
+
+def test_fused_inverse_in_ragged_batches(built, tmp_path):
+    """Several problems whose plans take the fused inverse (different lengths
+    along x and y, so several fused launches of different cluster sizes, and
+    one problem whose length along y has no fused kernel) in one ragged
+    batch: equal bit for bit to the same batch with every inverse apart."""
+    probs = [c[2] for c in cases()]
+    probs.append(_case(9, 16, [[0, 0, 0]], li.box_blocks(2, 10, 1)))   # 160+ along y: never fused
+    outs, reps = {}, {}
+    for fuse in (1, 0):
+        path = tmp_path / f"tune_{fuse}.txt"
+        path.write_text("".join(f"{_key(p, p.ncomp)} -> x0 y0 bx0 by0 bz0 z0 f{fuse}\n" for p in probs))
+        ctx = lgf.Context("f32", flags=lgf._binding.LGF_FLAG_BATCH_RAGGED)
+        ctx.table_build(48)
+        ctx.autotune(lgf.LGF_TUNE_CACHED, str(path))
+        batch = []
+        for p in probs:
+            f = torch.tensor(p.f.reshape(-1), dtype=torch.float32, device="cuda")
+            u = torch.full((p.ncomp * p.tgt.shape[0] * p.b ** 3,), float("nan"), device="cuda")
+            batch.append(dict(b=p.b, src=p.src, tgt=p.tgt, f=f, u=u, ncomp=p.ncomp, op=lgf.LGF_OP_POISSON))
+        s = torch.cuda.Stream()
+        for _ in range(2):   # capture, then replay
+            with torch.cuda.stream(s):
+                ctx.batch_apply(batch, stream=s)
+            s.synchronize()
+        outs[fuse] = [q["u"].cpu() for q in batch]
+        reps[fuse] = ctx.tune_report()
+        ctx.close()
+    assert reps[1]["last_ragged"] == 1 and reps[1]["fused_inverse"] == len(probs) - 1
+    assert reps[0]["fused_inverse"] == 0
+    for a, b in zip(outs[1], outs[0]):
+        assert torch.equal(a, b) and not torch.isnan(a).any()
