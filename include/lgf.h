@@ -220,7 +220,8 @@ typedef struct {
    ragged mode (see LGF_FLAG_BATCH_RAGGED) the Poisson parts of all
    problems instead run together: one launch per pass and transform length
    (each CTA finds its problem in a job table passed with the launch, up to
-   64 problems per launch), the lengths of a pass on concurrent branches,
+   64 problems per launch), the lengths of a pass on 2 concurrent branches
+   (4 when the autotuner finds that faster),
    every part with its own slice of one scratch; the integrating-factor
    groups that read Poisson results follow, their jobs of all block sets
    together in one launch per pass (and block edge and stencil radius

@@ -831,7 +831,10 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
                                     probs[i].ncomp * probs[i].nrhs, probs[i].dx});
     // (the default for batches of several Poisson parts, or on request)
     bool rag = !ctx->opt_units && ((ctx->opt_rag && !parts.empty()) || parts.size() >= 2);
-    if (rag && !ctx->prof) nb = std::min(kDefaultBranches, kBranches);
+    // (the ragged mode's length groups of a pass on 2 branches by default:
+    // on the 64-plate batch 2 branches ran 1.7 % faster than 4, 8 and 1 slower)
+    constexpr int kRagBranches = 2;
+    if (rag && !ctx->prof) nb = kRagBranches;
     // integrating-factor groups of the ragged mode: those that read the
     // batch's Poisson results (after the Poisson passes, scratch of branch 0)
     // and those that read only batch inputs (alongside the Poisson passes on
@@ -959,10 +962,9 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
     };
     // 4. the execution of this batch shape: the persisted choice, or (tuning
     //    on, a new shape) the fastest of 1, 2, 4 and 8 branches of per-problem
-    //    launches and of the ragged mode (on 4 branches), timed with direct
+    //    launches and of the ragged mode on 2 or 4 branches, timed with direct
     //    launches on the caller's stream (the default first: the others must
     //    win by 3 %)
-    const int nb_rag = std::min(kDefaultBranches, kBranches);
     if (ctx->tune_mode != LGF_TUNE_OFF && !ctx->prof && s != nullptr && nb_max > 1) {
         const std::string tk = tune_batch_key(ctx->prec == LGF_F64, tune_hash(shape.data(), shape.size()));
         auto it = ctx->tune_db.find(tk);
@@ -983,11 +985,18 @@ lgf_status lgf_batch_apply(lgf_ctx *ctx, const lgf_problem *probs, int32_t nprob
             int best = nb;
             bool best_rag = false;
             // the default first: the others must beat it by 3 %
-            static constexpr int kCand[4] = {4, 8, 2, 1};
-            const bool rag0 = rag;
-            for (int ci = 0; ci < 5; ++ci) {
-                const bool crag = rag0 ? ci == 0 : ci == 4;
-                const int cand = crag ? nb_rag : kCand[rag0 ? ci - 1 : ci];
+            struct Cand {
+                bool rag;
+                int nb;
+            };
+            static constexpr Cand kRagFirst[6] = {{true, kRagBranches}, {true, 4}, {false, 4},
+                                                  {false, 8}, {false, 2}, {false, 1}};
+            static constexpr Cand kUnitsFirst[6] = {{false, 4}, {false, 8}, {false, 2},
+                                                    {false, 1}, {true, kRagBranches}, {true, 4}};
+            const Cand *cands = rag ? kRagFirst : kUnitsFirst;
+            for (int ci = 0; ci < 6; ++ci) {
+                const bool crag = cands[ci].rag;
+                const int cand = cands[ci].nb;
                 if (!crag && cand > nb_max) continue;
                 if (crag && parts.empty()) continue;
                 rag = crag;
